@@ -1,0 +1,359 @@
+"""Benchmark of the docking hot path on GB300 (one JSON line on rank 0).
+
+A step is one whole plain-mode search over the batch: every ligand's
+population drawn, then (generations - 1) fused GA-step + pose + FP32-score
+generations, then the per-ligand best-8 FP64 rescoring, all through the C ABI.
+Workload (default): 1,000 synthetic ligands, heavy atoms uniform in 10-60,
+rotatable bonds uniform in 0-12, against a 4,000-atom pocket (cavity radius
+16 A, 86^3 grid at 0.375 A), 1,024 poses x 50 generations per ligand.
+
+value: ligands/s with the ligand set already resident on the device.
+e2e: ligands/s through the public API from host arrays (ligand upload with
+its host-side preparation, the search, and the D2H copy of the results).
+Under torchrun each rank docks its own shard of the same size (weak scaling,
+no collective on the data path).
+
+--impl reference times the CPU oracle (plain FP64 C, all host cores) on a
+bounded sample of the same workload; it is the only other user of oracle/.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "c2"
+METRIC = "ligands/s (plain exact GA docking: 1,024 poses x 50 generations per ligand)"
+DESCR = ("1,000 synthetic ligands (10-60 heavy atoms, 0-12 torsions) vs a 4,000-atom pocket "
+         "(16 A cavity, 86^3 x 7 grid maps), 1,024 poses x 50 generations, FP64 best-8 rescoring")
+
+# Algorithmic work per pose (FMA = 2 flops); see DESIGN.md "Roofline".
+FLOP_RIGID_PER_ATOM = 18        # 3x3 rotation + translation
+FLOP_POSE_FIXED = 40            # quaternion -> matrix
+FLOP_TORSION = 40               # axis, sin/cos, rotation matrix
+FLOP_PER_MOVED_ATOM = 21        # rotate one atom about the bond
+FLOP_INTER_PER_ATOM = 62        # grid coordinates, 8 corners, 7 lerps
+FLOP_PER_PAIR = 34              # distance + the four pair terms + sum
+MUFU_PER_PAIR = 4               # rsqrt, 2 x ex2, rcp
+MUFU_PER_TORSION = 3            # sin, cos, rsqrt
+MUFU_PER_POSE = 1               # rsqrt of the quaternion norm
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def src_hash():
+    h = hashlib.sha256()
+    for f in ("search.cu", "device_common.cuh", "dock_internal.h"):
+        with open(os.path.join(ROOT, "paper_2509_12232_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic():
+    """DRAM bytes per launch of the search kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "search_kernel_c2.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != src_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def work_per_pose(info, n_lig):
+    """Algorithmic FP32 flops and MUFU ops for one pose of every ligand (sum)."""
+    flops = (n_lig * FLOP_POSE_FIXED + info["n_atoms"] * (FLOP_RIGID_PER_ATOM + FLOP_INTER_PER_ATOM) +
+             info["n_torsions"] * FLOP_TORSION + info["n_moved"] * FLOP_PER_MOVED_ATOM +
+             info["n_pairs"] * FLOP_PER_PAIR)
+    mufu = n_lig * MUFU_PER_POSE + info["n_torsions"] * MUFU_PER_TORSION + info["n_pairs"] * MUFU_PER_PAIR
+    return flops, mufu
+
+
+def run_reference(args, rank, world):
+    """CPU oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return 0
+    from oracle import oracle as o
+    from paper_2509_12232_gb300 import synth
+    pk, ligs, w = synth.make_workload(WORKLOAD)
+    P = o.Params(synth.TYPE_PARAMS)
+    pks = o.pocket_from(pk)
+    grid = o.grid_build(pks, P)
+    cores = os.cpu_count() or 1
+    n_sample = cores * args.ref_ligands_per_core
+    times = []
+    for step in range(args.warmup + args.steps):
+        idx = [(step * n_sample + i) % ligs.n_ligands for i in range(n_sample)]
+        sub = ligs.subset(idx)
+        t0 = time.perf_counter()
+        o.dock_batch(sub, P, pks, grid, pop=w.pop, generations=w.generations, seed=0, n_threads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = n_sample * len(times) / tot
+    sample = "%d ligands per step (%d per core) of the %s set, full %d poses x %d generations each" % (
+        n_sample, args.ref_ligands_per_core, WORKLOAD, w.pop, w.generations)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ligands/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": DESCR, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "ligands/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "ligands/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(budget_s):
+    """The oracle as it stands, on all host cores, on a bounded sample of the
+    workload (about budget_s seconds)."""
+    from oracle import oracle as o
+    from paper_2509_12232_gb300 import synth
+    pk, ligs, w = synth.make_workload(WORKLOAD)
+    P = o.Params(synth.TYPE_PARAMS)
+    pks = o.pocket_from(pk)
+    grid = o.grid_build(pks, P)
+    cores = os.cpu_count() or 1
+    # calibrate on one ligand x 2 generations
+    sub = ligs.subset([0])
+    t0 = time.perf_counter()
+    o.dock_batch(sub, P, pks, grid, pop=w.pop, generations=2, seed=0, n_threads=1)
+    per_lig = (time.perf_counter() - t0) / 2 * w.generations
+    per_lig *= float(np.diff(ligs.atom_off).mean() ** 2) / float(ligs.n_atoms(0) ** 2)
+    n = int(max(cores, min(ligs.n_ligands, round(budget_s * cores / max(per_lig, 1e-3)))))
+    n = max(cores, (n // cores) * cores)
+    idx = list(range(n))
+    sub = ligs.subset(idx)
+    t0 = time.perf_counter()
+    o.dock_batch(sub, P, pks, grid, pop=w.pop, generations=w.generations, seed=0, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "ligands/s", "cores": cores, "kind": "oracle",
+            "sample": "first %d ligands of the %s set, full %d poses x %d generations each, %.1f s" % (
+                n, WORKLOAD, w.pop, w.generations, dt)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-ligands-per-core", type=int, default=1)
+    ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    rank, world, local = env_rank()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2509_12232_gb300 import build, dock, synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    build.build()
+    dock.lib()
+    stream = torch.cuda.current_stream()
+    pk, _, w = synth.make_workload(WORKLOAD, pocket=True)
+    # rank r docks shard r: same size distribution, its own draw and ligand ids
+    rng = np.random.Generator(np.random.Philox(1000 + rank))
+    na, nt = synth.ligand_sizes(rng, w.sizes, w.n_ligands)
+    ligs = synth.make_ligands(rng, na, nt, id_base=rank * w.n_ligands)
+    pocket = dock.dock_create_pocket(pk.x, pk.y, pk.z, pk.q, pk.type, pk.center, pk.radius,
+                                     pk.spacing, synth.TYPE_PARAMS, stream=stream)
+    largs = (ligs.atom_off, ligs.x, ligs.y, ligs.z, ligs.q, ligs.type, ligs.parent, ligs.tors_off,
+             ligs.tors_b, ligs.ligand_id)
+    gl = dock.dock_load_ligands(pocket, *largs, stream=stream)
+    info = dock.dock_ligands_info(gl)
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        job = dock.dock_batch(pocket, gl, w.pop, w.generations, seed=0, use_graph=1, stream=stream)
+        return job
+
+    # warm-up
+    for _ in range(args.warmup):
+        j = step()
+        torch.cuda.synchronize()
+        j.close()
+    # per-launch kernel times for the roofline (separate profiled pass)
+    os.environ["DOCK_PROFILE_LAUNCHES"] = "1"
+    j = step()
+    ms_kernels, n_launch = dock.dock_job_kernel_time(j)
+    j.close()
+    del os.environ["DOCK_PROFILE_LAUNCHES"]
+    # timed region
+    clocks = Clocks(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    jobs = []
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)          # evict L2 between steps
+        ev[i][0].record(stream)
+        jobs.append(step())
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    for j in jobs:
+        j.close()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_step = ms / args.steps
+    total_ligands = w.n_ligands * world
+    value = total_ligands / (ms_step / 1000.0)
+    poses_per_step = w.n_ligands * w.pop * w.generations * world
+
+    # end to end through the public API from host arrays
+    h2d = info["h2d_bytes"]
+    d2h = w.n_ligands * dock.RESULT_DTYPE.itemsize + 4
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        g2 = dock.dock_load_ligands(pocket, *largs, stream=stream)
+        j = dock.dock_batch(pocket, g2, w.pop, w.generations, seed=0, use_graph=1, stream=stream)
+        dock.dock_results(j)
+        j.close()
+        g2.close()
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12           # TFLOP/s
+    mufu_peak = n_sm * 16 * sm_mhz * 1e6 / 1e12                 # Tops/s
+    flops_pose, mufu_pose = work_per_pose(info, w.n_ligands)
+    per_launch_s = ms_kernels / 1000.0 / max(n_launch, 1)
+    ach_fp32 = flops_pose * w.pop / per_launch_s / 1e12
+    ach_mufu = mufu_pose * w.pop / per_launch_s / 1e12
+    roof = {"bound": "alu", "achieved": round(ach_fp32, 3), "peak": round(fp32_peak, 2),
+            "unit": "TFLOP/s", "frac": round(ach_fp32 / fp32_peak, 4),
+            "traffic": read_traffic(), "kernel": "search_kernel",
+            "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
+            "mufu": {"achieved": round(ach_mufu, 4), "peak": round(mufu_peak, 4), "unit": "Tops/s",
+                     "frac": round(ach_mufu / mufu_peak, 4)},
+            "launch_ms": round(per_launch_s * 1000, 4), "launches_timed": n_launch}
+    line = {"metric": METRIC, "value": round(value, 2), "unit": "ligands/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": DESCR, "l2": "flushed between steps (256 MiB write)",
+                       "ligands_per_gpu": w.n_ligands, "pop": w.pop, "generations": w.generations},
+            "poses_scored_per_s": round(poses_per_step / (ms_step / 1000.0), 1),
+            "roofline": roof,
+            "e2e": {"value": round(total_ligands / e2e_s, 2), "unit": "ligands/s",
+                    "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": args.steps * (w.generations + 1),
+            "clocks": clk}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_baseline_seconds)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

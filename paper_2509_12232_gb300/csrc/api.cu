@@ -1,0 +1,893 @@
+// C ABI of the docking library: pocket and ligand set preparation, the
+// batched search (one persistent kernel per generation, optionally captured
+// as a CUDA graph), results and pose scoring. See include/dock.h.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "dock_internal.h"
+
+namespace dk {
+cudaError_t search_occupancy(int threads, int smem, int *blocks_per_sm);
+cudaError_t launch_set_deadline(uint64_t *deadline, uint64_t timeout_ns, cudaStream_t s);
+}  // namespace dk
+
+using namespace dk;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static int fail(int st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CU(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      int st_ = e_ == cudaErrorMemoryAllocation ? DOCK_ENOMEM : DOCK_ECUDA;          \
+      return fail(st_, "%s failed: %s", #call, cudaGetErrorString(e_));              \
+    }                                                                                \
+  } while (0)
+
+extern "C" const char *dock_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *dock_version(void) {
+  return "gb300-dock 0.1 (sm_103a, Philox4x64-10 GA, FP32 Kahan scoring, FP64 rescoring)";
+}
+
+template <typename T>
+static cudaError_t dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+template <typename T>
+static void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+// AutoDock4 free-energy constants for the host-side pair coefficients.
+static const double kHWVdw = 0.1662, kHWHb = 0.1209, kHWElec = 0.1406, kHWSol = 0.1322;
+static const double kHCoulomb = 332.06363, kHQasp = 0.01097;
+
+// ---------------------------------------------------------------------------
+// pocket
+// ---------------------------------------------------------------------------
+struct dock_pocket {
+  int device = 0;
+  int n_types = 0;
+  std::vector<dock_type_params> params;
+  dock_type_params *d_params = nullptr;
+  float4 *d_prot = nullptr;
+  uint8_t *d_ptype = nullptr;
+  int n_prot = 0;
+  float4 *d_maps = nullptr;
+  int n = 0;
+  double ox = 0, oy = 0, oz = 0, h = 0;
+  float center[3] = {0, 0, 0};
+  float radius = 0;
+  ~dock_pocket() {
+    dfree(d_params);
+    dfree(d_prot);
+    dfree(d_ptype);
+    dfree(d_maps);
+  }
+};
+
+static GridView grid_view(const dock_pocket *p) {
+  GridView g;
+  g.maps = p->d_maps;
+  g.n = p->n;
+  g.ox = (float)p->ox;
+  g.oy = (float)p->oy;
+  g.oz = (float)p->oz;
+  g.inv_h = (float)(1.0 / p->h);
+  g.n_types = p->n_types;
+  return g;
+}
+
+extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_pocket **out) {
+  if (!d || !out) return fail(DOCK_EINVAL, "dock_create_pocket: NULL argument");
+  *out = nullptr;
+  if (d->n_types < 1 || d->n_types > DOCK_MAX_TYPES || !d->params)
+    return fail(DOCK_EINVAL, "dock_create_pocket: n_types %d out of range", d->n_types);
+  if (!(d->spacing > 0.0f) || !(d->radius > 0.0f))
+    return fail(DOCK_EINVAL, "dock_create_pocket: spacing and radius must be > 0");
+  if (d->n_atoms < 0 || (d->n_atoms > 0 && (!d->x || !d->y || !d->z || !d->q || !d->type)))
+    return fail(DOCK_EINVAL, "dock_create_pocket: bad protein arrays");
+  for (int t = 0; t < d->n_types; ++t) {
+    const dock_type_params &p = d->params[t];
+    if (p.hb_role < 0 || p.hb_role > 2 || !(p.Rii > 0) || !(p.eps >= 0))
+      return fail(DOCK_EINVAL, "dock_create_pocket: bad parameters for type %d", t);
+  }
+  std::vector<float4> prot((size_t)d->n_atoms);
+  for (int i = 0; i < d->n_atoms; ++i) {
+    if (d->type[i] >= d->n_types) return fail(DOCK_EINVAL, "protein atom %d: type out of range", i);
+    if (!std::isfinite(d->x[i]) || !std::isfinite(d->y[i]) || !std::isfinite(d->z[i]) ||
+        !std::isfinite(d->q[i]))
+      return fail(DOCK_EINVAL, "protein atom %d: non-finite value", i);
+    prot[i] = make_float4(d->x[i], d->y[i], d->z[i], d->q[i]);
+  }
+  const double n_f = std::floor(2.0 * (double)d->radius / (double)d->spacing + 1e-9) + 1.0;
+  if (n_f < 2 || n_f > 1024) return fail(DOCK_EINVAL, "grid of %g nodes per axis", n_f);
+  dock_pocket *P = new dock_pocket();
+  std::unique_ptr<dock_pocket> guard(P);
+  CU(cudaGetDevice(&P->device));
+  P->n_types = d->n_types;
+  P->params.assign(d->params, d->params + d->n_types);
+  P->n_prot = d->n_atoms;
+  P->n = (int)n_f;
+  P->h = d->spacing;
+  const double half = 0.5 * (P->n - 1) * P->h;
+  P->ox = (double)d->center[0] - half;
+  P->oy = (double)d->center[1] - half;
+  P->oz = (double)d->center[2] - half;
+  for (int m = 0; m < 3; ++m) P->center[m] = d->center[m];
+  P->radius = d->radius;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nodes = (size_t)P->n * P->n * P->n;
+  CU(dalloc(&P->d_params, P->n_types));
+  CU(dalloc(&P->d_prot, prot.size()));
+  CU(dalloc(&P->d_ptype, (size_t)d->n_atoms));
+  CU(dalloc(&P->d_maps, nodes * P->n_types));
+  CU(cudaMemcpyAsync(P->d_params, P->params.data(), sizeof(dock_type_params) * P->n_types,
+                     cudaMemcpyHostToDevice, s));
+  if (d->n_atoms) {
+    CU(cudaMemcpyAsync(P->d_prot, prot.data(), sizeof(float4) * prot.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(P->d_ptype, d->type, d->n_atoms, cudaMemcpyHostToDevice, s));
+  }
+  CU(launch_grid_build_impl(P->d_prot, P->d_ptype, P->n_prot, P->d_params, P->n_types, P->n,
+                            P->ox, P->oy, P->oz, P->h, P->d_maps, s));
+  CU(cudaStreamSynchronize(s));
+  *out = guard.release();
+  return DOCK_OK;
+}
+
+extern "C" void dock_pocket_destroy(dock_pocket *p) { delete p; }
+
+extern "C" int dock_pocket_grid(const dock_pocket *p, int32_t *n, float origin[3],
+                                const void **maps) {
+  if (!p) return fail(DOCK_EINVAL, "dock_pocket_grid: NULL pocket");
+  if (n) *n = p->n;
+  if (origin) {
+    origin[0] = (float)p->ox;
+    origin[1] = (float)p->oy;
+    origin[2] = (float)p->oz;
+  }
+  if (maps) *maps = p->d_maps;
+  return DOCK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// ligands
+// ---------------------------------------------------------------------------
+struct Workspace {
+  size_t geno_cap = 0, score_cap = 0, best_cap = 0, item_cap = 0, gen_cap = 0, lig_cap = 0;
+  float *geno[2] = {nullptr, nullptr};
+  float *score[2] = {nullptr, nullptr};
+  unsigned long long *best = nullptr;  // [generations][n_ligands]
+  uint32_t *counters = nullptr;        // [generations]
+  Item *items = nullptr;
+  int64_t *geno_off = nullptr;
+  int32_t *status = nullptr;           // [1] + deadline slot
+  uint64_t *deadline = nullptr;
+  int32_t *lig_status = nullptr;
+  dock_result *results = nullptr;
+  // cached graph
+  cudaGraphExec_t graph = nullptr;
+  std::vector<uint8_t> graph_key;
+  ~Workspace() {
+    for (int i = 0; i < 2; ++i) {
+      dfree(geno[i]);
+      dfree(score[i]);
+    }
+    dfree(best);
+    dfree(counters);
+    dfree(items);
+    dfree(geno_off);
+    dfree(status);
+    dfree(deadline);
+    dfree(lig_status);
+    dfree(results);
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+};
+
+struct dock_ligands {
+  int device = 0;
+  int n_ligands = 0;
+  int max_atoms = 0;
+  std::vector<LigInfo> info;
+  LigInfo *d_info = nullptr;
+  float4 *d_atoms = nullptr;      // centred
+  float4 *d_atoms_raw = nullptr;  // input coordinates
+  double *d_centroid = nullptr;
+  uint8_t *d_types = nullptr;
+  uint32_t *d_pair_idx = nullptr;
+  float4 *d_pair_coef = nullptr;
+  TorInfo *d_tors = nullptr;
+  uint8_t *d_moves = nullptr;
+  int64_t total_pairs = 0, total_atoms = 0, total_tors = 0, total_moved = 0, h2d_bytes = 0;
+  Workspace ws;
+  ~dock_ligands() {
+    dfree(d_info);
+    dfree(d_atoms);
+    dfree(d_atoms_raw);
+    dfree(d_centroid);
+    dfree(d_types);
+    dfree(d_pair_idx);
+    dfree(d_pair_coef);
+    dfree(d_tors);
+    dfree(d_moves);
+  }
+};
+
+namespace {
+struct LigHost {
+  std::vector<uint32_t> pair_idx;
+  std::vector<float4> pair_coef;
+  std::vector<TorInfo> tors;   // move_off relative to this ligand's moves
+  std::vector<uint8_t> moves;
+  double cent[3];
+  std::string err;
+};
+
+// Topology and pair coefficients of ligand l (see dock_load_ligands in dock.h).
+void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, LigHost &H) {
+  const int a0 = b->atom_off[l], n = b->atom_off[l + 1] - a0;
+  const int t0 = b->tors_off[l], k = b->tors_off[l + 1] - t0;
+  char msg[160];
+  if (n < 1 || n > DOCK_MAX_ATOMS) {
+    snprintf(msg, sizeof msg, "ligand %d: %d atoms (1..%d)", l, n, DOCK_MAX_ATOMS);
+    H.err = msg;
+    return;
+  }
+  if (k < 0 || k > DOCK_MAX_TORSIONS) {
+    snprintf(msg, sizeof msg, "ligand %d: %d torsions (0..%d)", l, k, DOCK_MAX_TORSIONS);
+    H.err = msg;
+    return;
+  }
+  const int16_t *par = b->parent + a0;
+  for (int i = 0; i < n; ++i) {
+    if ((i == 0 && par[i] != -1) || (i > 0 && (par[i] < 0 || par[i] >= i))) {
+      snprintf(msg, sizeof msg, "ligand %d: atom %d has parent %d (need parent < index)", l, i, par[i]);
+      H.err = msg;
+      return;
+    }
+    if (b->type[a0 + i] >= P->n_types) {
+      snprintf(msg, sizeof msg, "ligand %d: atom %d type out of range", l, i);
+      H.err = msg;
+      return;
+    }
+    if (!std::isfinite(b->x[a0 + i]) || !std::isfinite(b->y[a0 + i]) ||
+        !std::isfinite(b->z[a0 + i]) || !std::isfinite(b->q[a0 + i])) {
+      snprintf(msg, sizeof msg, "ligand %d: atom %d non-finite", l, i);
+      H.err = msg;
+      return;
+    }
+  }
+  std::vector<uint8_t> rot((size_t)n, 0);
+  for (int j = 0; j < k; ++j) {
+    const int bb = b->tors_b[t0 + j];
+    if (bb <= 0 || bb >= n || (j > 0 && b->tors_b[t0 + j - 1] >= bb)) {
+      snprintf(msg, sizeof msg, "ligand %d: torsion %d child atom %d invalid or out of order", l, j, bb);
+      H.err = msg;
+      return;
+    }
+    rot[bb] = 1;
+  }
+  // centroid and children
+  double c[3] = {0, 0, 0};
+  for (int i = 0; i < n; ++i) {
+    c[0] += b->x[a0 + i];
+    c[1] += b->y[a0 + i];
+    c[2] += b->z[a0 + i];
+  }
+  for (int m = 0; m < 3; ++m) H.cent[m] = c[m] / n;
+  std::vector<std::vector<int>> kids((size_t)n);
+  for (int i = 1; i < n; ++i) kids[par[i]].push_back(i);
+  // atoms moved by each torsion: the subtree below b (b itself stays on the axis)
+  for (int j = 0; j < k; ++j) {
+    const int bb = b->tors_b[t0 + j];
+    TorInfo T;
+    T.move_off = (int32_t)H.moves.size();
+    std::vector<int> stack(kids[bb].begin(), kids[bb].end());
+    while (!stack.empty()) {
+      const int a = stack.back();
+      stack.pop_back();
+      H.moves.push_back((uint8_t)a);
+      for (int ch : kids[a]) stack.push_back(ch);
+    }
+    T.n_move = (int16_t)(H.moves.size() - T.move_off);
+    T.a = (uint8_t)par[bb];
+    T.b = (uint8_t)bb;
+    H.tors.push_back(T);
+  }
+  // rigid fragments: a rotatable bond starts a new fragment
+  std::vector<int> frag((size_t)n, 0);
+  int nf = 0;
+  for (int i = 1; i < n; ++i) frag[i] = rot[i] ? ++nf : frag[par[i]];
+  // bond distances by BFS from every atom
+  std::vector<uint8_t> dist((size_t)n * n, 255);
+  std::vector<int> queue((size_t)n);
+  for (int s0 = 0; s0 < n; ++s0) {
+    uint8_t *d = &dist[(size_t)s0 * n];
+    int qh = 0, qt = 0;
+    queue[qt++] = s0;
+    d[s0] = 0;
+    while (qh < qt) {
+      const int a = queue[qh++];
+      auto visit = [&](int v) {
+        if (d[v] == 255) {
+          d[v] = (uint8_t)std::min(254, d[a] + 1);
+          queue[qt++] = v;
+        }
+      };
+      if (a > 0) visit(par[a]);
+      for (int ch : kids[a]) visit(ch);
+    }
+  }
+  const dock_type_params *tp = P->params.data();
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j) {
+      if (dist[(size_t)i * n + j] <= 3 || frag[i] == frag[j]) continue;
+      const int ti = b->type[a0 + i], tj = b->type[a0 + j];
+      const double qi = b->q[a0 + i], qj = b->q[a0 + j];
+      const bool hb = (tp[ti].hb_role == 1 && tp[tj].hb_role == 2) ||
+                      (tp[ti].hb_role == 2 && tp[tj].hb_role == 1);
+      double c12, cx;
+      if (hb) {
+        const int acc = tp[ti].hb_role == 2 ? ti : tj;
+        const double R = tp[acc].hb_R, e = tp[acc].hb_eps;
+        c12 = kHWHb * 5.0 * e * std::pow(R, 12);
+        cx = kHWHb * 6.0 * e * std::pow(R, 10);
+      } else {
+        const double R = 0.5 * ((double)tp[ti].Rii + (double)tp[tj].Rii);
+        const double e = std::sqrt((double)tp[ti].eps * (double)tp[tj].eps);
+        c12 = kHWVdw * e * std::pow(R, 12);
+        cx = kHWVdw * 2.0 * e * std::pow(R, 6);
+      }
+      const double si = (double)tp[ti].solpar + kHQasp * std::fabs(qi);
+      const double sj = (double)tp[tj].solpar + kHQasp * std::fabs(qj);
+      H.pair_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
+      H.pair_coef.push_back(make_float4((float)c12, (float)cx, (float)(kHWElec * kHCoulomb * qi * qj),
+                                        (float)(kHWSol * (si * tp[tj].vol + sj * tp[ti].vol))));
+    }
+}
+
+template <typename F>
+void parallel_for(int n, F f) {
+  int nt = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 64u);
+  if (n < 64) nt = 1;
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    for (;;) {
+      const int i = next.fetch_add(64);
+      if (i >= n) break;
+      for (int j = i; j < std::min(n, i + 64); ++j) f(j);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(work);
+  work();
+  for (auto &t : th) t.join();
+}
+}  // namespace
+
+extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *b, void *stream,
+                                 dock_ligands **out) {
+  if (!P || !b || !out) return fail(DOCK_EINVAL, "dock_load_ligands: NULL argument");
+  *out = nullptr;
+  const int nl = b->n_ligands;
+  if (nl < 0) return fail(DOCK_EINVAL, "dock_load_ligands: n_ligands < 0");
+  if (nl > 0 && (!b->atom_off || !b->tors_off || !b->x || !b->y || !b->z || !b->q || !b->type ||
+                 !b->parent || !b->ligand_id || (!b->tors_b && b->tors_off[nl] > 0)))
+    return fail(DOCK_EINVAL, "dock_load_ligands: NULL array");
+  if (nl > 0 && (b->atom_off[0] != 0 || b->tors_off[0] != 0))
+    return fail(DOCK_EINVAL, "dock_load_ligands: offsets must start at 0");
+  for (int l = 0; l < nl; ++l)
+    if (b->atom_off[l + 1] < b->atom_off[l] || b->tors_off[l + 1] < b->tors_off[l])
+      return fail(DOCK_EINVAL, "dock_load_ligands: offsets decrease at ligand %d", l);
+  std::vector<LigHost> H((size_t)nl);
+  parallel_for(nl, [&](int l) { prepare_ligand(b, P, l, H[l]); });
+  for (int l = 0; l < nl; ++l)
+    if (!H[l].err.empty()) return fail(DOCK_EINVAL, "dock_load_ligands: %s", H[l].err.c_str());
+  dock_ligands *L = new dock_ligands();
+  std::unique_ptr<dock_ligands> guard(L);
+  CU(cudaGetDevice(&L->device));
+  L->n_ligands = nl;
+  L->info.resize((size_t)nl);
+  const int n_atoms = nl ? b->atom_off[nl] : 0;
+  int64_t np = 0, nm = 0, nt = 0;
+  for (int l = 0; l < nl; ++l) {
+    LigInfo &I = L->info[l];
+    I.atom_off = b->atom_off[l];
+    I.n = b->atom_off[l + 1] - b->atom_off[l];
+    I.k = b->tors_off[l + 1] - b->tors_off[l];
+    I.pair_off = (int32_t)np;
+    I.n_pairs = (int32_t)H[l].pair_idx.size();
+    I.tors_off = (int32_t)nt;
+    I.ligand_id = b->ligand_id[l];
+    for (auto &T : H[l].tors) T.move_off += (int32_t)nm;
+    np += I.n_pairs;
+    nm += (int64_t)H[l].moves.size();
+    nt += I.k;
+    L->max_atoms = std::max(L->max_atoms, I.n);
+  }
+  if (np > INT32_MAX || nm > INT32_MAX) return fail(DOCK_EINVAL, "dock_load_ligands: batch too large");
+  L->total_pairs = np;
+  std::vector<float4> atoms((size_t)n_atoms), raw((size_t)n_atoms);
+  std::vector<double> cent((size_t)nl * 3);
+  std::vector<uint32_t> pidx((size_t)np);
+  std::vector<float4> pcoef((size_t)np);
+  std::vector<TorInfo> tors((size_t)nt);
+  std::vector<uint8_t> moves((size_t)nm);
+  parallel_for(nl, [&](int l) {
+    const LigInfo &I = L->info[l];
+    for (int i = 0; i < I.n; ++i) {
+      const int a = I.atom_off + i;
+      raw[a] = make_float4(b->x[a], b->y[a], b->z[a], b->q[a]);
+      atoms[a] = make_float4((float)(b->x[a] - H[l].cent[0]), (float)(b->y[a] - H[l].cent[1]),
+                             (float)(b->z[a] - H[l].cent[2]), b->q[a]);
+    }
+    for (int m = 0; m < 3; ++m) cent[(size_t)l * 3 + m] = H[l].cent[m];
+    std::copy(H[l].pair_idx.begin(), H[l].pair_idx.end(), pidx.begin() + I.pair_off);
+    std::copy(H[l].pair_coef.begin(), H[l].pair_coef.end(), pcoef.begin() + I.pair_off);
+    std::copy(H[l].tors.begin(), H[l].tors.end(), tors.begin() + I.tors_off);
+    if (!H[l].tors.empty())
+      std::copy(H[l].moves.begin(), H[l].moves.end(), moves.begin() + H[l].tors[0].move_off);
+  });
+  cudaStream_t s = (cudaStream_t)stream;
+  CU(dalloc(&L->d_info, (size_t)nl));
+  CU(dalloc(&L->d_atoms, (size_t)n_atoms));
+  CU(dalloc(&L->d_atoms_raw, (size_t)n_atoms));
+  CU(dalloc(&L->d_centroid, (size_t)nl * 3));
+  CU(dalloc(&L->d_types, (size_t)n_atoms));
+  CU(dalloc(&L->d_pair_idx, (size_t)np));
+  CU(dalloc(&L->d_pair_coef, (size_t)np));
+  CU(dalloc(&L->d_tors, (size_t)nt));
+  CU(dalloc(&L->d_moves, (size_t)nm));
+  auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
+    return bytes ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  CU(up(L->d_info, L->info.data(), sizeof(LigInfo) * nl));
+  CU(up(L->d_atoms, atoms.data(), sizeof(float4) * n_atoms));
+  CU(up(L->d_atoms_raw, raw.data(), sizeof(float4) * n_atoms));
+  CU(up(L->d_centroid, cent.data(), sizeof(double) * cent.size()));
+  CU(up(L->d_types, b->type, (size_t)n_atoms));
+  CU(up(L->d_pair_idx, pidx.data(), sizeof(uint32_t) * np));
+  CU(up(L->d_pair_coef, pcoef.data(), sizeof(float4) * np));
+  CU(up(L->d_tors, tors.data(), sizeof(TorInfo) * nt));
+  CU(up(L->d_moves, moves.data(), (size_t)nm));
+  CU(cudaStreamSynchronize(s));
+  L->total_atoms = n_atoms;
+  L->total_tors = nt;
+  L->total_moved = nm;
+  L->h2d_bytes = (int64_t)(sizeof(LigInfo) * nl + 2 * sizeof(float4) * n_atoms + sizeof(double) * 3 * nl +
+                           n_atoms + (sizeof(uint32_t) + sizeof(float4)) * np + sizeof(TorInfo) * nt + nm);
+  *out = guard.release();
+  return DOCK_OK;
+}
+
+extern "C" int dock_ligands_info(const dock_ligands *L, int32_t *n_ligands, int64_t *n_atoms,
+                                 int64_t *n_pairs, int64_t *n_torsions, int64_t *n_moved,
+                                 int64_t *h2d_bytes) {
+  if (!L) return fail(DOCK_EINVAL, "dock_ligands_info: NULL ligands");
+  if (n_ligands) *n_ligands = L->n_ligands;
+  if (n_atoms) *n_atoms = L->total_atoms;
+  if (n_pairs) *n_pairs = L->total_pairs;
+  if (n_torsions) *n_torsions = L->total_tors;
+  if (n_moved) *n_moved = L->total_moved;
+  if (h2d_bytes) *h2d_bytes = L->h2d_bytes;
+  return DOCK_OK;
+}
+
+extern "C" void dock_ligands_destroy(dock_ligands *l) { delete l; }
+
+// ---------------------------------------------------------------------------
+// search
+// ---------------------------------------------------------------------------
+struct dock_job {
+  dock_ligands *L = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  int n_ligands = 0, pop = 0, generations = 0;
+  int final_buf = 0;
+  // optional per-launch timing of the search kernels
+  std::vector<cudaEvent_t> ev;
+  ~dock_job() {
+    if (done) cudaEventDestroy(done);
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+static uint64_t prob_threshold(float p) {
+  double t = (double)p * 4294967296.0;
+  if (!(t > 0)) t = 0;
+  if (t > 4294967296.0) t = 4294967296.0;
+  return (uint64_t)t;
+}
+
+// Launch configuration of the search kernel: threads per CTA and the smem
+// capacity in atoms per lane; a ligand of n atoms runs with the smallest
+// L in {1, 2, 4, 8} with L * atoms_per_lane >= n.
+struct LaunchCfg {
+  int threads = 128;
+  int atoms_per_lane = 16;
+};
+
+static int lanes_for(int n, int apl, int forced) {
+  if (forced) return forced;
+  int L = 1;
+  while (L * apl < n && L < 8) L <<= 1;
+  return L;
+}
+
+extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_params *sp, void *stream,
+                          dock_job **out) {
+  if (!P || !L || !sp || !out) return fail(DOCK_EINVAL, "dock_batch: NULL argument");
+  *out = nullptr;
+  if (sp->pop < 2 || sp->pop > DOCK_MAX_POP) return fail(DOCK_EINVAL, "dock_batch: pop %d", sp->pop);
+  if (sp->generations < 1) return fail(DOCK_EINVAL, "dock_batch: generations %d", sp->generations);
+  if (!(sp->p_cross >= 0 && sp->p_cross <= 1 && sp->p_mut >= 0 && sp->p_mut <= 1))
+    return fail(DOCK_EINVAL, "dock_batch: probabilities out of [0, 1]");
+  const int forced = sp->lanes_per_pose;
+  if (forced != 0 && forced != 1 && forced != 2 && forced != 4 && forced != 8)
+    return fail(DOCK_EINVAL, "dock_batch: lanes_per_pose %d", forced);
+  CU(cudaSetDevice(L->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nl = L->n_ligands, pop = sp->pop, gens = sp->generations;
+  LaunchCfg cfg;
+  if (const char *e = getenv("DOCK_THREADS")) cfg.threads = atoi(e);
+  if (const char *e = getenv("DOCK_ATOMS_PER_LANE")) cfg.atoms_per_lane = atoi(e);
+  if (forced) cfg.atoms_per_lane = std::max(cfg.atoms_per_lane, (L->max_atoms + forced - 1) / forced);
+  if (L->max_atoms > 8 * cfg.atoms_per_lane) cfg.atoms_per_lane = (L->max_atoms + 7) / 8;
+  if (cfg.threads < 32 || cfg.threads > 256 || (cfg.threads & (cfg.threads - 1)) || cfg.atoms_per_lane < 1)
+    return fail(DOCK_EINVAL, "dock_batch: launch shape %d threads x %d atoms per lane", cfg.threads,
+                cfg.atoms_per_lane);
+  // keep the coordinate planes within the shared memory an SM offers
+  while (search_smem_bytes(cfg.threads, cfg.atoms_per_lane) > 200 * 1024 && cfg.threads > 32)
+    cfg.threads >>= 1;
+  if (search_smem_bytes(cfg.threads, cfg.atoms_per_lane) > 200 * 1024)
+    return fail(DOCK_EINVAL, "dock_batch: ligands too large for the requested lanes per pose");
+  Workspace &W = L->ws;
+  // genotype offsets and work items (largest first)
+  std::vector<int64_t> goff((size_t)nl);
+  int64_t total_genes = 0;
+  for (int l = 0; l < nl; ++l) {
+    goff[l] = total_genes;
+    total_genes += (int64_t)pop * (7 + L->info[l].k);
+  }
+  struct Keyed {
+    float cost;
+    Item it;
+  };
+  std::vector<Keyed> items;
+  for (int l = 0; l < nl; ++l) {
+    const LigInfo &I = L->info[l];
+    const int Ln = lanes_for(I.n, cfg.atoms_per_lane, forced);
+    const int S = cfg.threads / Ln;
+    const int tiles = (pop + S - 1) / S;
+    const float cost = (float)(I.n_pairs + 6 * I.n + 12 * I.k) / Ln + 60.0f;
+    for (int t = 0; t < tiles; ++t) items.push_back({cost, Item{l, (int16_t)t, (int8_t)Ln, 0}});
+  }
+  std::stable_sort(items.begin(), items.end(),
+                   [](const Keyed &a, const Keyed &b) { return a.cost > b.cost; });
+  std::vector<Item> host_items(items.size());
+  for (size_t i = 0; i < items.size(); ++i) host_items[i] = items[i].it;
+  const size_t n_scores = (size_t)nl * pop;
+  // workspace: grown on demand and reused by later batches on this ligand set
+  if ((size_t)total_genes > W.geno_cap || !W.geno[0]) {
+    dfree(W.geno[0]);
+    dfree(W.geno[1]);
+    W.geno_cap = 0;
+    CU(dalloc(&W.geno[0], (size_t)total_genes));
+    CU(dalloc(&W.geno[1], (size_t)total_genes));
+    W.geno_cap = (size_t)total_genes;
+  }
+  if (n_scores > W.score_cap || !W.score[0]) {
+    dfree(W.score[0]);
+    dfree(W.score[1]);
+    W.score_cap = 0;
+    CU(dalloc(&W.score[0], n_scores));
+    CU(dalloc(&W.score[1], n_scores));
+    W.score_cap = n_scores;
+  }
+  if ((size_t)gens * nl > W.best_cap || !W.best) {
+    dfree(W.best);
+    W.best_cap = 0;
+    CU(dalloc(&W.best, (size_t)gens * nl));
+    W.best_cap = (size_t)gens * nl;
+  }
+  if ((size_t)gens > W.gen_cap || !W.counters) {
+    dfree(W.counters);
+    W.gen_cap = 0;
+    CU(dalloc(&W.counters, (size_t)gens));
+    W.gen_cap = (size_t)gens;
+  }
+  if (host_items.size() > W.item_cap || !W.items) {
+    dfree(W.items);
+    W.item_cap = 0;
+    CU(dalloc(&W.items, host_items.size()));
+    W.item_cap = host_items.size();
+  }
+  if ((size_t)nl > W.lig_cap || !W.geno_off) {
+    dfree(W.geno_off);
+    dfree(W.lig_status);
+    dfree(W.results);
+    W.lig_cap = 0;
+    CU(dalloc(&W.geno_off, (size_t)nl));
+    CU(dalloc(&W.lig_status, (size_t)nl));
+    CU(dalloc(&W.results, (size_t)nl));
+    W.lig_cap = (size_t)nl;
+  }
+  if (!W.status) CU(dalloc(&W.status, 1));
+  if (!W.deadline) CU(dalloc(&W.deadline, 1));
+  CU(cudaMemcpyAsync(W.geno_off, goff.data(), sizeof(int64_t) * nl, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(W.items, host_items.data(), sizeof(Item) * host_items.size(),
+                     cudaMemcpyHostToDevice, s));
+  const int smem = search_smem_bytes(cfg.threads, cfg.atoms_per_lane);
+  int per_sm = 0, n_sm = 0;
+  CU(search_occupancy(cfg.threads, smem, &per_sm));
+  CU(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, L->device));
+  if (per_sm < 1) return fail(DOCK_EINVAL, "dock_batch: launch shape does not fit an SM");
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm,
+                                                                   (int64_t)host_items.size()));
+
+  dock_job *J = new dock_job();
+  std::unique_ptr<dock_job> jguard(J);
+  J->L = L;
+  J->stream = s;
+  J->n_ligands = nl;
+  J->pop = pop;
+  J->generations = gens;
+  J->final_buf = (gens - 1) & 1;
+  CU(cudaEventCreateWithFlags(&J->done, cudaEventDisableTiming));
+  const bool profile = getenv("DOCK_PROFILE_LAUNCHES") != nullptr;
+
+  SearchArgs A;
+  A.ligs = L->d_info;
+  A.atoms = L->d_atoms;
+  A.types = L->d_types;
+  A.pair_idx = L->d_pair_idx;
+  A.pair_coef = L->d_pair_coef;
+  A.tors = L->d_tors;
+  A.moves = L->d_moves;
+  A.geno_off = W.geno_off;
+  A.items = W.items;
+  A.n_items = (int32_t)host_items.size();
+  A.atoms_per_lane = cfg.atoms_per_lane;
+  A.grid = grid_view(P);
+  A.cx = P->center[0];
+  A.cy = P->center[1];
+  A.cz = P->center[2];
+  A.radius = P->radius;
+  A.pop = pop;
+  A.seed = sp->seed;
+  A.thr_cross = prob_threshold(sp->p_cross);
+  A.thr_mut = prob_threshold(sp->p_mut);
+  A.status = W.status;
+  A.lig_status = W.lig_status;
+  A.deadline = sp->timeout_ns ? W.deadline : nullptr;
+
+  Fp64Args F;
+  F.ligs = L->d_info;
+  F.atoms = L->d_atoms_raw;
+  F.types = L->d_types;
+  F.pair_idx = L->d_pair_idx;
+  F.tors = L->d_tors;
+  F.moves = L->d_moves;
+  F.grid = grid_view(P);
+  F.h = P->h;
+  F.cx = P->center[0];
+  F.cy = P->center[1];
+  F.cz = P->center[2];
+  F.params = P->d_params;
+
+  auto enqueue = [&](cudaStream_t q) -> int {
+    CU(cudaMemsetAsync(W.counters, 0, sizeof(uint32_t) * gens, q));
+    CU(cudaMemsetAsync(W.best, 0xFF, sizeof(unsigned long long) * (size_t)gens * nl, q));
+    CU(cudaMemsetAsync(W.status, 0, sizeof(int32_t), q));
+    CU(cudaMemsetAsync(W.lig_status, 0, sizeof(int32_t) * (size_t)nl, q));
+    if (sp->timeout_ns) CU(launch_set_deadline(W.deadline, sp->timeout_ns, q));
+    for (int g = 0; g < gens; ++g) {
+      SearchArgs a = A;
+      a.gen = g;
+      a.counter = W.counters + g;
+      a.geno_prev = W.geno[(g + 1) & 1];
+      a.geno_next = W.geno[g & 1];
+      a.score_prev = W.score[(g + 1) & 1];
+      a.score_next = W.score[g & 1];
+      a.best_prev = g ? W.best + (size_t)(g - 1) * nl : nullptr;
+      a.best_next = W.best + (size_t)g * nl;
+      if (profile) {
+        cudaEvent_t e0, e1;
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+        J->ev.push_back(e0);
+        J->ev.push_back(e1);
+        CU(cudaEventRecord(e0, q));
+        CU(launch_search(a, blocks, cfg.threads, q));
+        CU(cudaEventRecord(e1, q));
+      } else {
+        CU(launch_search(a, blocks, cfg.threads, q));
+      }
+      if (sp->trace_genotypes && total_genes)
+        CU(cudaMemcpyAsync(sp->trace_genotypes + (size_t)g * total_genes, W.geno[g & 1],
+                           sizeof(float) * total_genes, cudaMemcpyDeviceToDevice, q));
+      if (sp->trace_scores && n_scores)
+        CU(cudaMemcpyAsync(sp->trace_scores + (size_t)g * n_scores, W.score[g & 1],
+                           sizeof(float) * n_scores, cudaMemcpyDeviceToDevice, q));
+    }
+    CU(launch_finalize_impl(F, L->d_centroid, nl, pop, W.geno_off, W.geno[(gens - 1) & 1],
+                            W.score[(gens - 1) & 1], W.lig_status, W.status,
+                            (uint64_t)pop * gens, P->ox, P->oy, P->oz, W.results, q));
+    return DOCK_OK;
+  };
+
+  if (sp->use_graph && !profile && s != nullptr) {
+    // graph key: everything the captured launches depend on
+    std::vector<uint8_t> key;
+    auto put = [&](const void *p, size_t n) {
+      const uint8_t *c = (const uint8_t *)p;
+      key.insert(key.end(), c, c + n);
+    };
+    put(&A, sizeof A);
+    put(&F, sizeof F);
+    put(&gens, sizeof gens);
+    put(&blocks, sizeof blocks);
+    put(&cfg, sizeof cfg);
+    put(&sp->trace_genotypes, sizeof(void *));
+    put(&sp->trace_scores, sizeof(void *));
+    const void *bufs[6] = {W.geno[0], W.geno[1], W.score[0], W.score[1], W.best, W.results};
+    put(bufs, sizeof bufs);
+    if (!W.graph || key != W.graph_key) {
+      if (W.graph) {
+        cudaGraphExecDestroy(W.graph);
+        W.graph = nullptr;
+      }
+      cudaGraph_t graph;
+      CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      int est = enqueue(s);
+      cudaError_t ce = cudaStreamEndCapture(s, &graph);
+      if (est != DOCK_OK) {
+        if (ce == cudaSuccess) cudaGraphDestroy(graph);
+        return est;
+      }
+      CU(ce);
+      cudaError_t ie = cudaGraphInstantiate(&W.graph, graph, 0);
+      cudaGraphDestroy(graph);
+      CU(ie);
+      W.graph_key = key;
+    }
+    CU(cudaGraphLaunch(W.graph, s));
+  } else {
+    int est = enqueue(s);
+    if (est != DOCK_OK) return est;
+  }
+  CU(cudaEventRecord(J->done, s));
+  *out = jguard.release();
+  return DOCK_OK;
+}
+
+extern "C" int dock_results(dock_job *J, dock_result *out, int32_t cap, uint64_t timeout_ns) {
+  if (!J) return fail(DOCK_EINVAL, "dock_results: NULL job");
+  if (cap < 0 || (cap > 0 && !out)) return fail(DOCK_EINVAL, "dock_results: bad output buffer");
+  CU(cudaSetDevice(J->L->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t q = cudaEventQuery(J->done);
+    if (q == cudaSuccess) break;
+    if (q != cudaErrorNotReady) return fail(DOCK_ECUDA, "dock_results: %s", cudaGetErrorString(q));
+    const uint64_t el = (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                            std::chrono::steady_clock::now() - t0).count();
+    if (timeout_ns && el > timeout_ns) return fail(DOCK_ETIMEOUT, "dock_results: job still running");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+  int32_t status = 0;
+  CU(cudaMemcpy(&status, J->L->ws.status, sizeof status, cudaMemcpyDeviceToHost));
+  const int n = std::min(cap, J->n_ligands);
+  if (n > 0) CU(cudaMemcpy(out, J->L->ws.results, sizeof(dock_result) * n, cudaMemcpyDeviceToHost));
+  if (status == DOCK_ETIMEOUT) return fail(DOCK_ETIMEOUT, "dock_results: device deadline exceeded");
+  if (status != 0) return fail(DOCK_EDEVICE, "dock_results: device status %d", status);
+  return DOCK_OK;
+}
+
+extern "C" int dock_job_population(const dock_job *J, const float **genos, const float **scores) {
+  if (!J) return fail(DOCK_EINVAL, "dock_job_population: NULL job");
+  if (genos) *genos = J->L->ws.geno[J->final_buf];
+  if (scores) *scores = J->L->ws.score[J->final_buf];
+  return DOCK_OK;
+}
+
+// Sum of the device times of the search-kernel launches of a job enqueued with
+// DOCK_PROFILE_LAUNCHES set in the environment (waits for the job).
+extern "C" int dock_job_kernel_time(const dock_job *J, double *ms_total, int32_t *launches) {
+  if (!J) return fail(DOCK_EINVAL, "dock_job_kernel_time: NULL job");
+  CU(cudaEventSynchronize(J->done));
+  double tot = 0;
+  for (size_t i = 0; i + 1 < J->ev.size(); i += 2) {
+    float ms = 0;
+    CU(cudaEventElapsedTime(&ms, J->ev[i], J->ev[i + 1]));
+    tot += ms;
+  }
+  if (ms_total) *ms_total = tot;
+  if (launches) *launches = (int32_t)(J->ev.size() / 2);
+  return DOCK_OK;
+}
+
+extern "C" void dock_job_destroy(dock_job *J) { delete J; }
+
+// ---------------------------------------------------------------------------
+// scoring of given poses
+// ---------------------------------------------------------------------------
+extern "C" int dock_score(dock_pocket *P, dock_ligands *L, const int32_t *pose_ligand,
+                          const float *genos, int64_t n_poses, float *scores, double *scores64,
+                          float *coords, int32_t fp64, void *stream) {
+  if (!P || !L) return fail(DOCK_EINVAL, "dock_score: NULL pocket or ligands");
+  if (n_poses < 0) return fail(DOCK_EINVAL, "dock_score: n_poses < 0");
+  if (n_poses == 0) return DOCK_OK;
+  if (!pose_ligand || !genos || (fp64 ? !scores64 : !scores))
+    return fail(DOCK_EINVAL, "dock_score: NULL device buffer");
+  CU(cudaSetDevice(L->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  if (fp64) {
+    Fp64Args F;
+    F.ligs = L->d_info;
+    F.atoms = L->d_atoms_raw;
+    F.types = L->d_types;
+    F.pair_idx = L->d_pair_idx;
+    F.tors = L->d_tors;
+    F.moves = L->d_moves;
+    F.grid = grid_view(P);
+    F.h = P->h;
+    F.cx = P->center[0];
+    F.cy = P->center[1];
+    F.cz = P->center[2];
+    F.params = P->d_params;
+    CU(launch_score_fp64_impl(F, L->d_centroid, P->ox, P->oy, P->oz, pose_ligand, L->n_ligands, genos,
+                              n_poses, scores64, s));
+    return DOCK_OK;
+  }
+  ScoreArgs A;
+  A.ligs = L->d_info;
+  A.atoms = L->d_atoms;
+  A.types = L->d_types;
+  A.pair_idx = L->d_pair_idx;
+  A.pair_coef = L->d_pair_coef;
+  A.tors = L->d_tors;
+  A.moves = L->d_moves;
+  A.grid = grid_view(P);
+  A.cx = P->center[0];
+  A.cy = P->center[1];
+  A.cz = P->center[2];
+  A.pose_ligand = pose_ligand;
+  A.n_ligands = L->n_ligands;
+  A.genos = genos;
+  A.n_poses = n_poses;
+  A.scores = scores;
+  A.coords = coords;
+  A.lanes = 8;
+  A.atoms_per_lane = DOCK_MAX_ATOMS / 8;
+  CU(launch_score(A, s));
+  return DOCK_OK;
+}

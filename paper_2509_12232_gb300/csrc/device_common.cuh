@@ -1,0 +1,292 @@
+// Device building blocks of the docking hot path: counter-based RNG, GA
+// operators, pair energy, grid lookup and compensated sums.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dock_internal.h"
+
+namespace dk {
+
+// ---- AutoDock4 free-energy constants (the scoring form the paper's muDock
+// ---- is "functionally equivalent" to, Section V) ----------------------------
+constexpr float kWVdw = 0.1662f, kWHb = 0.1209f, kWElec = 0.1406f, kWSol = 0.1322f;
+constexpr double kCoulomb = 332.06363, kQasp = 0.01097, kSigma = 3.6;
+constexpr double kDielA = -8.5525, kDielEps0 = 78.4, kDielK = 7.7839, kDielLambda = 0.003627;
+constexpr double kDielB = kDielEps0 - kDielA;
+// Readings of what the paper leaves open.
+constexpr float kCutoff2 = 64.0f;   // (8 A)^2 non-bonded cutoff
+constexpr float kRmin2 = 0.25f;     // distances floored at 0.5 A
+constexpr double kEmax = 1.0e5;     // cap on a pair's raw 12-6 / 12-10 value and on M_t
+constexpr float kEout = 1000.0f;    // energy of a ligand atom outside the grid box
+
+// ---------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11). Counter (slot, individual, generation,
+// ligand id), key (seed, 0). Word 2i / 2i+1 = low / high half of output i.
+// ---------------------------------------------------------------------------
+struct Words8 {
+  uint32_t w[8];
+};
+
+__device__ __forceinline__ Words8 rng_words(uint64_t seed, uint64_t lig, uint32_t gen,
+                                            uint32_t ind, uint32_t slot) {
+  uint64_t c0 = slot, c1 = ind, c2 = gen, c3 = lig, k0 = seed, k1 = 0;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
+    uint64_t hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
+    uint64_t hi1 = __umul64hi(m1, c2), lo1 = m1 * c2;
+    uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B97F4A7C15ULL;
+    k1 += 0xBB67AE8584CAA73BULL;
+  }
+  Words8 o;
+  o.w[0] = (uint32_t)c0; o.w[1] = (uint32_t)(c0 >> 32);
+  o.w[2] = (uint32_t)c1; o.w[3] = (uint32_t)(c1 >> 32);
+  o.w[4] = (uint32_t)c2; o.w[5] = (uint32_t)(c2 >> 32);
+  o.w[6] = (uint32_t)c3; o.w[7] = (uint32_t)(c3 >> 32);
+  return o;
+}
+
+// Irwin-Hall normal from the first 12 words of slots (s, s+1):
+// (sum of 12 top-24-bit words - 6 * 2^24) * 2^-24, converted round-to-nearest.
+__device__ __forceinline__ float rng_normal(uint64_t seed, uint64_t lig, uint32_t gen,
+                                            uint32_t ind, uint32_t s) {
+  Words8 a = rng_words(seed, lig, gen, ind, s);
+  Words8 b = rng_words(seed, lig, gen, ind, s + 1);
+  int64_t S = 0;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) S += a.w[i] >> 8;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) S += b.w[i] >> 8;
+  float z = __ll2float_rn(S - 6LL * 16777216LL);
+  return __fmul_rn(z, 0x1p-24f);
+}
+
+__device__ __forceinline__ float u24(uint32_t w) {
+  return __fmul_rn(__uint2float_rn(w >> 8), 0x1p-24f);
+}
+
+__device__ __forceinline__ int pick(uint32_t w, int n) {
+  return (int)(((uint64_t)w * (uint64_t)n) >> 32);
+}
+
+// Order-preserving key of an FP32 score: NaN counts as +inf, -0 as +0.
+__device__ __forceinline__ uint32_t score_key(float s) {
+  if (s != s) s = __int_as_float(0x7f800000);
+  if (s == 0.0f) s = 0.0f;
+  uint32_t u = __float_as_uint(s);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ bool better(const float *s, int a, int b) {
+  uint32_t ka = score_key(s[a]), kb = score_key(s[b]);
+  return ka < kb || (ka == kb && a < b);
+}
+
+constexpr float kPiF = 3.14159265358979323846f;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+
+__device__ __forceinline__ void quat_normalize(float &w, float &x, float &y, float &z) {
+  float n2 = __fmul_rn(w, w);
+  n2 = __fadd_rn(n2, __fmul_rn(x, x));
+  n2 = __fadd_rn(n2, __fmul_rn(y, y));
+  n2 = __fadd_rn(n2, __fmul_rn(z, z));
+  float n = __fsqrt_rn(n2);
+  if (!(n > 0.0f)) {
+    w = 1.0f; x = y = z = 0.0f;
+    return;
+  }
+  w = __fdiv_rn(w, n); x = __fdiv_rn(x, n); y = __fdiv_rn(y, n); z = __fdiv_rn(z, n);
+}
+
+// Generation 0 genotype of individual ind (translation uniform in
+// [-R/2, R/2)^3 from slot 0, quaternion of 4 normals from slots 1..8,
+// torsions uniform in [-pi, pi) from slots 9, 10).
+__device__ __forceinline__ void ga_init(float (&g)[DOCK_MAX_GENES], int k, float radius,
+                                        uint64_t seed, uint64_t lig, uint32_t ind) {
+  Words8 w = rng_words(seed, lig, 0, ind, 0);
+  float half = __fmul_rn(0.5f, radius);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) g[m] = __fadd_rn(__fmul_rn(u24(w.w[m]), radius), -half);
+  float qv[4];
+#pragma unroll 1
+  for (int m = 0; m < 4; ++m) {
+    float z = rng_normal(seed, lig, 0, ind, 1 + 2 * m);
+#pragma unroll
+    for (int mm = 0; mm < 4; ++mm)
+      if (mm == m) qv[mm] = z;
+  }
+  quat_normalize(qv[0], qv[1], qv[2], qv[3]);
+  g[3] = qv[0]; g[4] = qv[1]; g[5] = qv[2]; g[6] = qv[3];
+  Words8 t0 = rng_words(seed, lig, 0, ind, 9);
+  Words8 t1 = t0;
+  if (k > 8) t1 = rng_words(seed, lig, 0, ind, 10);
+#pragma unroll
+  for (int j = 0; j < DOCK_MAX_TORSIONS; ++j) {
+    float v = 0.0f;
+    if (j < k) {
+      uint32_t ww = j < 8 ? t0.w[j] : t1.w[j - 8];
+      v = __fadd_rn(__fmul_rn(u24(ww), kTwoPiF), -kPiF);
+    }
+    g[7 + j] = v;
+  }
+}
+
+__device__ __forceinline__ int gene_block(int g) { return g < 3 ? g : (g < 7 ? 3 : g - 3); }
+
+// One GA step for individual ind >= 1 of a ligand with k torsions: binary
+// tournaments (slot 0 words 0-3), two-point block crossover (words 4-6),
+// per-gene mutation decisions (slots 1..3) and Irwin-Hall normal steps
+// (slots 4+2g, 5+2g), torsion wrap, quaternion renormalisation.
+__device__ __forceinline__ void ga_child(float (&g)[DOCK_MAX_GENES], int k, int P,
+                                         const float *prev, const float *score, uint64_t thr_c,
+                                         uint64_t thr_m, uint64_t seed, uint64_t lig,
+                                         uint32_t gen, uint32_t ind) {
+  const int G = 7 + k, B = 4 + k;
+  Words8 w = rng_words(seed, lig, gen, ind, 0);
+  int a1 = pick(w.w[0], P), a2 = pick(w.w[1], P), b1 = pick(w.w[2], P), b2 = pick(w.w[3], P);
+  int pa = better(score, a1, a2) ? a1 : a2;
+  int pb = better(score, b1, b2) ? b1 : b2;
+  int lo = 0, hi = 0;
+  if ((uint64_t)w.w[4] < thr_c) {
+    int c1 = pick(w.w[5], B + 1), c2 = pick(w.w[6], B + 1);
+    lo = min(c1, c2);
+    hi = max(c1, c2);
+  }
+  const float *A = prev + (int64_t)pa * G, *Bp = prev + (int64_t)pb * G;
+#pragma unroll
+  for (int e = 0; e < DOCK_MAX_GENES; ++e) {
+    float v = 0.0f;
+    if (e < G) {
+      int blk = gene_block(e);
+      v = (blk >= lo && blk < hi) ? __ldg(Bp + e) : __ldg(A + e);
+    }
+    g[e] = v;
+  }
+  Words8 m0 = rng_words(seed, lig, gen, ind, 1);
+  Words8 m1 = m0, m2 = m0;
+  if (G > 8) m1 = rng_words(seed, lig, gen, ind, 2);
+  if (G > 16) m2 = rng_words(seed, lig, gen, ind, 3);
+  uint32_t mask = 0;
+#pragma unroll
+  for (int e = 0; e < DOCK_MAX_GENES; ++e) {
+    uint32_t ww = e < 8 ? m0.w[e] : (e < 16 ? m1.w[e - 8] : m2.w[e - 16]);
+    if (e < G && (uint64_t)ww < thr_m) mask |= 1u << e;
+  }
+  bool qmut = false;
+  // mutations are rare: draw each normal in a rolled loop, then apply it
+#pragma unroll 1
+  while (mask) {
+    const int e = __ffs(mask) - 1;
+    mask &= mask - 1;
+    float z = rng_normal(seed, lig, gen, ind, 4 + 2 * e);
+    float sigma = e < 3 ? 1.0f : (e < 7 ? 0.1f : 0.5f);
+    float d = __fmul_rn(sigma, z);
+    qmut |= (e >= 3 && e < 7);
+#pragma unroll
+    for (int ee = 0; ee < DOCK_MAX_GENES; ++ee) {
+      if (ee == e) {
+        float v = __fadd_rn(g[ee], d);
+        if (ee >= 7) {
+          if (v > kPiF) v = __fadd_rn(v, -kTwoPiF);
+          else if (v < -kPiF) v = __fadd_rn(v, kTwoPiF);
+        }
+        g[ee] = v;
+      }
+    }
+  }
+  if (qmut) quat_normalize(g[3], g[4], g[5], g[6]);
+}
+
+// ---------------------------------------------------------------------------
+// Compensated sums
+// ---------------------------------------------------------------------------
+struct Kahan {
+  float s = 0.0f, c = 0.0f;  // true sum ~ s - c
+  __device__ __forceinline__ void add(float x) {
+    float y = __fsub_rn(x, c);
+    float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ float value() const { return __fsub_rn(s, c); }
+};
+
+// Knuth TwoSum: a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float aa = __fsub_rn(s, bb);
+  e = __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
+}
+
+// ---------------------------------------------------------------------------
+// Pair energy (FP32). r2: squared distance; coef {c12, cx, qq, ds} with the
+// weights folded in; hb selects the 12-10 form (x = 10) over 12-6 (x = 6).
+// Zero at r >= 8 A; r floored at 0.5 A; the dispersion part is capped at
+// w * EMAX (cap before weighting).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float pair_energy(float r2, float4 coef, bool hb) {
+  const float lb = (float)(kDielLambda * kDielB);
+  const float inv_2s2 = (float)(1.0 / (2.0 * kSigma * kSigma));
+  const float dA = (float)kDielA, dB = (float)kDielB, dK = (float)kDielK;
+  const float log2e = 1.4426950408889634f;
+  float r2c = fmaxf(r2, kRmin2);
+  float inv_r = rsqrtf(r2c);
+  float inv_r2 = inv_r * inv_r;
+  float r = r2c * inv_r;
+  float inv_r6 = inv_r2 * inv_r2 * inv_r2;
+  float inv_r12 = inv_r6 * inv_r6;
+  float inv_rx = hb ? inv_r6 * (inv_r2 * inv_r2) : inv_r6;
+  float cap = hb ? (float)(kWHb * kEmax) : (float)(kWVdw * kEmax);
+  float disp = fminf(coef.x * inv_r12 - coef.y * inv_rx, cap);
+  float ex = exp2f(-lb * log2e * r);
+  float onek = 1.0f + dK * ex;
+  float elec = __fdividef(coef.z * onek, (dA * onek + dB) * r);
+  float des = coef.w * exp2f(-r2c * (inv_2s2 * log2e));
+  float e = disp + elec + des;
+  return r2 < kCutoff2 ? e : 0.0f;
+}
+
+// Trilinear interpolation of M_t + q E + |q| D at (x, y, z); returns false if
+// the point is outside the grid box (faces included as inside).
+__device__ __forceinline__ bool grid_energy(const GridView &G, int t, float q, float x, float y,
+                                            float z, float &e) {
+  float ux = (x - G.ox) * G.inv_h, uy = (y - G.oy) * G.inv_h, uz = (z - G.oz) * G.inv_h;
+  float nm1 = (float)(G.n - 1);
+  if (!(ux >= 0.0f && ux <= nm1 && uy >= 0.0f && uy <= nm1 && uz >= 0.0f && uz <= nm1))
+    return false;
+  int ix = min((int)ux, G.n - 2), iy = min((int)uy, G.n - 2), iz = min((int)uz, G.n - 2);
+  float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
+  const float aq = fabsf(q);
+  const float4 *m = G.maps + (((int64_t)t * G.n + iz) * G.n + iy) * G.n + ix;
+  const int sy = G.n, sz = G.n * G.n;
+  float v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    float4 a = __ldg(m + ((c >> 2) & 1) * sz + ((c >> 1) & 1) * sy + (c & 1));
+    v[c] = a.x + q * a.y + aq * a.z;
+  }
+  float x00 = v[0] + fx * (v[1] - v[0]);
+  float x10 = v[2] + fx * (v[3] - v[2]);
+  float x01 = v[4] + fx * (v[5] - v[4]);
+  float x11 = v[6] + fx * (v[7] - v[6]);
+  float y0 = x00 + fy * (x10 - x00);
+  float y1 = x01 + fy * (x11 - x01);
+  e = y0 + fz * (y1 - y0);
+  return true;
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+}  // namespace dk

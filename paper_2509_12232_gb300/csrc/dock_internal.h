@@ -1,0 +1,138 @@
+// Internal types shared by the library's translation units (host + device).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dock.h"
+
+namespace dk {
+
+// Per-ligand record, pop-independent (built by dock_load_ligands).
+struct LigInfo {
+  int32_t atom_off;   // first atom in the atom arrays
+  int32_t n;          // atoms
+  int32_t k;          // torsions
+  int32_t pair_off;   // first included intra pair
+  int32_t n_pairs;
+  int32_t tors_off;   // first torsion record
+  uint64_t ligand_id;
+};
+
+// One rotatable bond: rotate atoms moves[move_off .. move_off + n_move) about
+// the axis parent(b) = a -> b.
+struct TorInfo {
+  int32_t move_off;
+  int16_t n_move;
+  uint8_t a, b;
+};
+
+// A work item of the search kernel: poses [first, first + count) of ligand lig,
+// run with `lanes` lanes per pose.
+struct Item {
+  int32_t lig;
+  int16_t first_div;  // first pose / slots (tile index)
+  int8_t lanes;       // lanes per pose: 1, 2, 4, 8
+  int8_t pad;
+};
+
+// Pair record: bits 0-7 atom i, 8-15 atom j, 16 H-bond (12-10) flag.
+// Coefficients (weights folded in): c12, cx (x = 6 or 10), qq (W_elec *
+// 332.06363 * q_i q_j), ds (W_sol * (S_i V_j + S_j V_i)).
+
+struct GridView {
+  const float4 *maps;   // [n_types][n][n][n] {M_t, E, D, 0}
+  int32_t n;            // nodes per axis
+  float ox, oy, oz;     // origin
+  float inv_h;
+  int32_t n_types;
+};
+
+struct SearchArgs {
+  // ligands
+  const LigInfo *ligs;
+  const float4 *atoms;      // {x, y, z, q}, centred on the ligand centroid
+  const uint8_t *types;
+  const uint32_t *pair_idx;
+  const float4 *pair_coef;
+  const TorInfo *tors;
+  const uint8_t *moves;
+  const int64_t *geno_off;  // [n_ligands]
+  // work queue
+  const Item *items;
+  int32_t n_items;
+  uint32_t *counter;        // this generation's queue counter (starts at 0)
+  int32_t atoms_per_lane;   // smem capacity: lanes * atoms_per_lane >= n
+  // pocket
+  GridView grid;
+  float cx, cy, cz;         // pocket centre
+  float radius;
+  // GA
+  int32_t pop;
+  int32_t gen;
+  uint64_t seed;
+  uint64_t thr_cross, thr_mut;
+  const float *geno_prev;
+  float *geno_next;
+  const float *score_prev;
+  float *score_next;
+  const unsigned long long *best_prev;  // [n_ligands] best key of gen-1
+  unsigned long long *best_next;        // [n_ligands] best key of gen (init ~0)
+  // control
+  int32_t *status;          // device status word
+  int32_t *lig_status;      // [n_ligands]
+  const uint64_t *deadline;  // device globaltimer deadline, NULL = none
+};
+
+struct ScoreArgs {
+  const LigInfo *ligs;
+  const float4 *atoms;
+  const uint8_t *types;
+  const uint32_t *pair_idx;
+  const float4 *pair_coef;
+  const TorInfo *tors;
+  const uint8_t *moves;
+  GridView grid;
+  float cx, cy, cz;
+  const int32_t *pose_ligand;
+  int32_t n_ligands;        // pose_ligand entries outside [0, n_ligands) score NaN
+  const float *genos;       // [n_poses][DOCK_MAX_GENES]
+  int64_t n_poses;
+  float *scores;
+  float *coords;            // optional
+  int32_t lanes;            // lanes per pose
+  int32_t atoms_per_lane;
+};
+
+// FP64 rescoring / scoring inputs (type table in FP32 as given).
+struct Fp64Args {
+  const LigInfo *ligs;
+  const float4 *atoms;             // raw input coordinates + charge
+  const uint8_t *types;
+  const uint32_t *pair_idx;
+  const TorInfo *tors;
+  const uint8_t *moves;
+  GridView grid;
+  double h;                        // grid spacing (exact)
+  double cx, cy, cz;
+  const dock_type_params *params;  // device [n_types]
+};
+
+// Launchers (defined in the .cu files).
+cudaError_t launch_grid_build_impl(const float4 *prot, const uint8_t *ptype, int n_prot,
+                                   const dock_type_params *params_dev, int n_types, int n,
+                                   double ox, double oy, double oz, double h, float4 *maps,
+                                   cudaStream_t s);
+cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStream_t s);
+cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
+cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int n_ligands, int pop,
+                                 const int64_t *geno_off, const float *genos, const float *scores,
+                                 const int32_t *lig_status, const int32_t *status,
+                                 uint64_t exact_evals, double ox, double oy, double oz,
+                                 dock_result *out, cudaStream_t s);
+cudaError_t launch_score_fp64_impl(const Fp64Args &f, const double *centroids, double ox, double oy,
+                                   double oz, const int32_t *pose_ligand, int n_ligands,
+                                   const float *genos, int64_t n_poses, double *out, cudaStream_t s);
+int search_smem_bytes(int threads, int atoms_per_lane);
+
+}  // namespace dk

@@ -1,0 +1,299 @@
+"""Python binding of libdock.so (include/dock.h): argument marshalling only.
+
+Every step of the docking path runs in the library's CUDA kernels; this
+module converts numpy arrays and torch tensors to the C structs and pointers
+the ABI takes. It raises if the compiled library is missing: there is no
+Python or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdock.so")
+
+DOCK_OK, DOCK_EINVAL, DOCK_ENOMEM, DOCK_ECUDA, DOCK_ETIMEOUT, DOCK_EDEVICE, DOCK_ENOTIMPL = \
+    0, -1, -2, -3, -4, -5, -6
+DOCK_MAX_ATOMS, DOCK_MAX_TORSIONS, DOCK_MAX_GENES, DOCK_MAX_TYPES, DOCK_N_BEST = 128, 16, 23, 16, 8
+
+P_f = C.POINTER(C.c_float)
+P_u8 = C.POINTER(C.c_uint8)
+P_i16 = C.POINTER(C.c_int16)
+P_i32 = C.POINTER(C.c_int32)
+P_u64 = C.POINTER(C.c_uint64)
+
+
+class DockError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("dock status %d: %s" % (status, msg))
+        self.status = status
+
+
+class dock_type_params(C.Structure):
+    _fields_ = [("Rii", C.c_float), ("eps", C.c_float), ("vol", C.c_float), ("solpar", C.c_float),
+                ("hb_R", C.c_float), ("hb_eps", C.c_float), ("hb_role", C.c_int32)]
+
+
+class dock_pocket_desc(C.Structure):
+    _fields_ = [("n_atoms", C.c_int32), ("x", P_f), ("y", P_f), ("z", P_f), ("q", P_f),
+                ("type", P_u8), ("center", C.c_float * 3), ("radius", C.c_float),
+                ("spacing", C.c_float), ("n_types", C.c_int32),
+                ("params", C.POINTER(dock_type_params))]
+
+
+class dock_ligand_batch(C.Structure):
+    _fields_ = [("n_ligands", C.c_int32), ("atom_off", P_i32), ("x", P_f), ("y", P_f), ("z", P_f),
+                ("q", P_f), ("type", P_u8), ("parent", P_i16), ("tors_off", P_i32),
+                ("tors_b", P_i16), ("ligand_id", P_u64)]
+
+
+class dock_search_params(C.Structure):
+    _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("p_cross", C.c_float),
+                ("p_mut", C.c_float), ("seed", C.c_uint64), ("lanes_per_pose", C.c_int32),
+                ("use_graph", C.c_int32), ("timeout_ns", C.c_uint64),
+                ("trace_genotypes", C.c_void_p), ("trace_scores", C.c_void_p)]
+
+
+class dock_result(C.Structure):
+    _fields_ = [("ligand_id", C.c_uint64), ("n_genes", C.c_int32), ("status", C.c_int32),
+                ("best_fp32", C.c_float * DOCK_N_BEST), ("best_fp64", C.c_double * DOCK_N_BEST),
+                ("best_index", C.c_int32 * DOCK_N_BEST),
+                ("genotype", (C.c_float * DOCK_MAX_GENES) * DOCK_N_BEST),
+                ("exact_evals", C.c_uint64), ("surrogate_evals", C.c_uint64)]
+
+
+RESULT_DTYPE = np.dtype([("ligand_id", np.uint64), ("n_genes", np.int32), ("status", np.int32),
+                         ("best_fp32", np.float32, DOCK_N_BEST),
+                         ("best_fp64", np.float64, DOCK_N_BEST),
+                         ("best_index", np.int32, DOCK_N_BEST),
+                         ("genotype", np.float32, (DOCK_N_BEST, DOCK_MAX_GENES)),
+                         ("exact_evals", np.uint64), ("surrogate_evals", np.uint64)], align=True)
+
+_lib = None
+
+
+def lib():
+    """Load libdock.so (built by paper_2509_12232_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libdock.so is not built: run paper_2509_12232_gb300.build.build() "
+                               "(nvcc, sm_103a); there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        L.dock_last_error.restype = C.c_char_p
+        L.dock_version.restype = C.c_char_p
+        L.dock_create_pocket.argtypes = [C.POINTER(dock_pocket_desc), vp, C.POINTER(vp)]
+        L.dock_pocket_destroy.argtypes = [vp]
+        L.dock_pocket_destroy.restype = None
+        L.dock_pocket_grid.argtypes = [vp, P_i32, P_f, C.POINTER(vp)]
+        L.dock_load_ligands.argtypes = [vp, C.POINTER(dock_ligand_batch), vp, C.POINTER(vp)]
+        L.dock_ligands_destroy.argtypes = [vp]
+        L.dock_ligands_destroy.restype = None
+        L.dock_batch.argtypes = [vp, vp, C.POINTER(dock_search_params), vp, C.POINTER(vp)]
+        L.dock_results.argtypes = [vp, vp, C.c_int32, C.c_uint64]
+        L.dock_job_population.argtypes = [vp, C.POINTER(vp), C.POINTER(vp)]
+        L.dock_job_kernel_time.argtypes = [vp, C.POINTER(C.c_double), P_i32]
+        L.dock_job_destroy.argtypes = [vp]
+        L.dock_job_destroy.restype = None
+        L.dock_score.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp, vp, C.c_int32, vp]
+        P_i64 = C.POINTER(C.c_int64)
+        L.dock_ligands_info.argtypes = [vp, P_i32, P_i64, P_i64, P_i64, P_i64, P_i64]
+        for name in ("dock_create_pocket", "dock_pocket_grid", "dock_load_ligands", "dock_batch",
+                     "dock_results", "dock_job_population", "dock_job_kernel_time", "dock_score",
+                     "dock_ligands_info"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != DOCK_OK:
+        raise DockError(status, lib().dock_last_error().decode())
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _dptr(t):
+    """Device pointer of a torch tensor (or an int), None for None."""
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return C.c_void_p(t.data_ptr())
+    return C.c_void_p(int(t))
+
+
+class Pocket:
+    """Owns a dock_pocket handle."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def grid(self):
+        n = C.c_int32()
+        o = (C.c_float * 3)()
+        maps = C.c_void_p()
+        check(lib().dock_pocket_grid(self.handle, C.byref(n), o, C.byref(maps)))
+        return n.value, np.array(list(o), np.float32), maps.value
+
+    def close(self):
+        if self.handle:
+            lib().dock_pocket_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ligands:
+    def __init__(self, handle, n_ligands, n_tors):
+        self.handle = handle
+        self.n_ligands = n_ligands
+        self.n_tors = n_tors
+
+    def geno_offsets(self, pop: int) -> np.ndarray:
+        g = (7 + self.n_tors.astype(np.int64)) * pop
+        return np.concatenate([[0], np.cumsum(g)]).astype(np.int64)
+
+    def close(self):
+        if self.handle:
+            lib().dock_ligands_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Job:
+    def __init__(self, handle, n_ligands, keep=()):
+        self.handle = handle
+        self.n_ligands = n_ligands
+        self._keep = keep          # the pocket and ligands must outlive the job
+
+    def close(self):
+        if self.handle:
+            lib().dock_job_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def type_params_array(table: dict):
+    n = len(table["Rii"])
+    arr = (dock_type_params * n)()
+    for t in range(n):
+        arr[t] = dock_type_params(float(table["Rii"][t]), float(table["eps"][t]),
+                                  float(table["vol"][t]), float(table["solpar"][t]),
+                                  float(table["hb_R"][t]), float(table["hb_eps"][t]),
+                                  int(table["hb_role"][t]))
+    return arr
+
+
+def dock_create_pocket(x, y, z, q, type, center, radius, spacing, params_table, stream=None) -> Pocket:
+    keep = dict(x=_c(x, np.float32), y=_c(y, np.float32), z=_c(z, np.float32), q=_c(q, np.float32),
+                type=_c(type, np.uint8))
+    params = type_params_array(params_table)
+    d = dock_pocket_desc(int(keep["x"].shape[0]), _p(keep["x"], P_f), _p(keep["y"], P_f),
+                         _p(keep["z"], P_f), _p(keep["q"], P_f), _p(keep["type"], P_u8),
+                         (C.c_float * 3)(*[float(c) for c in center]), float(radius), float(spacing),
+                         len(params), params)
+    h = C.c_void_p()
+    check(lib().dock_create_pocket(C.byref(d), _stream(stream), C.byref(h)))
+    return Pocket(h, keep)
+
+
+def dock_load_ligands(pocket: Pocket, atom_off, x, y, z, q, type, parent, tors_off, tors_b, ligand_id,
+                      stream=None) -> Ligands:
+    a = dict(atom_off=_c(atom_off, np.int32), x=_c(x, np.float32), y=_c(y, np.float32),
+             z=_c(z, np.float32), q=_c(q, np.float32), type=_c(type, np.uint8),
+             parent=_c(parent, np.int16), tors_off=_c(tors_off, np.int32),
+             tors_b=_c(tors_b, np.int16), ligand_id=_c(ligand_id, np.uint64))
+    nl = int(a["atom_off"].shape[0] - 1)
+    b = dock_ligand_batch(nl, _p(a["atom_off"], P_i32), _p(a["x"], P_f), _p(a["y"], P_f),
+                          _p(a["z"], P_f), _p(a["q"], P_f), _p(a["type"], P_u8),
+                          _p(a["parent"], P_i16), _p(a["tors_off"], P_i32), _p(a["tors_b"], P_i16),
+                          _p(a["ligand_id"], P_u64))
+    h = C.c_void_p()
+    check(lib().dock_load_ligands(pocket.handle, C.byref(b), _stream(stream), C.byref(h)))
+    return Ligands(h, nl, np.diff(a["tors_off"]).astype(np.int64))
+
+
+def dock_ligands_info(ligands: Ligands) -> dict:
+    nl = C.c_int32()
+    v = [C.c_int64() for _ in range(5)]
+    check(lib().dock_ligands_info(ligands.handle, C.byref(nl), *[C.byref(x) for x in v]))
+    return dict(n_ligands=nl.value, n_atoms=v[0].value, n_pairs=v[1].value, n_torsions=v[2].value,
+                n_moved=v[3].value, h2d_bytes=v[4].value)
+
+
+def dock_batch(pocket: Pocket, ligands: Ligands, pop: int, generations: int, p_cross=0.8,
+               p_mut=0.02, seed=0, lanes_per_pose=0, use_graph=1, timeout_ns=0,
+               trace_genotypes=None, trace_scores=None, stream=None) -> Job:
+    sp = dock_search_params(pop, generations, p_cross, p_mut, seed, lanes_per_pose, use_graph,
+                            timeout_ns, _dptr(trace_genotypes), _dptr(trace_scores))
+    h = C.c_void_p()
+    check(lib().dock_batch(pocket.handle, ligands.handle, C.byref(sp), _stream(stream), C.byref(h)))
+    return Job(h, ligands.n_ligands, keep=(pocket, ligands))
+
+
+def dock_results(job: Job, cap: int | None = None, timeout_ns: int = 0) -> np.ndarray:
+    cap = job.n_ligands if cap is None else int(cap)
+    out = np.zeros(cap, RESULT_DTYPE)
+    assert RESULT_DTYPE.itemsize == C.sizeof(dock_result)
+    check(lib().dock_results(job.handle, out.ctypes.data_as(C.c_void_p), cap, timeout_ns))
+    return out
+
+
+def dock_job_population(job: Job):
+    g, s = C.c_void_p(), C.c_void_p()
+    check(lib().dock_job_population(job.handle, C.byref(g), C.byref(s)))
+    return g.value, s.value
+
+
+def dock_job_kernel_time(job: Job):
+    ms = C.c_double()
+    n = C.c_int32()
+    check(lib().dock_job_kernel_time(job.handle, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def dock_score(pocket: Pocket, ligands: Ligands, pose_ligand, genotypes, scores=None, scores64=None,
+               coords=None, fp64=False, stream=None):
+    """pose_ligand, genotypes ([n, 23] float32), scores / scores64 / coords:
+    device tensors (torch) or device pointers; asynchronous on stream."""
+    n = int(pose_ligand.shape[0]) if hasattr(pose_ligand, "shape") else int(genotypes.shape[0])
+    check(lib().dock_score(pocket.handle, ligands.handle, _dptr(pose_ligand), _dptr(genotypes), n,
+                           _dptr(scores), _dptr(scores64), _dptr(coords), 1 if fp64 else 0,
+                           _stream(stream)))
+
+
+def version() -> str:
+    return lib().dock_version().decode()

@@ -1,0 +1,279 @@
+"""GPU vs CPU-oracle parity through the C ABI (libdock.so).
+
+Bars (per pose): genotypes bit-exact every generation (the GA replayed on
+the CPU from the GPU's own FP32 scores); FP32 scores within 1e-4 relative or
+1e-3 absolute of the FP64 oracle; posed coordinates within 1e-4 A; FP64
+rescores within 1e-5 relative (the GPU interpolates FP32 maps, the oracle
+FP64 maps). Poses within 2e-4 A of a score discontinuity (grid face, 8 A
+cutoff) are counted separately and must be rare.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import OracleSide, compare_scores, gpu_ligands, gpu_pocket, within
+from oracle import oracle as o
+from paper_2509_12232_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from gpu_util import d2h, to_dev  # noqa: E402
+
+SEARCH = dict(p_cross=0.8, p_mut=0.02)
+
+
+@pytest.fixture(scope="module")
+def dock():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2509_12232_gb300 import build
+    build.build()
+    from paper_2509_12232_gb300 import dock as d
+    d.lib()
+    return d
+
+
+@pytest.fixture(scope="module")
+def c1(dock):
+    pk, ligs, w = synth.make_workload("c1")
+    ora = OracleSide(pk, ligs)
+    pocket = gpu_pocket(dock, pk)
+    gl = gpu_ligands(dock, pocket, ligs)
+    return dict(pk=pk, ligs=ligs, w=w, ora=ora, pocket=pocket, gl=gl)
+
+
+def test_grid_maps_match_oracle(dock, c1):
+    n, origin, ptr = c1["pocket"].grid()
+    g = c1["ora"].grid
+    assert (n, n, n) == g.n
+    np.testing.assert_allclose(origin, g.origin, atol=1e-5)
+    T = synth.N_TYPES
+    maps = d2h(ptr, T * n ** 3 * 4, np.float32).reshape(T, n, n, n, 4)
+    ref = g.maps
+    for t in range(T):
+        assert np.all(within(maps[t, ..., 0], ref[t], rel=1e-6, abs_=1e-6))
+    assert np.all(within(maps[0, ..., 1], ref[T], rel=1e-6, abs_=1e-6))
+    assert np.all(within(maps[0, ..., 2], ref[T + 1], rel=1e-6, abs_=1e-6))
+    assert np.all(maps[..., 3] == 0)
+
+
+def _pose_set(k, n_poses, seed):
+    g = np.concatenate([o.ga_init(k, 256, 12.0, seed + s, 77) for s in range((n_poses + 255) // 256)])
+    g = g[:n_poses]
+    out = np.zeros((n_poses, 23), np.float32)
+    out[:, :7 + k] = g
+    # pull a third of the poses towards the cavity wall
+    out[: n_poses // 3, :3] *= 1.6
+    return out
+
+
+def test_pose_and_score_parity_c1(dock, c1):
+    lig = c1["ora"].lig(0)
+    genos = _pose_set(lig.k, 1024, 5)
+    n = genos.shape[0]
+    dg = to_dev(torch, genos)
+    pl = torch.zeros(n, dtype=torch.int32, device="cuda")
+    sc = torch.zeros(n, dtype=torch.float32, device="cuda")
+    s64 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    co = torch.zeros(n, 128, 3, dtype=torch.float32, device="cuda")
+    dock.dock_score(c1["pocket"], c1["gl"], pl, dg, scores=sc, coords=co)
+    dock.dock_score(c1["pocket"], c1["gl"], pl, dg, scores64=s64, fp64=True)
+    torch.cuda.synchronize()
+    ref = c1["ora"].score(0, genos[:, :lig.n_genes], want_xyz=True)
+    xyz = co.cpu().numpy()[:, :lig.n]
+    assert np.abs(xyz - ref["xyz"]).max() < 1e-4
+    checked, near, worst, fails = compare_scores(sc.cpu().numpy(), ref["score"], ref["margin"])
+    assert len(fails) == 0, (fails[:5], sc.cpu().numpy()[fails[:5]], ref["score"][fails[:5]])
+    assert near <= n // 100
+    ok64 = within(s64.cpu().numpy(), ref["score"], rel=1e-5, abs_=1e-4)
+    assert np.all(ok64 | (ref["margin"] < 2e-4))
+
+
+def _replay(dock, side, gl, pocket, pop, gens, seed, lanes=0, use_graph=1, ligs_check=None,
+            gens_check=None, poses_per_gen=None):
+    """Run a traced search; replay the GA on the CPU from the GPU scores."""
+    ligs = side.ligs
+    nl = ligs.n_ligands
+    goff = gl.geno_offsets(pop)
+    tot = int(goff[-1])
+    tg = torch.zeros(gens * max(tot, 1), dtype=torch.float32, device="cuda")
+    ts = torch.zeros(gens * max(nl * pop, 1), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    job = dock.dock_batch(pocket, gl, pop, gens, seed=seed, lanes_per_pose=lanes,
+                          use_graph=use_graph, trace_genotypes=tg, trace_scores=ts, stream=stream,
+                          **SEARCH)
+    res = dock.dock_results(job)
+    R = side.pk.radius
+    ligs_check = range(nl) if ligs_check is None else ligs_check
+    gens_check = range(gens) if gens_check is None else gens_check
+    stats = dict(checked=0, near=0, worst=0.0)
+    for l in ligs_check:
+        k = ligs.n_tors(l)
+        G = 7 + k
+        lid = int(ligs.ligand_id[l])
+
+        def geno(g):
+            base = g * tot + int(goff[l])
+            return tg[base: base + pop * G].cpu().numpy().reshape(pop, G)
+
+        def scores(g):
+            base = g * nl * pop + l * pop
+            return ts[base: base + pop].cpu().numpy()
+
+        for g in gens_check:
+            cur = geno(g)
+            if g == 0:
+                exp = o.ga_init(k, pop, R, seed, lid)
+            else:
+                exp = o.ga_step(k, pop, SEARCH["p_cross"], SEARCH["p_mut"], seed, lid, g,
+                                geno(g - 1), scores(g - 1))
+            np.testing.assert_array_equal(cur.view(np.uint32), exp.view(np.uint32),
+                                          err_msg="ligand %d generation %d" % (l, g))
+            sel = np.arange(pop) if poses_per_gen is None else \
+                np.random.default_rng(l * 1000 + g).choice(pop, min(pop, poses_per_gen), replace=False)
+            ref = side.score(l, cur[sel])
+            c, nr, worst, fails = compare_scores(scores(g)[sel], ref["score"], ref["margin"])
+            assert len(fails) == 0, ("ligand", l, "gen", g, fails[:5], scores(g)[sel][fails[:5]],
+                                     ref["score"][fails[:5]])
+            stats["checked"] += c
+            stats["near"] += nr
+            stats["worst"] = max(stats["worst"], worst)
+        # results: best 8 of the final population and their FP64 rescores
+        r = res[l]
+        fin = scores(gens - 1)
+        key = [(np.inf if math.isnan(v) else v, i) for i, v in enumerate(fin.tolist())]
+        order = [i for _, i in sorted(key)][:8]
+        assert r["best_index"].tolist()[:len(order)] == order
+        np.testing.assert_array_equal(r["best_fp32"][:len(order)], fin[order])
+        final = geno(gens - 1)
+        np.testing.assert_array_equal(r["genotype"][:len(order), :G], final[order])
+        ref = side.score(l, final[order])
+        assert np.all(within(r["best_fp64"][:len(order)], ref["score"], rel=1e-5, abs_=1e-4) |
+                      (ref["margin"] < 2e-4))
+        assert int(r["exact_evals"]) == pop * gens
+        assert int(r["ligand_id"]) == lid and int(r["n_genes"]) == G and int(r["status"]) == 0
+    job.close()
+    return stats
+
+
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_search_replay_c1(dock, c1, use_graph):
+    st = _replay(dock, c1["ora"], c1["gl"], c1["pocket"], pop=256, gens=10, seed=0,
+                 use_graph=use_graph)
+    assert st["checked"] >= 2500
+    assert st["near"] <= 26
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_search_forced_lanes(dock, c1, lanes):
+    _replay(dock, c1["ora"], c1["gl"], c1["pocket"], pop=96, gens=3, seed=3, lanes=lanes)
+
+
+def test_edge_ligands_ragged_population(dock, c1):
+    """1- and 2-atom ligands, a 128-atom ligand with 16 torsions, a rigid
+    40-atom ligand; a population that is no multiple of any tile."""
+    rng = np.random.Generator(np.random.Philox(99))
+    ligs = synth.make_ligands(rng, [1, 2, 128, 40, 9], [0, 0, 16, 0, 3], id_base=500)
+    assert ligs.n_tors(2) == 16
+    side = OracleSide(c1["pk"], ligs, grid=c1["ora"].grid)
+    gl = gpu_ligands(dock, c1["pocket"], ligs)
+    for gens in (1, 3):
+        _replay(dock, side, gl, c1["pocket"], pop=37, gens=gens, seed=11)
+    _replay(dock, side, gl, c1["pocket"], pop=2, gens=2, seed=12)
+
+
+def test_empty_batch(dock, c1):
+    ligs = synth.make_ligands(np.random.default_rng(0), [], [])
+    gl = gpu_ligands(dock, c1["pocket"], ligs)
+    job = dock.dock_batch(c1["pocket"], gl, 64, 2, stream=torch.cuda.current_stream())
+    assert dock.dock_results(job).shape == (0,)
+
+
+def test_invalid_input_rejected(dock, c1):
+    ligs = c1["ligs"]
+    bad_parent = ligs.parent.copy()
+    bad_parent[5] = 7      # parent after child
+    with pytest.raises(dock.DockError) as e:
+        dock.dock_load_ligands(c1["pocket"], ligs.atom_off, ligs.x, ligs.y, ligs.z, ligs.q, ligs.type,
+                               bad_parent, ligs.tors_off, ligs.tors_b, ligs.ligand_id)
+    assert e.value.status == dock.DOCK_EINVAL
+    bad_type = ligs.type.copy()
+    bad_type[0] = 200
+    with pytest.raises(dock.DockError):
+        dock.dock_load_ligands(c1["pocket"], ligs.atom_off, ligs.x, ligs.y, ligs.z, ligs.q, bad_type,
+                               ligs.parent, ligs.tors_off, ligs.tors_b, ligs.ligand_id)
+    with pytest.raises(dock.DockError):
+        dock.dock_batch(c1["pocket"], c1["gl"], 1, 5)
+    with pytest.raises(dock.DockError):
+        dock.dock_batch(c1["pocket"], c1["gl"], 64, 5, lanes_per_pose=3)
+
+
+def test_device_deadline_sets_timeout_status(dock, c1):
+    """A deadline that has passed before the first work item stops the
+    persistent loops; the host sees DOCK_ETIMEOUT, the context stays usable."""
+    job = dock.dock_batch(c1["pocket"], c1["gl"], 256, 10, timeout_ns=1, use_graph=0,
+                          stream=torch.cuda.current_stream())
+    with pytest.raises(dock.DockError) as e:
+        dock.dock_results(job)
+    assert e.value.status == dock.DOCK_ETIMEOUT
+    job.close()
+    # the next job runs normally
+    job = dock.dock_batch(c1["pocket"], c1["gl"], 64, 2, stream=torch.cuda.current_stream())
+    dock.dock_results(job)
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c2(dock):
+    pk, ligs, w = synth.make_workload("c2")
+    ora = OracleSide(pk, ligs)
+    pocket = gpu_pocket(dock, pk)
+    gl = gpu_ligands(dock, pocket, ligs)
+    return dict(pk=pk, ligs=ligs, w=w, ora=ora, pocket=pocket, gl=gl)
+
+
+def test_c2_full_size_sampled(dock, c2):
+    """1,000 ligands x 1,024 poses x 50 generations, graph launch, default
+    lane shapes (the benchmark's configuration); replay and score sampled
+    ligands and generations."""
+    w = c2["w"]
+    rng = np.random.default_rng(7)
+    ligs_check = sorted(rng.choice(w.n_ligands, 6, replace=False).tolist())
+    ligs_check += [int(np.argmax(np.diff(c2["ligs"].atom_off)))]
+    st = _replay(dock, c2["ora"], c2["gl"], c2["pocket"], pop=w.pop, gens=w.generations, seed=0,
+                 ligs_check=ligs_check, gens_check=[0, 1, 2, 25, 49], poses_per_gen=48)
+    assert st["checked"] > 1500
+    assert st["near"] <= st["checked"] // 100
+
+
+def test_c3_full_size_sampled(dock):
+    """100,000 uneven ligands x 512 poses: GA replay over two generations on
+    sampled ligands, then the full 30-generation search with results checked
+    on a sample."""
+    pk, ligs, w = synth.make_workload("c3")
+    pocket = gpu_pocket(dock, pk)
+    gl = gpu_ligands(dock, pocket, ligs)
+    side = OracleSide(pk, ligs)
+    rng = np.random.default_rng(3)
+    na = np.diff(ligs.atom_off)
+    ligs_check = sorted(set(rng.choice(w.n_ligands, 5, replace=False).tolist() +
+                            [int(np.argmax(na)), int(np.argmin(na))]))
+    _replay(dock, side, gl, pocket, pop=w.pop, gens=2, seed=0, ligs_check=ligs_check,
+            poses_per_gen=32)
+    job = dock.dock_batch(pocket, gl, w.pop, w.generations, seed=0,
+                          stream=torch.cuda.current_stream(), **SEARCH)
+    res = dock.dock_results(job)
+    assert np.all(res["status"] == 0)
+    assert np.all(res["exact_evals"] == w.pop * w.generations)
+    for l in rng.choice(w.n_ligands, 40, replace=False):
+        G = 7 + ligs.n_tors(l)
+        ref = side.score(int(l), res[l]["genotype"][:, :G])
+        ok = within(res[l]["best_fp32"], ref["score"]) | (ref["margin"] < 2e-4)
+        assert np.all(ok), l
+        assert np.all(within(res[l]["best_fp64"], ref["score"], rel=1e-5, abs_=1e-4) |
+                      (ref["margin"] < 2e-4))
+        assert np.all(np.diff(res[l]["best_fp32"]) >= 0)
