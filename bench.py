@@ -226,6 +226,8 @@ def main():
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ligands", type=int, default=0,
+                    help="dock only the first N ligands (profiling runs; not a bench line)")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -244,6 +246,8 @@ def main():
     pk, _, w = synth.make_workload(WORKLOAD, pocket=True)
     # rank r docks shard r: same size distribution, its own draw and ligand ids
     rng = np.random.Generator(np.random.Philox(1000 + rank))
+    if args.ligands:
+        w.n_ligands = args.ligands
     na, nt = synth.ligand_sizes(rng, w.sizes, w.n_ligands)
     ligs = synth.make_ligands(rng, na, nt, id_base=rank * w.n_ligands)
     pocket = dock.dock_create_pocket(pk.x, pk.y, pk.z, pk.q, pk.type, pk.center, pk.radius,
@@ -309,7 +313,7 @@ def main():
         dock.dock_results(j)
         j.close()
         g2.close()
-    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = (time.perf_counter() - t0) / max(args.e2e_steps, 1)
     if world > 1:
         t = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)

@@ -81,6 +81,7 @@ struct dock_pocket {
   uint8_t *d_ptype = nullptr;
   int n_prot = 0;
   float4 *d_maps = nullptr;
+  float *d_pairs = nullptr;  // x-cell records, 32-byte aligned
   int n = 0;
   double ox = 0, oy = 0, oz = 0, h = 0;
   float center[3] = {0, 0, 0};
@@ -90,12 +91,14 @@ struct dock_pocket {
     dfree(d_prot);
     dfree(d_ptype);
     dfree(d_maps);
+    dfree(d_pairs);
   }
 };
 
 static GridView grid_view(const dock_pocket *p) {
   GridView g;
   g.maps = p->d_maps;
+  g.pairs = p->d_pairs;
   g.n = p->n;
   g.ox = (float)p->ox;
   g.oy = (float)p->oy;
@@ -155,8 +158,10 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
     CU(cudaMemcpyAsync(P->d_prot, prot.data(), sizeof(float4) * prot.size(), cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(P->d_ptype, d->type, d->n_atoms, cudaMemcpyHostToDevice, s));
   }
+  CU(dalloc(&P->d_pairs, (size_t)P->n_types * P->n * P->n * (P->n - 1) * 8));
   CU(launch_grid_build_impl(P->d_prot, P->d_ptype, P->n_prot, P->d_params, P->n_types, P->n,
                             P->ox, P->oy, P->oz, P->h, P->d_maps, s));
+  CU(launch_pair_maps(P->d_maps, P->n_types, P->n, P->d_pairs, s));
   CU(cudaStreamSynchronize(s));
   *out = guard.release();
   return DOCK_OK;
@@ -561,7 +566,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   if (const char *e = getenv("DOCK_ATOMS_PER_LANE")) cfg.atoms_per_lane = atoi(e);
   if (forced) cfg.atoms_per_lane = std::max(cfg.atoms_per_lane, (L->max_atoms + forced - 1) / forced);
   if (L->max_atoms > 8 * cfg.atoms_per_lane) cfg.atoms_per_lane = (L->max_atoms + 7) / 8;
-  if (cfg.threads < 32 || cfg.threads > 256 || (cfg.threads & (cfg.threads - 1)) || cfg.atoms_per_lane < 1)
+  if (cfg.threads < 32 || cfg.threads > 128 || (cfg.threads & (cfg.threads - 1)) || cfg.atoms_per_lane < 1)
     return fail(DOCK_EINVAL, "dock_batch: launch shape %d threads x %d atoms per lane", cfg.threads,
                 cfg.atoms_per_lane);
   // keep the coordinate planes within the shared memory an SM offers

@@ -254,8 +254,17 @@ __device__ __forceinline__ float pair_energy(float r2, float4 coef, bool hb) {
   return r2 < kCutoff2 ? e : 0.0f;
 }
 
+// One 256-bit read-only load (8 floats, 32-byte aligned address).
+__device__ __forceinline__ void ld8(const float *p, float (&v)[8]) {
+  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                 "=f"(v[6]), "=f"(v[7])
+               : "l"(p));
+}
+
 // Trilinear interpolation of M_t + q E + |q| D at (x, y, z); returns false if
-// the point is outside the grid box (faces included as inside).
+// the point is outside the grid box (faces included as inside). Reads the
+// x-cell records: one 32-byte load per (y, z) corner pair.
 __device__ __forceinline__ bool grid_energy(const GridView &G, int t, float q, float x, float y,
                                             float z, float &e) {
   float ux = (x - G.ox) * G.inv_h, uy = (y - G.oy) * G.inv_h, uz = (z - G.oz) * G.inv_h;
@@ -265,20 +274,23 @@ __device__ __forceinline__ bool grid_energy(const GridView &G, int t, float q, f
   int ix = min((int)ux, G.n - 2), iy = min((int)uy, G.n - 2), iz = min((int)uz, G.n - 2);
   float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
   const float aq = fabsf(q);
-  const float4 *m = G.maps + (((int64_t)t * G.n + iz) * G.n + iy) * G.n + ix;
-  const int sy = G.n, sz = G.n * G.n;
-  float v[8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    float4 a = __ldg(m + ((c >> 2) & 1) * sz + ((c >> 1) & 1) * sy + (c & 1));
-    v[c] = a.x + q * a.y + aq * a.z;
-  }
-  float x00 = v[0] + fx * (v[1] - v[0]);
-  float x10 = v[2] + fx * (v[3] - v[2]);
-  float x01 = v[4] + fx * (v[5] - v[4]);
-  float x11 = v[6] + fx * (v[7] - v[6]);
-  float y0 = x00 + fy * (x10 - x00);
-  float y1 = x01 + fy * (x11 - x01);
+  const int nx = G.n - 1;
+  const float *base = G.pairs + ((((int64_t)t * G.n + iz) * G.n + iy) * nx + ix) * 8;
+  const int64_t sy = (int64_t)nx * 8, sz = (int64_t)G.n * nx * 8;
+  float c00[8], c10[8], c01[8], c11[8];
+  ld8(base, c00);
+  ld8(base + sy, c10);
+  ld8(base + sz, c01);
+  ld8(base + sz + sy, c11);
+  // corner values v = M + q E + |q| D, interpolated along x
+  auto lx = [&](const float (&c)[8]) {
+    const float v0 = c[0] + q * c[1] + aq * c[2];
+    const float v1 = c[3] + q * c[4] + aq * c[5];
+    return v0 + fx * (v1 - v0);
+  };
+  const float a = lx(c00), b = lx(c10), c = lx(c01), d = lx(c11);
+  const float y0 = a + fy * (b - a);
+  const float y1 = c + fy * (d - c);
   e = y0 + fz * (y1 - y0);
   return true;
 }

@@ -42,6 +42,8 @@ struct Item {
 
 struct GridView {
   const float4 *maps;   // [n_types][n][n][n] {M_t, E, D, 0}
+  const float *pairs;   // [n_types][n][n][n-1] x-cell records of 8 floats, 32 B aligned:
+                        // {M(x), E(x), D(x), M(x+1), E(x+1), D(x+1), 0, 0}
   int32_t n;            // nodes per axis
   float ox, oy, oz;     // origin
   float inv_h;
@@ -134,5 +136,6 @@ cudaError_t launch_score_fp64_impl(const Fp64Args &f, const double *centroids, d
                                    double oz, const int32_t *pose_ligand, int n_ligands,
                                    const float *genos, int64_t n_poses, double *out, cudaStream_t s);
 int search_smem_bytes(int threads, int atoms_per_lane);
+cudaError_t launch_pair_maps(const float4 *maps, int n_types, int n, float *pairs, cudaStream_t s);
 
 }  // namespace dk

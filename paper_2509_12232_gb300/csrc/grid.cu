@@ -127,4 +127,24 @@ cudaError_t launch_grid_build_impl(const float4 *prot, const uint8_t *ptype, int
   return cudaGetLastError();
 }
 
+// x-cell records for the FP32 scorer: cell (x, y, z) of type t holds
+// {M(x), E(x), D(x), M(x+1), E(x+1), D(x+1), 0, 0}.
+__global__ void pair_maps_kernel(const float4 *maps, int n_types, int n, float *pairs) {
+  const int64_t nx = n - 1;
+  const int64_t total = (int64_t)n_types * n * n * nx;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ix = c % nx, row = c / nx;  // row = (t * n + z) * n + y
+    const float4 a = maps[row * n + ix], b = maps[row * n + ix + 1];
+    float4 *o = reinterpret_cast<float4 *>(pairs + c * 8);
+    o[0] = make_float4(a.x, a.y, a.z, b.x);
+    o[1] = make_float4(b.y, b.z, 0.0f, 0.0f);
+  }
+}
+
+cudaError_t launch_pair_maps(const float4 *maps, int n_types, int n, float *pairs, cudaStream_t s) {
+  pair_maps_kernel<<<152 * 8, 256, 0, s>>>(maps, n_types, n, pairs);
+  return cudaGetLastError();
+}
+
 }  // namespace dk

@@ -16,9 +16,19 @@
 
 namespace dk {
 
+// Coordinate planes: L * atoms_per_lane rows (atoms) by SP columns (pose
+// slots). For L > 1 the row stride SP is an odd multiple of 32 / L, so the L
+// lanes of a group reading consecutive atoms of one pose hit disjoint banks;
+// rows * SP <= atoms_per_lane * (threads + 32) for every L.
+__host__ __device__ __forceinline__ int plane_stride(int threads, int L) {
+  const int S = threads / L;
+  if (L == 1) return S;
+  const int w = 32 / L;
+  return ((S / w) & 1) ? S : S + w;
+}
+
 int search_smem_bytes(int threads, int atoms_per_lane) {
-  // planes of atoms_per_lane * L rows by (threads / L + 1) columns, L <= 8
-  return 3 * atoms_per_lane * (threads + 8) * (int)sizeof(float);
+  return 3 * atoms_per_lane * (threads + 32) * (int)sizeof(float);
 }
 
 struct LigView {
@@ -101,6 +111,7 @@ __device__ __forceinline__ float pose_and_score(const float (&g)[DOCK_MAX_GENES]
   }
   // ---- Algorithm 2: inter-energy by grid lookup ----------------------------
   Kahan acc;
+#pragma unroll 2
   for (int a = lane; a < V.n; a += L) {
     const float x = sx[a * SP + slot], y = sy[a * SP + slot], z = sz[a * SP + slot];
     float e;
@@ -142,11 +153,11 @@ __device__ __forceinline__ unsigned group_mask(int L) {
   return ((1u << L) - 1u) << base;
 }
 
-__global__ void __launch_bounds__(256) search_kernel(const SearchArgs A) {
+__global__ void __launch_bounds__(128, 6) search_kernel(const SearchArgs A) {
   extern __shared__ float smem[];
   __shared__ int s_item;
   const int T = blockDim.x;
-  const int plane = A.atoms_per_lane * (T + 8);
+  const int plane = A.atoms_per_lane * (T + 32);
   float *sx = smem, *sy = smem + plane, *sz = smem + 2 * plane;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(256) search_kernel(const SearchArgs A) {
     const Item item = A.items[it];
     const int L = item.lanes;
     const int S = T / L;
-    const int SP = S + (L > 1 ? 1 : 0);
+    const int SP = plane_stride(T, L);
     const int lane = threadIdx.x & (L - 1);
     const int slot = threadIdx.x / L;
     const int ind = item.first_div * S + slot;
@@ -236,8 +247,8 @@ cudaError_t launch_set_deadline(uint64_t *deadline, uint64_t timeout_ns, cudaStr
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) score_kernel(const ScoreArgs A) {
   extern __shared__ float smem[];
-  const int T = blockDim.x, L = A.lanes, S = T / L, SP = S + (L > 1 ? 1 : 0);
-  const int plane = A.atoms_per_lane * (T + 8);
+  const int T = blockDim.x, L = A.lanes, S = T / L, SP = plane_stride(T, L);
+  const int plane = A.atoms_per_lane * (T + 32);
   float *sx = smem, *sy = smem + plane, *sz = smem + 2 * plane;
   const int lane = threadIdx.x & (L - 1), slot = threadIdx.x / L;
   const int64_t pose = (int64_t)blockIdx.x * S + slot;
