@@ -67,7 +67,7 @@ static void dfree(T *&p) {
 
 // AutoDock4 free-energy constants for the host-side pair coefficients.
 static const double kHWVdw = 0.1662, kHWHb = 0.1209, kHWElec = 0.1406, kHWSol = 0.1322;
-static const double kHCoulomb = 332.06363, kHQasp = 0.01097;
+static const double kHCoulomb = 332.06363, kHQasp = 0.01097, kHEmax = 1.0e5;
 
 // ---------------------------------------------------------------------------
 // pocket
@@ -81,7 +81,8 @@ struct dock_pocket {
   uint8_t *d_ptype = nullptr;
   int n_prot = 0;
   float4 *d_maps = nullptr;
-  float *d_pairs = nullptr;  // x-cell records, 32-byte aligned
+  float *d_xycell = nullptr;  // (x, y)-cell records of the FP32 scorer
+  float2 *d_fpm = nullptr;    // per node {E + D, E - D}
   int n = 0;
   double ox = 0, oy = 0, oz = 0, h = 0;
   float center[3] = {0, 0, 0};
@@ -91,14 +92,15 @@ struct dock_pocket {
     dfree(d_prot);
     dfree(d_ptype);
     dfree(d_maps);
-    dfree(d_pairs);
+    dfree(d_xycell);
+    dfree(d_fpm);
   }
 };
 
 static GridView grid_view(const dock_pocket *p) {
   GridView g;
   g.maps = p->d_maps;
-  g.pairs = p->d_pairs;
+  g.xycell = p->d_xycell;
   g.n = p->n;
   g.ox = (float)p->ox;
   g.oy = (float)p->oy;
@@ -158,10 +160,11 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
     CU(cudaMemcpyAsync(P->d_prot, prot.data(), sizeof(float4) * prot.size(), cudaMemcpyHostToDevice, s));
     CU(cudaMemcpyAsync(P->d_ptype, d->type, d->n_atoms, cudaMemcpyHostToDevice, s));
   }
-  CU(dalloc(&P->d_pairs, (size_t)P->n_types * P->n * P->n * (P->n - 1) * 8));
+  CU(dalloc(&P->d_xycell, (size_t)P->n_types * 2 * P->n * (P->n - 1) * (P->n - 1) * 8));
+  CU(dalloc(&P->d_fpm, nodes));
   CU(launch_grid_build_impl(P->d_prot, P->d_ptype, P->n_prot, P->d_params, P->n_types, P->n,
-                            P->ox, P->oy, P->oz, P->h, P->d_maps, s));
-  CU(launch_pair_maps(P->d_maps, P->n_types, P->n, P->d_pairs, s));
+                            P->ox, P->oy, P->oz, P->h, P->d_maps, P->d_fpm, s));
+  CU(launch_xycell_maps(P->d_maps, P->d_fpm, P->n_types, P->n, P->d_xycell, s));
   CU(cudaStreamSynchronize(s));
   *out = guard.release();
   return DOCK_OK;
@@ -228,7 +231,7 @@ struct dock_ligands {
   double *d_centroid = nullptr;
   uint8_t *d_types = nullptr;
   uint32_t *d_pair_idx = nullptr;
-  float4 *d_pair_coef = nullptr;
+  float *d_pair_rec = nullptr;
   TorInfo *d_tors = nullptr;
   uint8_t *d_moves = nullptr;
   int64_t total_pairs = 0, total_atoms = 0, total_tors = 0, total_moved = 0, h2d_bytes = 0;
@@ -240,7 +243,7 @@ struct dock_ligands {
     dfree(d_centroid);
     dfree(d_types);
     dfree(d_pair_idx);
-    dfree(d_pair_coef);
+    dfree(d_pair_rec);
     dfree(d_tors);
     dfree(d_moves);
   }
@@ -249,7 +252,7 @@ struct dock_ligands {
 namespace {
 struct LigHost {
   std::vector<uint32_t> pair_idx;
-  std::vector<float4> pair_coef;
+  std::vector<float> pair_rec;   // 8 per pair
   std::vector<TorInfo> tors;   // move_off relative to this ligand's moves
   std::vector<uint8_t> moves;
   double cent[3];
@@ -359,23 +362,30 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
       const double qi = b->q[a0 + i], qj = b->q[a0 + j];
       const bool hb = (tp[ti].hb_role == 1 && tp[tj].hb_role == 2) ||
                       (tp[ti].hb_role == 2 && tp[tj].hb_role == 1);
-      double c12, cx;
+      double c12, c6 = 0.0, c10 = 0.0, w;
       if (hb) {
         const int acc = tp[ti].hb_role == 2 ? ti : tj;
         const double R = tp[acc].hb_R, e = tp[acc].hb_eps;
-        c12 = kHWHb * 5.0 * e * std::pow(R, 12);
-        cx = kHWHb * 6.0 * e * std::pow(R, 10);
+        w = kHWHb;
+        c12 = w * 5.0 * e * std::pow(R, 12);
+        c10 = w * 6.0 * e * std::pow(R, 10);
       } else {
         const double R = 0.5 * ((double)tp[ti].Rii + (double)tp[tj].Rii);
         const double e = std::sqrt((double)tp[ti].eps * (double)tp[tj].eps);
-        c12 = kHWVdw * e * std::pow(R, 12);
-        cx = kHWVdw * 2.0 * e * std::pow(R, 6);
+        w = kHWVdw;
+        c12 = w * e * std::pow(R, 12);
+        c6 = w * 2.0 * e * std::pow(R, 6);
       }
       const double si = (double)tp[ti].solpar + kHQasp * std::fabs(qi);
       const double sj = (double)tp[tj].solpar + kHQasp * std::fabs(qj);
       H.pair_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
-      H.pair_coef.push_back(make_float4((float)c12, (float)cx, (float)(kHWElec * kHCoulomb * qi * qj),
-                                        (float)(kHWSol * (si * tp[tj].vol + sj * tp[ti].vol))));
+      const uint32_t ij = (uint32_t)i | ((uint32_t)j << 16);
+      float ijf;
+      std::memcpy(&ijf, &ij, 4);
+      const float rec[8] = {(float)c12, (float)c6, (float)c10, (float)(w * kHEmax),
+                            (float)(kHWElec * kHCoulomb * qi * qj),
+                            (float)(kHWSol * (si * tp[tj].vol + sj * tp[ti].vol)), ijf, 0.0f};
+      H.pair_rec.insert(H.pair_rec.end(), rec, rec + 8);
     }
 }
 
@@ -443,7 +453,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   std::vector<float4> atoms((size_t)n_atoms), raw((size_t)n_atoms);
   std::vector<double> cent((size_t)nl * 3);
   std::vector<uint32_t> pidx((size_t)np);
-  std::vector<float4> pcoef((size_t)np);
+  std::vector<float> prec((size_t)np * 8);
   std::vector<TorInfo> tors((size_t)nt);
   std::vector<uint8_t> moves((size_t)nm);
   parallel_for(nl, [&](int l) {
@@ -456,7 +466,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
     }
     for (int m = 0; m < 3; ++m) cent[(size_t)l * 3 + m] = H[l].cent[m];
     std::copy(H[l].pair_idx.begin(), H[l].pair_idx.end(), pidx.begin() + I.pair_off);
-    std::copy(H[l].pair_coef.begin(), H[l].pair_coef.end(), pcoef.begin() + I.pair_off);
+    std::copy(H[l].pair_rec.begin(), H[l].pair_rec.end(), prec.begin() + (size_t)I.pair_off * 8);
     std::copy(H[l].tors.begin(), H[l].tors.end(), tors.begin() + I.tors_off);
     if (!H[l].tors.empty())
       std::copy(H[l].moves.begin(), H[l].moves.end(), moves.begin() + H[l].tors[0].move_off);
@@ -468,7 +478,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   CU(dalloc(&L->d_centroid, (size_t)nl * 3));
   CU(dalloc(&L->d_types, (size_t)n_atoms));
   CU(dalloc(&L->d_pair_idx, (size_t)np));
-  CU(dalloc(&L->d_pair_coef, (size_t)np));
+  CU(dalloc(&L->d_pair_rec, (size_t)np * 8));
   CU(dalloc(&L->d_tors, (size_t)nt));
   CU(dalloc(&L->d_moves, (size_t)nm));
   auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
@@ -480,7 +490,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   CU(up(L->d_centroid, cent.data(), sizeof(double) * cent.size()));
   CU(up(L->d_types, b->type, (size_t)n_atoms));
   CU(up(L->d_pair_idx, pidx.data(), sizeof(uint32_t) * np));
-  CU(up(L->d_pair_coef, pcoef.data(), sizeof(float4) * np));
+  CU(up(L->d_pair_rec, prec.data(), sizeof(float) * 8 * np));
   CU(up(L->d_tors, tors.data(), sizeof(TorInfo) * nt));
   CU(up(L->d_moves, moves.data(), (size_t)nm));
   CU(cudaStreamSynchronize(s));
@@ -488,7 +498,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   L->total_tors = nt;
   L->total_moved = nm;
   L->h2d_bytes = (int64_t)(sizeof(LigInfo) * nl + 2 * sizeof(float4) * n_atoms + sizeof(double) * 3 * nl +
-                           n_atoms + (sizeof(uint32_t) + sizeof(float4)) * np + sizeof(TorInfo) * nt + nm);
+                           n_atoms + (sizeof(uint32_t) + 8 * sizeof(float)) * np + sizeof(TorInfo) * nt + nm);
   *out = guard.release();
   return DOCK_OK;
 }
@@ -673,8 +683,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   A.ligs = L->d_info;
   A.atoms = L->d_atoms;
   A.types = L->d_types;
-  A.pair_idx = L->d_pair_idx;
-  A.pair_coef = L->d_pair_coef;
+  A.pair_rec = L->d_pair_rec;
   A.tors = L->d_tors;
   A.moves = L->d_moves;
   A.geno_off = W.geno_off;
@@ -877,8 +886,7 @@ extern "C" int dock_score(dock_pocket *P, dock_ligands *L, const int32_t *pose_l
   A.ligs = L->d_info;
   A.atoms = L->d_atoms;
   A.types = L->d_types;
-  A.pair_idx = L->d_pair_idx;
-  A.pair_coef = L->d_pair_coef;
+  A.pair_rec = L->d_pair_rec;
   A.tors = L->d_tors;
   A.moves = L->d_moves;
   A.grid = grid_view(P);

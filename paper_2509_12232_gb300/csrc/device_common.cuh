@@ -164,8 +164,9 @@ __device__ __forceinline__ void ga_child(float (&g)[DOCK_MAX_GENES], int k, int 
   for (int e = 0; e < DOCK_MAX_GENES; ++e) {
     float v = 0.0f;
     if (e < G) {
-      int blk = gene_block(e);
-      v = (blk >= lo && blk < hi) ? __ldg(Bp + e) : __ldg(A + e);
+      const int blk = gene_block(e);
+      const float *src = (blk >= lo && blk < hi) ? Bp : A;
+      v = __ldg(src + e);
     }
     g[e] = v;
   }
@@ -226,34 +227,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
 }
 
-// ---------------------------------------------------------------------------
-// Pair energy (FP32). r2: squared distance; coef {c12, cx, qq, ds} with the
-// weights folded in; hb selects the 12-10 form (x = 10) over 12-6 (x = 6).
-// Zero at r >= 8 A; r floored at 0.5 A; the dispersion part is capped at
-// w * EMAX (cap before weighting).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float pair_energy(float r2, float4 coef, bool hb) {
-  const float lb = (float)(kDielLambda * kDielB);
-  const float inv_2s2 = (float)(1.0 / (2.0 * kSigma * kSigma));
-  const float dA = (float)kDielA, dB = (float)kDielB, dK = (float)kDielK;
-  const float log2e = 1.4426950408889634f;
-  float r2c = fmaxf(r2, kRmin2);
-  float inv_r = rsqrtf(r2c);
-  float inv_r2 = inv_r * inv_r;
-  float r = r2c * inv_r;
-  float inv_r6 = inv_r2 * inv_r2 * inv_r2;
-  float inv_r12 = inv_r6 * inv_r6;
-  float inv_rx = hb ? inv_r6 * (inv_r2 * inv_r2) : inv_r6;
-  float cap = hb ? (float)(kWHb * kEmax) : (float)(kWVdw * kEmax);
-  float disp = fminf(coef.x * inv_r12 - coef.y * inv_rx, cap);
-  float ex = exp2f(-lb * log2e * r);
-  float onek = 1.0f + dK * ex;
-  float elec = __fdividef(coef.z * onek, (dA * onek + dB) * r);
-  float des = coef.w * exp2f(-r2c * (inv_2s2 * log2e));
-  float e = disp + elec + des;
-  return r2 < kCutoff2 ? e : 0.0f;
-}
-
 // One 256-bit read-only load (8 floats, 32-byte aligned address).
 __device__ __forceinline__ void ld8(const float *p, float (&v)[8]) {
   asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -262,37 +235,91 @@ __device__ __forceinline__ void ld8(const float *p, float (&v)[8]) {
                : "l"(p));
 }
 
-// Trilinear interpolation of M_t + q E + |q| D at (x, y, z); returns false if
-// the point is outside the grid box (faces included as inside). Reads the
-// x-cell records: one 32-byte load per (y, z) corner pair.
-__device__ __forceinline__ bool grid_energy(const GridView &G, int t, float q, float x, float y,
-                                            float z, float &e) {
-  float ux = (x - G.ox) * G.inv_h, uy = (y - G.oy) * G.inv_h, uz = (z - G.oz) * G.inv_h;
-  float nm1 = (float)(G.n - 1);
-  if (!(ux >= 0.0f && ux <= nm1 && uy >= 0.0f && uy <= nm1 && uz >= 0.0f && uz <= nm1))
-    return false;
-  int ix = min((int)ux, G.n - 2), iy = min((int)uy, G.n - 2), iz = min((int)uz, G.n - 2);
-  float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
-  const float aq = fabsf(q);
-  const int nx = G.n - 1;
-  const float *base = G.pairs + ((((int64_t)t * G.n + iz) * G.n + iy) * nx + ix) * 8;
-  const int64_t sy = (int64_t)nx * 8, sz = (int64_t)G.n * nx * 8;
-  float c00[8], c10[8], c01[8], c11[8];
-  ld8(base, c00);
-  ld8(base + sy, c10);
-  ld8(base + sz, c01);
-  ld8(base + sz + sy, c11);
-  // corner values v = M + q E + |q| D, interpolated along x
-  auto lx = [&](const float (&c)[8]) {
-    const float v0 = c[0] + q * c[1] + aq * c[2];
-    const float v1 = c[3] + q * c[4] + aq * c[5];
-    return v0 + fx * (v1 - v0);
+// ---------------------------------------------------------------------------
+// Pair energy (FP32) from a 32-byte pair record
+// {c12, c6, c10, cap, qq, ds, bits(i | j << 16), 0} (weights folded in):
+//   min(c12 r^-12 - c6 r^-6 - c10 r^-10, cap) + qq / (eps(r) r) + ds exp(-r^2 / 2 sigma^2)
+// with eps(r) = A + B / (1 + k exp(-lambda B r)), so 1 / (eps r) = (1 + k e) / ((A (1 + k e) + B) r).
+// Zero at r >= 8 A; r floored at 0.5 A. The hardware approximations
+// (rsqrt, ex2, rcp, flush-to-zero) see arguments far from the denormal range.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float pair_energy(float r2, const float (&rec)[8]) {
+  const float kLb = (float)(-kDielLambda * kDielB * 1.4426950408889634);  // ex2 argument per A
+  const float kS = (float)(-1.4426950408889634 / (2.0 * kSigma * kSigma));
+  const float dA = (float)kDielA, dB = (float)kDielB, dK = (float)kDielK;
+  const float r2c = fmaxf(r2, kRmin2);
+  const float ir = rsqrt_ftz(r2c);
+  const float ir2 = ir * ir;
+  const float r = r2c * ir;
+  const float ir4 = ir2 * ir2;
+  const float ir6 = ir4 * ir2;
+  const float disp = fminf(rec[0] * (ir6 * ir6) - rec[1] * ir6 - rec[2] * (ir6 * ir4), rec[3]);
+  const float onek = 1.0f + dK * ex2_ftz(kLb * r);
+  const float elec = rec[4] * onek * rcp_ftz((dA * onek + dB) * r);
+  const float des = rec[5] * ex2_ftz(kS * r2c);
+  const float e = disp + elec + des;
+  return r2 < kCutoff2 ? e : 0.0f;
+}
+
+
+// Grid lookup of M_t + q E + |q| D split in two halves so other work can run
+// while the loads are in flight: grid_issue computes the cell and issues the
+// two 32-byte (x, y)-cell loads (planes z and z+1), grid_finish interpolates.
+// A point outside the grid box (faces count as inside) gives EOUT.
+struct Lookup {
+  float c0[8], c1[8];
+  float fx, fy, fz, q;
+  bool inside;
+};
+
+__device__ __forceinline__ Lookup grid_issue(const GridView &G, int t, float q, float x, float y,
+                                             float z) {
+  Lookup L;
+  const float ux = (x - G.ox) * G.inv_h, uy = (y - G.oy) * G.inv_h, uz = (z - G.oz) * G.inv_h;
+  const float nm1 = (float)(G.n - 1);
+  L.inside = ux >= 0.0f && ux <= nm1 && uy >= 0.0f && uy <= nm1 && uz >= 0.0f && uz <= nm1;
+  L.q = q;
+  if (L.inside) {
+    const int ix = min((int)ux, G.n - 2), iy = min((int)uy, G.n - 2), iz = min((int)uz, G.n - 2);
+    L.fx = ux - (float)ix;
+    L.fy = uy - (float)iy;
+    L.fz = uz - (float)iz;
+    const int nc = G.n - 1;
+    const int sg = q < 0.0f ? 1 : 0;
+    const float *base = G.xycell + ((((int64_t)(2 * t + sg) * G.n + iz) * nc + iy) * nc + ix) * 8;
+    ld8(base, L.c0);
+    ld8(base + (int64_t)nc * nc * 8, L.c1);
+  }
+  return L;
+}
+
+__device__ __forceinline__ float grid_finish(const Lookup &L) {
+  if (!L.inside) return kEout;
+  const float q = L.q, fx = L.fx, fy = L.fy;
+  auto plane = [&](const float (&c)[8]) {
+    const float v00 = c[0] + q * c[1], v10 = c[2] + q * c[3];
+    const float v01 = c[4] + q * c[5], v11 = c[6] + q * c[7];
+    const float a = v00 + fx * (v10 - v00), b = v01 + fx * (v11 - v01);
+    return a + fy * (b - a);
   };
-  const float a = lx(c00), b = lx(c10), c = lx(c01), d = lx(c11);
-  const float y0 = a + fy * (b - a);
-  const float y1 = c + fy * (d - c);
-  e = y0 + fz * (y1 - y0);
-  return true;
+  const float p0 = plane(L.c0), p1 = plane(L.c1);
+  return p0 + L.fz * (p1 - p0);
 }
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {

@@ -36,14 +36,18 @@ struct Item {
   int8_t pad;
 };
 
-// Pair record: bits 0-7 atom i, 8-15 atom j, 16 H-bond (12-10) flag.
-// Coefficients (weights folded in): c12, cx (x = 6 or 10), qq (W_elec *
-// 332.06363 * q_i q_j), ds (W_sol * (S_i V_j + S_j V_i)).
+// pair_idx (u32, FP64 path): bits 0-7 atom i, 8-15 atom j, 16 H-bond flag.
+// pair_rec (FP32 path): 8 floats per pair, 32-byte aligned, weights folded in:
+// {c12, c6, c10, cap, qq, ds, bits(i | j << 16), 0} for
+// E = min(c12 r^-12 - c6 r^-6 - c10 r^-10, cap) + qq / (eps(r) r) + ds exp(-r^2 / 2 sigma^2),
+// c6 = 0 for an H-bond (12-10) pair and c10 = 0 otherwise; cap = w * EMAX.
 
 struct GridView {
   const float4 *maps;   // [n_types][n][n][n] {M_t, E, D, 0}
-  const float *pairs;   // [n_types][n][n][n-1] x-cell records of 8 floats, 32 B aligned:
-                        // {M(x), E(x), D(x), M(x+1), E(x+1), D(x+1), 0, 0}
+  const float *xycell;  // [n_types][2][n][n-1][n-1] (x, y)-cell records, 8 floats, 32-byte
+                        // aligned: {M, F} at (x,y), (x+1,y), (x,y+1), (x+1,y+1) with
+                        // F = E + D (sign 0, for q >= 0) or E - D (sign 1, q < 0), so
+                        // M + q E + |q| D = M + q F
   int32_t n;            // nodes per axis
   float ox, oy, oz;     // origin
   float inv_h;
@@ -55,8 +59,7 @@ struct SearchArgs {
   const LigInfo *ligs;
   const float4 *atoms;      // {x, y, z, q}, centred on the ligand centroid
   const uint8_t *types;
-  const uint32_t *pair_idx;
-  const float4 *pair_coef;
+  const float *pair_rec;
   const TorInfo *tors;
   const uint8_t *moves;
   const int64_t *geno_off;  // [n_ligands]
@@ -90,8 +93,7 @@ struct ScoreArgs {
   const LigInfo *ligs;
   const float4 *atoms;
   const uint8_t *types;
-  const uint32_t *pair_idx;
-  const float4 *pair_coef;
+  const float *pair_rec;
   const TorInfo *tors;
   const uint8_t *moves;
   GridView grid;
@@ -124,7 +126,7 @@ struct Fp64Args {
 cudaError_t launch_grid_build_impl(const float4 *prot, const uint8_t *ptype, int n_prot,
                                    const dock_type_params *params_dev, int n_types, int n,
                                    double ox, double oy, double oz, double h, float4 *maps,
-                                   cudaStream_t s);
+                                   float2 *fpm, cudaStream_t s);
 cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int n_ligands, int pop,
@@ -136,6 +138,7 @@ cudaError_t launch_score_fp64_impl(const Fp64Args &f, const double *centroids, d
                                    double oz, const int32_t *pose_ligand, int n_ligands,
                                    const float *genos, int64_t n_poses, double *out, cudaStream_t s);
 int search_smem_bytes(int threads, int atoms_per_lane);
-cudaError_t launch_pair_maps(const float4 *maps, int n_types, int n, float *pairs, cudaStream_t s);
+cudaError_t launch_xycell_maps(const float4 *maps, const float2 *fpm, int n_types, int n,
+                               float *xycell, cudaStream_t s);
 
 }  // namespace dk

@@ -31,6 +31,7 @@ struct GridBuildArgs {
   int n;
   double ox, oy, oz, h;
   float4 *maps;
+  float2 *fpm;   // per node {E + D, E - D}, rounded once from FP64
 };
 
 __global__ void __launch_bounds__(256) grid_build_kernel(const GridBuildArgs A) {
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(256) grid_build_kernel(const GridBuildArgs A) 
     }
   }
   if (!active) return;
+  A.fpm[node] = make_float2((float)(E + D), (float)(E - D));
 #pragma unroll
   for (int t = 0; t < DOCK_MAX_TYPES; ++t) {
     if (t < T) {
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(256) grid_build_kernel(const GridBuildArgs A) 
 cudaError_t launch_grid_build_impl(const float4 *prot, const uint8_t *ptype, int n_prot,
                                    const dock_type_params *params_dev, int n_types, int n,
                                    double ox, double oy, double oz, double h, float4 *maps,
-                                   cudaStream_t s) {
+                                   float2 *fpm, cudaStream_t s) {
   GridBuildArgs A;
   A.prot = prot;
   A.ptype = ptype;
@@ -121,29 +123,41 @@ cudaError_t launch_grid_build_impl(const float4 *prot, const uint8_t *ptype, int
   A.n = n;
   A.ox = ox; A.oy = oy; A.oz = oz; A.h = h;
   A.maps = maps;
+  A.fpm = fpm;
   const int64_t nn = (int64_t)n * n * n;
   const int threads = 256;
   grid_build_kernel<<<(unsigned)((nn + threads - 1) / threads), threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 
-// x-cell records for the FP32 scorer: cell (x, y, z) of type t holds
-// {M(x), E(x), D(x), M(x+1), E(x+1), D(x+1), 0, 0}.
-__global__ void pair_maps_kernel(const float4 *maps, int n_types, int n, float *pairs) {
-  const int64_t nx = n - 1;
-  const int64_t total = (int64_t)n_types * n * n * nx;
+// (x, y)-cell records for the FP32 scorer: record (t, sign, z, y, x) holds
+// {M_t, F} at (x, y), (x+1, y), (x, y+1), (x+1, y+1); F = E + D for sign 0 and
+// E - D for sign 1.
+__global__ void xycell_maps_kernel(const float4 *maps, const float2 *fpm, int n_types, int n,
+                                   float *xycell) {
+  const int64_t nc = n - 1, plane = (int64_t)nc * nc, vol = (int64_t)n * n * n;
+  const int64_t total = (int64_t)n_types * 2 * n * plane;
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ix = c % nx, row = c / nx;  // row = (t * n + z) * n + y
-    const float4 a = maps[row * n + ix], b = maps[row * n + ix + 1];
-    float4 *o = reinterpret_cast<float4 *>(pairs + c * 8);
-    o[0] = make_float4(a.x, a.y, a.z, b.x);
-    o[1] = make_float4(b.y, b.z, 0.0f, 0.0f);
+    const int64_t ix = c % nc, iy = (c / nc) % nc, iz = (c / plane) % n, tsg = c / (plane * n);
+    const int t = (int)(tsg >> 1), sg = (int)(tsg & 1);
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t node = (iz * n + iy + (k >> 1)) * n + ix + (k & 1);
+      const float2 f = fpm[node];
+      v[2 * k] = maps[(int64_t)t * vol + node].x;
+      v[2 * k + 1] = sg ? f.y : f.x;
+    }
+    float4 *o = reinterpret_cast<float4 *>(xycell + c * 8);
+    o[0] = make_float4(v[0], v[1], v[2], v[3]);
+    o[1] = make_float4(v[4], v[5], v[6], v[7]);
   }
 }
 
-cudaError_t launch_pair_maps(const float4 *maps, int n_types, int n, float *pairs, cudaStream_t s) {
-  pair_maps_kernel<<<152 * 8, 256, 0, s>>>(maps, n_types, n, pairs);
+cudaError_t launch_xycell_maps(const float4 *maps, const float2 *fpm, int n_types, int n,
+                               float *xycell, cudaStream_t s) {
+  xycell_maps_kernel<<<152 * 8, 256, 0, s>>>(maps, fpm, n_types, n, xycell);
   return cudaGetLastError();
 }
 
