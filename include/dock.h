@@ -212,6 +212,42 @@ int dock_score(dock_pocket *pocket, dock_ligands *ligands, const int32_t *pose_l
                const float *genotypes, int64_t n_poses, float *scores, double *scores64,
                float *coords, int32_t fp64, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Search without device allocation                                          */
+/* ------------------------------------------------------------------------ */
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * allocate GPU memory while they run: code whose device memory belongs to
+ * another framework's pool, or that runs under a rule forbidding
+ * cudaMalloc/cudaFree after start-up (every other search call here allocates
+ * its working buffers on first use). dock_batch_noalloc runs the same plain
+ * search as dock_batch (same kernels, same genotypes and scores for the same
+ * seed; work items are queued in input order instead of largest first, and
+ * no CUDA graph is used) and writes one dock_result per ligand to `results`,
+ * a caller-owned device buffer of n_ligands records. All its working buffers
+ * (populations, scores, per-generation best keys, queue counters, work
+ * items, status words) live in one fixed device array of
+ * DOCK_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ * the library holds until the process exits. The call allocates nothing:
+ * no cudaMalloc, cudaFree, host heap or allocating library routine.
+ *  - Limits: at most DOCK_NOALLOC_MAX_LIGANDS ligands, and the search's
+ *    buffers (about 8 bytes per gene of the population, 8 per pose score
+ *    and 8 per ligand and generation) must fit the array; larger requests
+ *    return DOCK_EINVAL with the bytes needed in dock_last_error().
+ *    lanes_per_pose must be 0; use_graph is ignored.
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call shares the array and leaves its contents behind (each call
+ *    clears what must start at zero). Calls that overlap on the GPU (other
+ *    streams, other host threads) race on it: serialise them.
+ *  - Asynchronous on stream: synchronise it before reading `results`. A
+ *    device deadline (timeout_ns) shows as status DOCK_ETIMEOUT in the
+ *    result records.
+ * Errors: DOCK_EINVAL, DOCK_ECUDA. */
+#define DOCK_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+#define DOCK_NOALLOC_MAX_LIGANDS 64
+int dock_batch_noalloc(dock_pocket *pocket, dock_ligands *ligands, const dock_search_params *params,
+                       dock_result *results, void *stream);
+
 /* Profiling aid: device time of the search-kernel launches of a job enqueued
  * while the environment variable DOCK_PROFILE_LAUNCHES was set (CUDA events
  * around each generation's launch on the job's stream; no graph). Waits for

@@ -14,26 +14,28 @@
 #include <vector>
 
 #include "dock_internal.h"
+#include "handles.h"
 
-namespace dk {
-cudaError_t search_occupancy(int threads, int smem, int *blocks_per_sm);
-cudaError_t launch_set_deadline(uint64_t *deadline, uint64_t timeout_ns, cudaStream_t s);
-}  // namespace dk
 
 using namespace dk;
 
 // ---------------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------------
-static thread_local std::string g_err;
+// Message of the last failed call on this thread (fixed storage: recording an
+// error allocates nothing).
+static thread_local char g_err[512];
+
+int dk::vset_error(int st, const char *fmt, va_list ap) {
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  return st;
+}
 
 static int fail(int st, const char *fmt, ...) {
-  char buf[512];
   va_list ap;
   va_start(ap, fmt);
-  vsnprintf(buf, sizeof buf, fmt, ap);
+  vset_error(st, fmt, ap);
   va_end(ap);
-  g_err = buf;
   return st;
 }
 
@@ -46,24 +48,12 @@ static int fail(int st, const char *fmt, ...) {
     }                                                                                \
   } while (0)
 
-extern "C" const char *dock_last_error(void) { return g_err.c_str(); }
+extern "C" const char *dock_last_error(void) { return g_err; }
 
 extern "C" const char *dock_version(void) {
   return "gb300-dock 0.1 (sm_103a, Philox4x64-10 GA, FP32 Kahan scoring, FP64 rescoring)";
 }
 
-template <typename T>
-static cudaError_t dalloc(T **p, size_t count) {
-  *p = nullptr;
-  if (count == 0) count = 1;
-  return cudaMalloc((void **)p, count * sizeof(T));
-}
-
-template <typename T>
-static void dfree(T *&p) {
-  if (p) cudaFree((void *)p);
-  p = nullptr;
-}
 
 // AutoDock4 free-energy constants for the host-side pair coefficients.
 static const double kHWVdw = 0.1662, kHWHb = 0.1209, kHWElec = 0.1406, kHWSol = 0.1322;
@@ -72,43 +62,7 @@ static const double kHCoulomb = 332.06363, kHQasp = 0.01097, kHEmax = 1.0e5;
 // ---------------------------------------------------------------------------
 // pocket
 // ---------------------------------------------------------------------------
-struct dock_pocket {
-  int device = 0;
-  int n_types = 0;
-  std::vector<dock_type_params> params;
-  dock_type_params *d_params = nullptr;
-  float4 *d_prot = nullptr;
-  uint8_t *d_ptype = nullptr;
-  int n_prot = 0;
-  float4 *d_maps = nullptr;
-  float *d_xycell = nullptr;  // (x, y)-cell records of the FP32 scorer
-  float2 *d_fpm = nullptr;    // per node {E + D, E - D}
-  int n = 0;
-  double ox = 0, oy = 0, oz = 0, h = 0;
-  float center[3] = {0, 0, 0};
-  float radius = 0;
-  ~dock_pocket() {
-    dfree(d_params);
-    dfree(d_prot);
-    dfree(d_ptype);
-    dfree(d_maps);
-    dfree(d_xycell);
-    dfree(d_fpm);
-  }
-};
 
-static GridView grid_view(const dock_pocket *p) {
-  GridView g;
-  g.maps = p->d_maps;
-  g.xycell = p->d_xycell;
-  g.n = p->n;
-  g.ox = (float)p->ox;
-  g.oy = (float)p->oy;
-  g.oz = (float)p->oz;
-  g.inv_h = (float)(1.0 / p->h);
-  g.n_types = p->n_types;
-  return g;
-}
 
 extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_pocket **out) {
   if (!d || !out) return fail(DOCK_EINVAL, "dock_create_pocket: NULL argument");
@@ -188,66 +142,7 @@ extern "C" int dock_pocket_grid(const dock_pocket *p, int32_t *n, float origin[3
 // ---------------------------------------------------------------------------
 // ligands
 // ---------------------------------------------------------------------------
-struct Workspace {
-  size_t geno_cap = 0, score_cap = 0, best_cap = 0, item_cap = 0, gen_cap = 0, lig_cap = 0;
-  float *geno[2] = {nullptr, nullptr};
-  float *score[2] = {nullptr, nullptr};
-  unsigned long long *best = nullptr;  // [generations][n_ligands]
-  uint32_t *counters = nullptr;        // [generations]
-  Item *items = nullptr;
-  int64_t *geno_off = nullptr;
-  int32_t *status = nullptr;           // [1] + deadline slot
-  uint64_t *deadline = nullptr;
-  int32_t *lig_status = nullptr;
-  dock_result *results = nullptr;
-  // cached graph
-  cudaGraphExec_t graph = nullptr;
-  std::vector<uint8_t> graph_key;
-  ~Workspace() {
-    for (int i = 0; i < 2; ++i) {
-      dfree(geno[i]);
-      dfree(score[i]);
-    }
-    dfree(best);
-    dfree(counters);
-    dfree(items);
-    dfree(geno_off);
-    dfree(status);
-    dfree(deadline);
-    dfree(lig_status);
-    dfree(results);
-    if (graph) cudaGraphExecDestroy(graph);
-  }
-};
 
-struct dock_ligands {
-  int device = 0;
-  int n_ligands = 0;
-  int max_atoms = 0;
-  std::vector<LigInfo> info;
-  LigInfo *d_info = nullptr;
-  float4 *d_atoms = nullptr;      // centred
-  float4 *d_atoms_raw = nullptr;  // input coordinates
-  double *d_centroid = nullptr;
-  uint8_t *d_types = nullptr;
-  uint32_t *d_pair_idx = nullptr;
-  float *d_pair_rec = nullptr;
-  TorInfo *d_tors = nullptr;
-  uint8_t *d_moves = nullptr;
-  int64_t total_pairs = 0, total_atoms = 0, total_tors = 0, total_moved = 0, h2d_bytes = 0;
-  Workspace ws;
-  ~dock_ligands() {
-    dfree(d_info);
-    dfree(d_atoms);
-    dfree(d_atoms_raw);
-    dfree(d_centroid);
-    dfree(d_types);
-    dfree(d_pair_idx);
-    dfree(d_pair_rec);
-    dfree(d_tors);
-    dfree(d_moves);
-  }
-};
 
 namespace {
 struct LigHost {
@@ -535,12 +430,6 @@ struct dock_job {
   }
 };
 
-static uint64_t prob_threshold(float p) {
-  double t = (double)p * 4294967296.0;
-  if (!(t > 0)) t = 0;
-  if (t > 4294967296.0) t = 4294967296.0;
-  return (uint64_t)t;
-}
 
 // Launch configuration of the search kernel: threads per CTA and the smem
 // capacity in atoms per lane; a ligand of n atoms runs with the smallest
@@ -550,12 +439,6 @@ struct LaunchCfg {
   int atoms_per_lane = 16;
 };
 
-static int lanes_for(int n, int apl, int forced) {
-  if (forced) return forced;
-  int L = 1;
-  while (L * apl < n && L < 8) L <<= 1;
-  return L;
-}
 
 extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_params *sp, void *stream,
                           dock_job **out) {

@@ -1,0 +1,148 @@
+// Library-internal definitions of the opaque handles of include/dock.h and
+// small host helpers shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "dock_internal.h"
+
+namespace dk {
+// Records the message returned by dock_last_error() for this thread; returns st.
+int vset_error(int st, const char *fmt, va_list ap);
+cudaError_t search_occupancy(int threads, int smem, int *blocks_per_sm);
+cudaError_t launch_set_deadline(uint64_t *deadline, uint64_t timeout_ns, cudaStream_t s);
+}  // namespace dk
+
+using namespace dk;
+
+template <typename T>
+inline cudaError_t dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+template <typename T>
+inline void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+struct dock_pocket {
+  int device = 0;
+  int n_types = 0;
+  std::vector<dock_type_params> params;
+  dock_type_params *d_params = nullptr;
+  float4 *d_prot = nullptr;
+  uint8_t *d_ptype = nullptr;
+  int n_prot = 0;
+  float4 *d_maps = nullptr;
+  float *d_xycell = nullptr;  // (x, y)-cell records of the FP32 scorer
+  float2 *d_fpm = nullptr;    // per node {E + D, E - D}
+  int n = 0;
+  double ox = 0, oy = 0, oz = 0, h = 0;
+  float center[3] = {0, 0, 0};
+  float radius = 0;
+  ~dock_pocket() {
+    dfree(d_params);
+    dfree(d_prot);
+    dfree(d_ptype);
+    dfree(d_maps);
+    dfree(d_xycell);
+    dfree(d_fpm);
+  }
+};
+
+inline GridView grid_view(const dock_pocket *p) {
+  GridView g;
+  g.maps = p->d_maps;
+  g.xycell = p->d_xycell;
+  g.n = p->n;
+  g.ox = (float)p->ox;
+  g.oy = (float)p->oy;
+  g.oz = (float)p->oz;
+  g.inv_h = (float)(1.0 / p->h);
+  g.n_types = p->n_types;
+  return g;
+}
+
+struct Workspace {
+  size_t geno_cap = 0, score_cap = 0, best_cap = 0, item_cap = 0, gen_cap = 0, lig_cap = 0;
+  float *geno[2] = {nullptr, nullptr};
+  float *score[2] = {nullptr, nullptr};
+  unsigned long long *best = nullptr;  // [generations][n_ligands]
+  uint32_t *counters = nullptr;        // [generations]
+  Item *items = nullptr;
+  int64_t *geno_off = nullptr;
+  int32_t *status = nullptr;           // [1] + deadline slot
+  uint64_t *deadline = nullptr;
+  int32_t *lig_status = nullptr;
+  dock_result *results = nullptr;
+  // cached graph
+  cudaGraphExec_t graph = nullptr;
+  std::vector<uint8_t> graph_key;
+  ~Workspace() {
+    for (int i = 0; i < 2; ++i) {
+      dfree(geno[i]);
+      dfree(score[i]);
+    }
+    dfree(best);
+    dfree(counters);
+    dfree(items);
+    dfree(geno_off);
+    dfree(status);
+    dfree(deadline);
+    dfree(lig_status);
+    dfree(results);
+    if (graph) cudaGraphExecDestroy(graph);
+  }
+};
+
+struct dock_ligands {
+  int device = 0;
+  int n_ligands = 0;
+  int max_atoms = 0;
+  std::vector<LigInfo> info;
+  LigInfo *d_info = nullptr;
+  float4 *d_atoms = nullptr;      // centred
+  float4 *d_atoms_raw = nullptr;  // input coordinates
+  double *d_centroid = nullptr;
+  uint8_t *d_types = nullptr;
+  uint32_t *d_pair_idx = nullptr;
+  float *d_pair_rec = nullptr;
+  TorInfo *d_tors = nullptr;
+  uint8_t *d_moves = nullptr;
+  int64_t total_pairs = 0, total_atoms = 0, total_tors = 0, total_moved = 0, h2d_bytes = 0;
+  Workspace ws;
+  ~dock_ligands() {
+    dfree(d_info);
+    dfree(d_atoms);
+    dfree(d_atoms_raw);
+    dfree(d_centroid);
+    dfree(d_types);
+    dfree(d_pair_idx);
+    dfree(d_pair_rec);
+    dfree(d_tors);
+    dfree(d_moves);
+  }
+};
+
+inline uint64_t prob_threshold(float p) {
+  double t = (double)p * 4294967296.0;
+  if (!(t > 0)) t = 0;
+  if (t > 4294967296.0) t = 4294967296.0;
+  return (uint64_t)t;
+}
+
+// Lanes per pose of an n-atom ligand: the smallest L in {1, 2, 4, 8} with
+// L * atoms_per_lane >= n (or the forced value).
+inline int lanes_for(int n, int apl, int forced) {
+  if (forced) return forced;
+  int L = 1;
+  while (L * apl < n && L < 8) L <<= 1;
+  return L;
+}

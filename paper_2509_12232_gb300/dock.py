@@ -102,9 +102,10 @@ def lib():
         L.dock_score.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp, vp, C.c_int32, vp]
         P_i64 = C.POINTER(C.c_int64)
         L.dock_ligands_info.argtypes = [vp, P_i32, P_i64, P_i64, P_i64, P_i64, P_i64]
+        L.dock_batch_noalloc.argtypes = [vp, vp, C.POINTER(dock_search_params), vp, vp]
         for name in ("dock_create_pocket", "dock_pocket_grid", "dock_load_ligands", "dock_batch",
                      "dock_results", "dock_job_population", "dock_job_kernel_time", "dock_score",
-                     "dock_ligands_info"):
+                     "dock_ligands_info", "dock_batch_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -262,6 +263,19 @@ def dock_batch(pocket: Pocket, ligands: Ligands, pop: int, generations: int, p_c
     h = C.c_void_p()
     check(lib().dock_batch(pocket.handle, ligands.handle, C.byref(sp), _stream(stream), C.byref(h)))
     return Job(h, ligands.n_ligands, keep=(pocket, ligands))
+
+
+def dock_batch_noalloc(pocket: Pocket, ligands: Ligands, results, pop: int, generations: int,
+                       p_cross=0.8, p_mut=0.02, seed=0, timeout_ns=0, trace_genotypes=None,
+                       trace_scores=None, stream=None):
+    """The plain search with no device allocation: working buffers live in the
+    library's fixed scratch array; `results` is a caller-owned device buffer
+    of n_ligands dock_result records (RESULT_DTYPE.itemsize bytes each).
+    Asynchronous on stream."""
+    sp = dock_search_params(pop, generations, p_cross, p_mut, seed, 0, 0, timeout_ns,
+                            _dptr(trace_genotypes), _dptr(trace_scores))
+    check(lib().dock_batch_noalloc(pocket.handle, ligands.handle, C.byref(sp), _dptr(results),
+                                   _stream(stream)))
 
 
 def dock_results(job: Job, cap: int | None = None, timeout_ns: int = 0) -> np.ndarray:
