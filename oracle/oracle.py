@@ -145,11 +145,13 @@ def _declare(L):
 
 def _declare_surrogate(L):
     L.orc_features.restype = None
-    L.orc_features.argtypes = [C.POINTER(OrcLigand), P_d, P_d, P_f, P_d, C.c_double, P_d]
+    L.orc_features.argtypes = [C.POINTER(OrcLigand), P_d, P_d, P_f, C.c_double, P_d]
     L.orc_mlp_forward.restype = None
-    L.orc_mlp_forward.argtypes = [P_d, C.c_int, P_d, P_d, P_d]
-    L.orc_mlp_backward.restype = None
-    L.orc_mlp_backward.argtypes = [P_d, C.c_int, P_d, P_d, P_d, P_d]
+    L.orc_mlp_forward.argtypes = [P_d, C.c_int, P_d, P_d]
+    L.orc_mlp_backward.restype = C.c_double
+    L.orc_mlp_backward.argtypes = [P_d, C.c_int, P_d, P_d, P_d]
+    L.orc_mlp_n_params.restype = C.c_int
+    L.orc_mlp_n_params.argtypes = []
 
 
 def _p(a, t):
@@ -406,3 +408,65 @@ def dock_batch(ligs, params: Params, pocket: PocketS, grid: Grid, pop: int, gene
                          C.byref(s), nt, _p(geno, P_f), _p(score, P_f), _p(best64, P_d),
                          _p(best_idx, P_i32))
     return dict(geno=geno, score=score, best64=best64, best_idx=best_idx, threads=nt)
+
+
+# ---------------------------------------------------------------------------
+# Surrogate (features, MLP): oracle/surrogate.c
+# ---------------------------------------------------------------------------
+N_FEATURES, N_HIDDEN = 128, 256
+
+
+def to_bf16(a) -> np.ndarray:
+    """Round to bfloat16 (round to nearest even, via float32) and return the
+    values as float64: float64 -> float32 (RN) -> bfloat16 (RNE)."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> np.uint64(16)) & np.uint64(1)
+    r = ((u + np.uint64(0x7FFF) + lsb) >> np.uint64(16)) << np.uint64(16)
+    nan = np.isnan(f)
+    out = r.astype(np.uint32).view(np.float32).astype(np.float64)
+    out[nan] = np.nan
+    return out
+
+
+def features(lig: Ligand, xyz, center, geno, radius) -> np.ndarray:
+    """FP64 features of one posed ligand (before any rounding)."""
+    x = _c(xyz, np.float64)
+    c = _c(center, np.float64)
+    g = _c(geno, np.float32)
+    f = np.zeros(N_FEATURES, np.float64)
+    lib().orc_features(C.byref(lig.s), _p(x, P_d), _p(c, P_d), _p(g, P_f), float(radius), _p(f, P_d))
+    return f
+
+
+def mlp_n_params() -> int:
+    return lib().orc_mlp_n_params()
+
+
+def mlp_unpack(p):
+    """Split packed parameters into (W1, b1, W2, b2, W3, b3, W4, b4)."""
+    F, H = N_FEATURES, N_HIDDEN
+    sizes = [(F, H), (H,), (H, H), (H,), (H, H), (H,), (H,), (1,)]
+    out, o = [], 0
+    for sh in sizes:
+        n = int(np.prod(sh))
+        out.append(np.asarray(p[o:o + n]).reshape(sh))
+        o += n
+    return out
+
+
+def mlp_forward(params, X) -> np.ndarray:
+    p = _c(params, np.float64)
+    X = _c(X, np.float64).reshape(-1, N_FEATURES)
+    Y = np.zeros(X.shape[0], np.float64)
+    lib().orc_mlp_forward(_p(p, P_d), X.shape[0], _p(X, P_d), _p(Y, P_d))
+    return Y
+
+
+def mlp_backward(params, X, T):
+    p = _c(params, np.float64)
+    X = _c(X, np.float64).reshape(-1, N_FEATURES)
+    T = _c(T, np.float64)
+    g = np.zeros_like(p)
+    loss = lib().orc_mlp_backward(_p(p, P_d), X.shape[0], _p(X, P_d), _p(T, P_d), _p(g, P_d))
+    return loss, g
