@@ -144,6 +144,8 @@ int dock_ligands_info(const dock_ligands *ligands, int32_t *n_ligands, int64_t *
 /* ------------------------------------------------------------------------ */
 /* Search (Section V: GA without local search; fitness = score)               */
 /* ------------------------------------------------------------------------ */
+typedef struct dock_surrogate dock_surrogate;
+
 typedef struct {
   int32_t pop;                   /* individuals per ligand, 2..DOCK_MAX_POP     */
   int32_t generations;           /* scoring passes, >= 1 (generation 0 = init)  */
@@ -160,7 +162,18 @@ typedef struct {
   float *trace_genotypes;        /* optional device [generations][total genes]:
                                     every generation's population              */
   float *trace_scores;           /* optional device [generations][n_ligands*pop]*/
+  int32_t mode;                  /* DOCK_MODE_PLAIN or DOCK_MODE_SURROGATE        */
+  int32_t candidates;            /* surrogate: candidates per ligand and
+                                    generation, <= DOCK_MAX_CANDIDATES           */
+  int32_t keep;                  /* surrogate: candidates kept for exact scoring
+                                    (1..candidates), merged (mu + lambda) with the
+                                    population by exact score                   */
+  dock_surrogate *surrogate;     /* surrogate: the trained network                */
 } dock_search_params;
+
+#define DOCK_MODE_PLAIN 0
+#define DOCK_MODE_SURROGATE 1
+#define DOCK_MAX_CANDIDATES 8192
 
 typedef struct dock_job dock_job;
 
@@ -171,6 +184,12 @@ typedef struct dock_job dock_job;
  * generation the best DOCK_N_BEST individuals of each ligand are re-posed and
  * rescored in FP64. The pocket and ligands must outlive the job.
  * Errors: DOCK_EINVAL, DOCK_ENOMEM, DOCK_ECUDA. */
+/* With mode = DOCK_MODE_SURROGATE each generation after the first draws
+ * `candidates` children per ligand by the same GA operators, ranks them by the
+ * surrogate's predicted score from their features, scores the best `keep`
+ * exactly (FP32) and keeps the best pop of population and kept candidates by
+ * exact score (ties: population first, then index); every reported score is
+ * exact. */
 int dock_batch(dock_pocket *pocket, dock_ligands *ligands, const dock_search_params *params,
                void *stream, dock_job **out);
 
@@ -247,6 +266,75 @@ int dock_score(dock_pocket *pocket, dock_ligands *ligands, const int32_t *pose_l
 #define DOCK_NOALLOC_MAX_LIGANDS 64
 int dock_batch_noalloc(dock_pocket *pocket, dock_ligands *ligands, const dock_search_params *params,
                        dock_result *results, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Learned pre-screen (not in the paper: the build's surrogate configuration) */
+/* ------------------------------------------------------------------------ */
+/* Per-pose features (128 values, BF16, row-major [pose][128]):
+ *   [0, 56)    atom counts / 8 per (type t < 7, radial shell s < 8) around the
+ *              pocket centre, shell width R/8 (last shell open): 8 t + s
+ *   [56, 64)   sum of charges per shell; [64, 72) sum of |charge| per shell
+ *   [72, 104)  sin, cos of torsion j at 72 + 2j, 73 + 2j (0 for j >= k)
+ *   [104, 113) rotation matrix of the quaternion, row-major
+ *   [113, 116) translation gene / R; 116: n / 100; 117: k / 16; rest 0.
+ * Values are computed in FP32 and rounded to BF16 (round to nearest even).
+ * The network is MLP 128 -> 256 -> 256 -> 256 -> 1 with GELU (erf form):
+ * BF16 weights and activations, FP32 accumulation on the tensor cores, FP32
+ * master weights; parameters packed as W1[128][256], b1[256], W2[256][256],
+ * b2[256], W3[256][256], b3[256], W4[256], b4 (W stored [in][out]). */
+#define DOCK_N_FEATURES 128
+#define DOCK_MLP_N_PARAMS 164865
+
+/* Poses the given genotypes (same layout as dock_score) and writes their
+ * features (device BF16 [n_poses][128], as uint16_t) and, when scores is not
+ * NULL, their exact FP32 scores. Asynchronous on stream.
+ * Errors: DOCK_EINVAL (NULL buffers, pocket with more than 7 types), DOCK_ECUDA. */
+int dock_features(dock_pocket *pocket, dock_ligands *ligands, const int32_t *pose_ligand,
+                  const float *genotypes, int64_t n_poses, uint16_t *features, float *scores,
+                  void *stream);
+
+/* The same for whole populations in the search's genotype layout
+ * (dock_batch's trace or population buffers: ligand l, individual i at
+ * geno_off[l] + i * G_l for the given pop): row r = ligand r / pop,
+ * individual r % pop; features [n_ligands * pop][128], scores optional.
+ * Synchronises stream before returning. */
+int dock_features_population(dock_pocket *pocket, dock_ligands *ligands, int32_t pop,
+                             const float *genotypes, uint16_t *features, float *scores,
+                             void *stream);
+
+typedef struct {
+  int32_t epochs;      /* passes over the training set                        */
+  int32_t batch;       /* rows per step, a multiple of 128, <= 65536 (4096)    */
+  float lr;            /* Adam learning rate (1e-3); beta 0.9 / 0.999, eps 1e-8 */
+  float score_clip;    /* targets are min(score, clip), standardised by their
+                          mean and standard deviation over the training set    */
+  uint64_t seed;       /* order of the rows                                   */
+} dock_train_params;
+
+/* Creates a network with He-normal weights drawn from seed and zero biases. */
+int dock_surrogate_create(uint64_t seed, void *stream, dock_surrogate **out);
+void dock_surrogate_destroy(dock_surrogate *surrogate);
+/* Host copies of the FP32 master parameters (DOCK_MLP_N_PARAMS) and of the
+ * target standardisation (prediction = output * t_std + t_mean). */
+int dock_surrogate_set_params(dock_surrogate *surrogate, const float *params, float t_mean,
+                              float t_std, float t_clip, void *stream);
+int dock_surrogate_get_params(const dock_surrogate *surrogate, float *params, float *t_mean,
+                              float *t_std, float *t_clip);
+/* Predicted scores (device FP32 [n]) of device BF16 features [n][128]. */
+int dock_surrogate_predict(dock_surrogate *surrogate, const uint16_t *features, int64_t n,
+                           float *out, void *stream);
+/* Gradient (device FP32, packed like the parameters) of
+ * mean over n rows of (output - target)^2, targets used as given; n <= 65536.
+ * *loss (host, optional) receives the loss; waits for the stream. */
+int dock_surrogate_gradients(dock_surrogate *surrogate, const uint16_t *features,
+                             const float *targets, int32_t n, float *grad, float *loss,
+                             void *stream);
+/* Trains with Adam on (features [n][128] BF16, exact scores [n]) device
+ * arrays; loss_per_epoch (host, optional, [epochs]) gets the loss of each
+ * epoch's last batch in standardised units. Waits for the stream. */
+int dock_surrogate_train(dock_surrogate *surrogate, const uint16_t *features,
+                         const float *scores, int64_t n, const dock_train_params *params,
+                         float *loss_per_epoch, void *stream);
 
 /* Profiling aid: device time of the search-kernel launches of a job enqueued
  * while the environment variable DOCK_PROFILE_LAUNCHES was set (CUDA events

@@ -580,50 +580,70 @@ static int gene_block(int g) { return g < 3 ? g : (g < 7 ? 3 : g - 3); }
  * (elitism 1); individual i >= 1 = tournament(2) winners A, B -> two-point
  * crossover on blocks with probability p_cross -> per-gene mutation with
  * probability p_mut, adding sigma * N(0,1) (1 A, 0.1, 0.5 rad). */
+/* Child `ind` of the population `prev` (scores `score`): tournaments A, B,
+ * crossover, mutation, as described above. */
+static void ga_child_one(int k, int P, uint64_t tc, uint64_t tm, uint64_t seed, uint64_t lig,
+                         uint32_t gen, uint32_t ind, const float *prev, const float *score,
+                         float *c) {
+  int G = 7 + k, B = 4 + k;
+  uint32_t w[8];
+  orc_rng_words(seed, lig, gen, ind, 0, w);
+  int a1 = (int)(((uint64_t)w[0] * (uint64_t)P) >> 32), a2 = (int)(((uint64_t)w[1] * (uint64_t)P) >> 32);
+  int b1 = (int)(((uint64_t)w[2] * (uint64_t)P) >> 32), b2 = (int)(((uint64_t)w[3] * (uint64_t)P) >> 32);
+  int pa = better(score, a1, a2) ? a1 : a2;
+  int pb = better(score, b1, b2) ? b1 : b2;
+  int lo = 0, hi = 0;
+  if ((uint64_t)w[4] < tc) {
+    int c1 = (int)(((uint64_t)w[5] * (uint64_t)(B + 1)) >> 32);
+    int c2 = (int)(((uint64_t)w[6] * (uint64_t)(B + 1)) >> 32);
+    lo = c1 < c2 ? c1 : c2;
+    hi = c1 < c2 ? c2 : c1;
+  }
+  for (int g = 0; g < G; ++g) {
+    int blk = gene_block(g);
+    c[g] = (blk >= lo && blk < hi) ? prev[(size_t)pb * G + g] : prev[(size_t)pa * G + g];
+  }
+  int qmut = 0;
+  for (int g = 0; g < G; ++g) {
+    uint32_t m[8];
+    orc_rng_words(seed, lig, gen, ind, 1 + g / 8, m);
+    if ((uint64_t)m[g % 8] >= tm) continue;
+    float z = orc_normal(seed, lig, gen, ind, 4 + 2 * g);
+    float sigma = g < 3 ? 1.0f : (g < 7 ? 0.1f : 0.5f);
+    float d = sigma * z;
+    c[g] = c[g] + d;
+    if (g >= 3 && g < 7) qmut = 1;
+    if (g >= 7) {
+      if (c[g] > PI_F) c[g] = c[g] - TWO_PI_F;
+      else if (c[g] < -PI_F) c[g] = c[g] + TWO_PI_F;
+    }
+  }
+  if (qmut) quat_normalize(c + 3);
+}
+
+/* One generation: individual 0 is the best of the previous generation
+ * (elitism 1); individual i >= 1 = tournament(2) winners A, B -> two-point
+ * crossover on blocks with probability p_cross -> per-gene mutation with
+ * probability p_mut, adding sigma * N(0,1) (1 A, 0.1, 0.5 rad). */
 void orc_ga_step(int k, int P, float p_cross, float p_mut, uint64_t seed, uint64_t lig,
                  uint32_t gen, const float *prev, const float *score, float *next) {
-  int G = 7 + k, B = 4 + k;
+  int G = 7 + k;
   uint64_t tc = prob_threshold(p_cross), tm = prob_threshold(p_mut);
   int best = 0;
   for (int i = 1; i < P; ++i)
     if (better(score, i, best)) best = i;
   memcpy(next, prev + (size_t)best * G, sizeof(float) * G);
-  for (int i = 1; i < P; ++i) {
-    uint32_t w[8];
-    orc_rng_words(seed, lig, gen, (uint32_t)i, 0, w);
-    int a1 = (int)(((uint64_t)w[0] * (uint64_t)P) >> 32), a2 = (int)(((uint64_t)w[1] * (uint64_t)P) >> 32);
-    int b1 = (int)(((uint64_t)w[2] * (uint64_t)P) >> 32), b2 = (int)(((uint64_t)w[3] * (uint64_t)P) >> 32);
-    int pa = better(score, a1, a2) ? a1 : a2;
-    int pb = better(score, b1, b2) ? b1 : b2;
-    int lo = 0, hi = 0;
-    if ((uint64_t)w[4] < tc) {
-      int c1 = (int)(((uint64_t)w[5] * (uint64_t)(B + 1)) >> 32);
-      int c2 = (int)(((uint64_t)w[6] * (uint64_t)(B + 1)) >> 32);
-      lo = c1 < c2 ? c1 : c2;
-      hi = c1 < c2 ? c2 : c1;
-    }
-    float *c = next + (size_t)i * G;
-    for (int g = 0; g < G; ++g) {
-      int blk = gene_block(g);
-      c[g] = (blk >= lo && blk < hi) ? prev[(size_t)pb * G + g] : prev[(size_t)pa * G + g];
-    }
-    int qmut = 0;
-    for (int g = 0; g < G; ++g) {
-      uint32_t m[8];
-      orc_rng_words(seed, lig, gen, (uint32_t)i, 1 + g / 8, m);
-      if ((uint64_t)m[g % 8] >= tm) continue;
-      float z = orc_normal(seed, lig, gen, (uint32_t)i, 4 + 2 * g);
-      float sigma = g < 3 ? 1.0f : (g < 7 ? 0.1f : 0.5f);
-      float d = sigma * z;
-      c[g] = c[g] + d;
-      if (g >= 3 && g < 7) qmut = 1;
-      if (g >= 7) {
-        if (c[g] > PI_F) c[g] = c[g] - TWO_PI_F;
-        else if (c[g] < -PI_F) c[g] = c[g] + TWO_PI_F;
-      }
-    }
-    if (qmut) quat_normalize(c + 3);
-  }
+  for (int i = 1; i < P; ++i)
+    ga_child_one(k, P, tc, tm, seed, lig, gen, (uint32_t)i, prev, score, next + (size_t)i * G);
+}
+
+/* n children 0..n-1 of a population (candidates of the pre-screened search;
+ * child c uses the counters of individual c). */
+void orc_ga_children(int k, int P, int n, float p_cross, float p_mut, uint64_t seed, uint64_t lig,
+                     uint32_t gen, const float *prev, const float *score, float *out) {
+  uint64_t tc = prob_threshold(p_cross), tm = prob_threshold(p_mut);
+  for (int c = 0; c < n; ++c)
+    ga_child_one(k, P, tc, tm, seed, lig, gen, (uint32_t)c, prev, score, out + (size_t)c * (7 + k));
 }
 
 /* ======================================================================= */

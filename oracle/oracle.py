@@ -135,6 +135,9 @@ def _declare(L):
     L.orc_ga_step.restype = None
     L.orc_ga_step.argtypes = [C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64, C.c_uint64,
                               C.c_uint32, P_f, P_f, P_f]
+    L.orc_ga_children.restype = None
+    L.orc_ga_children.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64,
+                                  C.c_uint64, C.c_uint32, P_f, P_f, P_f]
     L.orc_dock_batch.restype = None
     L.orc_dock_batch.argtypes = [C.POINTER(OrcBatch), C.POINTER(OrcParams), C.POINTER(OrcPocket),
                                  C.POINTER(OrcGrid), C.POINTER(OrcSearch), C.c_int, P_f, P_f, P_d,
@@ -384,6 +387,38 @@ def ga_step(k: int, pop: int, p_cross: float, p_mut: float, seed: int, lig_id: i
     lib().orc_ga_step(k, pop, p_cross, p_mut, seed, lig_id, gen, _p(prev, P_f), _p(sc, P_f),
                       _p(nxt, P_f))
     return nxt.reshape(pop, 7 + k)
+
+
+def ga_children(k: int, pop: int, n: int, p_cross: float, p_mut: float, seed: int, lig_id: int,
+                gen: int, prev, scores) -> np.ndarray:
+    prev = _c(prev, np.float32)
+    sc = _c(scores, np.float32)
+    out = np.zeros(n * (7 + k), np.float32)
+    lib().orc_ga_children(k, pop, n, p_cross, p_mut, seed, lig_id, gen, _p(prev, P_f), _p(sc, P_f),
+                          _p(out, P_f))
+    return out.reshape(n, 7 + k)
+
+
+def _order_key(scores):
+    """Sort key of FP32 scores: NaN counts as +inf (the GA's comparison)."""
+    s = np.asarray(scores, np.float32).astype(np.float64)
+    return np.where(np.isnan(s), np.inf, s)
+
+
+def topk(pred, keep: int) -> np.ndarray:
+    """Indices of the `keep` lowest predictions, ties by index."""
+    idx = np.arange(len(pred))
+    return np.lexsort((idx, _order_key(pred)))[:keep]
+
+
+def merge(pop_scores, kept_scores, pop: int):
+    """mu + lambda: (origin, index) of the best `pop` of population (origin 0)
+    and kept candidates (origin 1) by score, ties by origin then index."""
+    s = np.concatenate([_order_key(pop_scores), _order_key(kept_scores)])
+    origin = np.concatenate([np.zeros(len(pop_scores), int), np.ones(len(kept_scores), int)])
+    index = np.concatenate([np.arange(len(pop_scores)), np.arange(len(kept_scores))])
+    order = np.lexsort((index, origin, s))[:pop]
+    return origin[order], index[order]
 
 
 def dock_batch(ligs, params: Params, pocket: PocketS, grid: Grid, pop: int, generations: int,

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "dock_internal.h"
+#include "surrogate_kernels.h"
 #include "handles.h"
 
 
@@ -448,6 +449,12 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   if (sp->generations < 1) return fail(DOCK_EINVAL, "dock_batch: generations %d", sp->generations);
   if (!(sp->p_cross >= 0 && sp->p_cross <= 1 && sp->p_mut >= 0 && sp->p_mut <= 1))
     return fail(DOCK_EINVAL, "dock_batch: probabilities out of [0, 1]");
+  const bool sur = sp->mode == DOCK_MODE_SURROGATE;
+  if (sp->mode != DOCK_MODE_PLAIN && !sur) return fail(DOCK_EINVAL, "dock_batch: mode %d", sp->mode);
+  if (sur && (!sp->surrogate || sp->candidates < 1 || sp->candidates > DOCK_MAX_CANDIDATES ||
+              sp->keep < 1 || sp->keep > sp->candidates || sp->pop + sp->keep > 16384))
+    return fail(DOCK_EINVAL, "dock_batch: surrogate mode needs a surrogate, 1 <= keep <= "
+                             "candidates <= %d and pop + keep <= 16384", DOCK_MAX_CANDIDATES);
   const int forced = sp->lanes_per_pose;
   if (forced != 0 && forced != 1 && forced != 2 && forced != 4 && forced != 8)
     return fail(DOCK_EINVAL, "dock_batch: lanes_per_pose %d", forced);
@@ -600,6 +607,89 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   F.cz = P->center[2];
   F.params = P->d_params;
 
+  const int C = sur ? sp->candidates : 0, K = sur ? sp->keep : 0;
+  if (sur) {
+    const size_t rows = (size_t)nl * C, kept = (size_t)nl * K;
+    if (rows > W.sur_cap || !W.cand_geno) {
+      dfree(W.cand_geno);
+      dfree(W.pred);
+      dfree(W.feats);
+      W.sur_cap = 0;
+      CU(dalloc(&W.cand_geno, rows * DOCK_MAX_GENES));
+      CU(dalloc(&W.pred, rows));
+      CU(dalloc(&W.feats, rows * DOCK_N_FEATURES));
+      W.sur_cap = rows;
+    }
+    if (kept > W.kept_cap || !W.kept_geno) {
+      dfree(W.kept_geno);
+      dfree(W.kept_score);
+      dfree(W.kept_lig);
+      W.kept_cap = 0;
+      CU(dalloc(&W.kept_geno, kept * DOCK_MAX_GENES));
+      CU(dalloc(&W.kept_score, kept));
+      CU(dalloc(&W.kept_lig, kept));
+      W.kept_cap = kept;
+    }
+  }
+  FeatureLaunch FL{};
+  FL.ligs = L->d_info;
+  FL.atoms = L->d_atoms;
+  FL.types = L->d_types;
+  FL.pair_rec = L->d_pair_rec;
+  FL.tors = L->d_tors;
+  FL.moves = L->d_moves;
+  FL.grid = grid_view(P);
+  FL.cx = P->center[0];
+  FL.cy = P->center[1];
+  FL.cz = P->center[2];
+  FL.radius = P->radius;
+  FL.n_ligands = nl;
+  FL.from_ga = true;
+  FL.pop = pop;
+  FL.candidates = C;
+  FL.seed = sp->seed;
+  FL.thr_cross = A.thr_cross;
+  FL.thr_mut = A.thr_mut;
+  FL.geno_off = W.geno_off;
+  FL.cand_geno = W.cand_geno;
+  FL.features = W.feats;
+  ScoreArgs KS{};
+  KS.ligs = L->d_info;
+  KS.atoms = L->d_atoms;
+  KS.types = L->d_types;
+  KS.pair_rec = L->d_pair_rec;
+  KS.tors = L->d_tors;
+  KS.moves = L->d_moves;
+  KS.grid = grid_view(P);
+  KS.cx = P->center[0];
+  KS.cy = P->center[1];
+  KS.cz = P->center[2];
+  KS.pose_ligand = W.kept_lig;
+  KS.n_ligands = nl;
+  KS.genos = W.kept_geno;
+  KS.n_poses = (int64_t)nl * K;
+  KS.scores = W.kept_score;
+  KS.coords = nullptr;
+  KS.lanes = 8;
+  KS.atoms_per_lane = DOCK_MAX_ATOMS / 8;
+
+  // One surrogate generation g >= 1: candidates + features, prediction, top
+  // `keep`, exact scores of the kept, mu + lambda merge into generation g.
+  auto surrogate_generation = [&](int g, cudaStream_t q) -> int {
+    FeatureLaunch f = FL;
+    f.gen = g;
+    f.geno_prev = W.geno[(g + 1) & 1];
+    f.score_prev = W.score[(g + 1) & 1];
+    CU(launch_features(f, q));
+    const int pst = dk_surrogate_predict_raw(sp->surrogate, W.feats, (int64_t)nl * C, W.pred, 0, q);
+    if (pst != DOCK_OK) return pst;
+    CU(launch_topk(W.pred, nl, C, K, W.cand_geno, W.kept_geno, W.kept_lig, q));
+    CU(launch_score(KS, q));
+    CU(launch_merge(W.geno[(g + 1) & 1], W.score[(g + 1) & 1], W.geno_off, L->d_info, nl, pop,
+                    W.kept_geno, W.kept_score, K, W.geno[g & 1], W.score[g & 1], q));
+    return DOCK_OK;
+  };
+
   auto enqueue = [&](cudaStream_t q) -> int {
     CU(cudaMemsetAsync(W.counters, 0, sizeof(uint32_t) * gens, q));
     CU(cudaMemsetAsync(W.best, 0xFF, sizeof(unsigned long long) * (size_t)gens * nl, q));
@@ -616,7 +706,10 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
       a.score_next = W.score[g & 1];
       a.best_prev = g ? W.best + (size_t)(g - 1) * nl : nullptr;
       a.best_next = W.best + (size_t)g * nl;
-      if (profile) {
+      if (sur && g > 0) {
+        const int st2 = surrogate_generation(g, q);
+        if (st2 != DOCK_OK) return st2;
+      } else if (profile) {
         cudaEvent_t e0, e1;
         CU(cudaEventCreate(&e0));
         CU(cudaEventCreate(&e1));
@@ -637,11 +730,12 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     }
     CU(launch_finalize_impl(F, L->d_centroid, nl, pop, W.geno_off, W.geno[(gens - 1) & 1],
                             W.score[(gens - 1) & 1], W.lig_status, W.status,
-                            (uint64_t)pop * gens, P->ox, P->oy, P->oz, W.results, q));
+                            sur ? (uint64_t)pop + (uint64_t)(gens - 1) * K : (uint64_t)pop * gens,
+                            sur ? (uint64_t)(gens - 1) * C : 0, P->ox, P->oy, P->oz, W.results, q));
     return DOCK_OK;
   };
 
-  if (sp->use_graph && !profile && s != nullptr) {
+  if (sp->use_graph && !profile && !sur && s != nullptr) {
     // graph key: everything the captured launches depend on
     std::vector<uint8_t> key;
     auto put = [&](const void *p, size_t n) {
@@ -785,5 +879,86 @@ extern "C" int dock_score(dock_pocket *P, dock_ligands *L, const int32_t *pose_l
   A.lanes = 8;
   A.atoms_per_lane = DOCK_MAX_ATOMS / 8;
   CU(launch_score(A, s));
+  return DOCK_OK;
+}
+
+extern "C" int dock_features(dock_pocket *P, dock_ligands *L, const int32_t *pose_ligand,
+                             const float *genotypes, int64_t n_poses, uint16_t *features,
+                             float *scores, void *stream) {
+  if (!P || !L) return fail(DOCK_EINVAL, "dock_features: NULL pocket or ligands");
+  if (n_poses < 0) return fail(DOCK_EINVAL, "dock_features: n_poses < 0");
+  if (n_poses == 0) return DOCK_OK;
+  if (!pose_ligand || !genotypes || !features) return fail(DOCK_EINVAL, "dock_features: NULL buffer");
+  CU(cudaSetDevice(L->device));
+  FeatureLaunch F{};
+  F.ligs = L->d_info;
+  F.atoms = L->d_atoms;
+  F.types = L->d_types;
+  F.pair_rec = L->d_pair_rec;
+  F.tors = L->d_tors;
+  F.moves = L->d_moves;
+  F.grid = grid_view(P);
+  F.cx = P->center[0];
+  F.cy = P->center[1];
+  F.cz = P->center[2];
+  F.radius = P->radius;
+  F.n_ligands = L->n_ligands;
+  F.from_ga = false;
+  F.pose_ligand = pose_ligand;
+  F.genos = genotypes;
+  F.n_poses = n_poses;
+  F.scores = scores;
+  F.features = features;
+  CU(launch_features(F, (cudaStream_t)stream));
+  return DOCK_OK;
+}
+
+extern "C" int dock_features_population(dock_pocket *P, dock_ligands *L, int32_t pop,
+                                        const float *genotypes, uint16_t *features, float *scores,
+                                        void *stream) {
+  if (!P || !L || !genotypes || !features)
+    return fail(DOCK_EINVAL, "dock_features_population: NULL argument");
+  if (pop < 1 || pop > DOCK_MAX_POP) return fail(DOCK_EINVAL, "dock_features_population: pop %d", pop);
+  CU(cudaSetDevice(L->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nl = L->n_ligands;
+  if (nl == 0) return DOCK_OK;
+  std::vector<int64_t> goff((size_t)nl);
+  int64_t tot = 0;
+  for (int l = 0; l < nl; ++l) {
+    goff[l] = tot;
+    tot += (int64_t)pop * (7 + L->info[l].k);
+  }
+  Workspace &W = L->ws;
+  if ((size_t)nl > W.feat_off_cap || !W.feat_off) {
+    dfree(W.feat_off);
+    W.feat_off_cap = 0;
+    CU(dalloc(&W.feat_off, (size_t)nl));
+    W.feat_off_cap = (size_t)nl;
+  }
+  CU(cudaMemcpyAsync(W.feat_off, goff.data(), sizeof(int64_t) * nl, cudaMemcpyHostToDevice, s));
+  FeatureLaunch F{};
+  F.ligs = L->d_info;
+  F.atoms = L->d_atoms;
+  F.types = L->d_types;
+  F.pair_rec = L->d_pair_rec;
+  F.tors = L->d_tors;
+  F.moves = L->d_moves;
+  F.grid = grid_view(P);
+  F.cx = P->center[0];
+  F.cy = P->center[1];
+  F.cz = P->center[2];
+  F.radius = P->radius;
+  F.n_ligands = nl;
+  F.from_ga = false;
+  F.pop_csr = pop;
+  F.genos = genotypes;
+  F.geno_off = W.feat_off;
+  F.n_poses = (int64_t)nl * pop;
+  F.scores = scores;
+  F.features = features;
+  CU(launch_features(F, s));
+  // the offsets buffer is reused by later calls: finish before returning
+  CU(cudaStreamSynchronize(s));
   return DOCK_OK;
 }

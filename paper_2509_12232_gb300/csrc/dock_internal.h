@@ -132,8 +132,8 @@ cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int n_ligands, int pop,
                                  const int64_t *geno_off, const float *genos, const float *scores,
                                  const int32_t *lig_status, const int32_t *status,
-                                 uint64_t exact_evals, double ox, double oy, double oz,
-                                 dock_result *out, cudaStream_t s);
+                                 uint64_t exact_evals, uint64_t surrogate_evals, double ox,
+                                 double oy, double oz, dock_result *out, cudaStream_t s);
 cudaError_t launch_score_fp64_impl(const Fp64Args &f, const double *centroids, double ox, double oy,
                                    double oz, const int32_t *pose_ligand, int n_ligands,
                                    const float *genos, int64_t n_poses, double *out, cudaStream_t s);

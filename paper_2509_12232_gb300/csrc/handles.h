@@ -10,6 +10,11 @@
 
 #include "dock_internal.h"
 
+struct dock_surrogate;
+// Inference of the surrogate (surrogate.cu): out[i] = prediction of row i.
+int dk_surrogate_predict_raw(dock_surrogate *S, const uint16_t *features, int64_t n, float *out,
+                             int destandardize, cudaStream_t s);
+
 namespace dk {
 // Records the message returned by dock_last_error() for this thread; returns st.
 int vset_error(int st, const char *fmt, va_list ap);
@@ -82,6 +87,13 @@ struct Workspace {
   uint64_t *deadline = nullptr;
   int32_t *lig_status = nullptr;
   dock_result *results = nullptr;
+  // surrogate mode: candidates, their features and predictions, kept candidates
+  size_t sur_cap = 0, kept_cap = 0;
+  float *cand_geno = nullptr, *pred = nullptr, *kept_geno = nullptr, *kept_score = nullptr;
+  uint16_t *feats = nullptr;
+  int32_t *kept_lig = nullptr;
+  size_t feat_off_cap = 0;
+  int64_t *feat_off = nullptr;  // genotype offsets for dock_features_population
   // cached graph
   cudaGraphExec_t graph = nullptr;
   std::vector<uint8_t> graph_key;
@@ -98,6 +110,13 @@ struct Workspace {
     dfree(deadline);
     dfree(lig_status);
     dfree(results);
+    dfree(cand_geno);
+    dfree(pred);
+    dfree(feats);
+    dfree(kept_geno);
+    dfree(kept_score);
+    dfree(kept_lig);
+    dfree(feat_off);
     if (graph) cudaGraphExecDestroy(graph);
   }
 };

@@ -1,0 +1,52 @@
+// Kernels of the BF16 surrogate MLP (mlp.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dk {
+namespace mlp {
+
+constexpr int FEATURES = 128, HIDDEN = 256;
+// Packed FP32 parameters: W1[128][256], b1[256], W2[256][256], b2[256],
+// W3[256][256], b3[256], W4[256], b4[1] (W stored [in][out]).
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + FEATURES * HIDDEN;
+constexpr int OFF_W2 = OFF_B1 + HIDDEN;
+constexpr int OFF_B2 = OFF_W2 + HIDDEN * HIDDEN;
+constexpr int OFF_W3 = OFF_B2 + HIDDEN;
+constexpr int OFF_B3 = OFF_W3 + HIDDEN * HIDDEN;
+constexpr int OFF_W4 = OFF_B3 + HIDDEN;
+constexpr int OFF_B4 = OFF_W4 + HIDDEN;
+constexpr int N_PARAMS = OFF_B4 + 1;
+
+enum { EPI_STORE_F32 = 0, EPI_BIAS_GELU = 1, EPI_GELU_BWD = 2 };
+
+struct Epilogue {
+  float *c32;               // FP32 output (STORE) or pre-activation cache (BIAS_GELU), or null
+  __nv_bfloat16 *c16;       // BF16 output (BIAS_GELU: activation; GELU_BWD: dZ)
+  const float *bias;        // BIAS_GELU
+  const float *zin;         // GELU_BWD: pre-activations
+  int ldc;
+};
+
+// C = A Bt^T: A [M][K] row-major, Bt [N][K] row-major.
+cudaError_t gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb, int M, int N,
+                    int K, int epi, const Epilogue &ep, cudaStream_t s);
+// C (FP32) = A^T B: A stored [K][M], B stored [K][N] (weight gradients).
+cudaError_t gemm_tt_f32(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M,
+                        int N, int K, float *C, int ldc, cudaStream_t s);
+cudaError_t out_layer(const __nv_bfloat16 *H, const float *w, const float *b, int rows, float *y,
+                      cudaStream_t s);
+cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const __nv_bfloat16 *H3,
+                          const float *Z3, const float *w4, __nv_bfloat16 *dZ3, float *part,
+                          int blocks, float *out, cudaStream_t s);
+cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, cudaStream_t s);
+cudaError_t adam(float *p, float *m, float *v, const float *g, int n, float lr, int step,
+                 cudaStream_t s);
+cudaError_t cast_weights(const float *W, int in, int out, __nv_bfloat16 *w16, __nv_bfloat16 *wt16,
+                         cudaStream_t s);
+
+}  // namespace mlp
+}  // namespace dk

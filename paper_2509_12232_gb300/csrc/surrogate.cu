@@ -1,0 +1,382 @@
+// The learned pre-screen of candidate poses: an MLP 128 -> 256 -> 256 -> 256
+// -> 1 (GELU) on per-pose features, trained on the GPU by the kernels of
+// mlp.cu on (features, exact score) pairs that the exact scorer produces.
+// C ABI: dock_surrogate_* in include/dock.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <random>
+#include <vector>
+
+#include "handles.h"
+#include "mlp.h"
+
+using namespace dk;
+using dk::mlp::FEATURES;
+using dk::mlp::HIDDEN;
+using dk::mlp::N_PARAMS;
+
+static int sfail(int st, const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vset_error(st, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+#define SCU(call)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      int st_ = e_ == cudaErrorMemoryAllocation ? DOCK_ENOMEM : DOCK_ECUDA;         \
+      return sfail(st_, "%s failed: %s", #call, cudaGetErrorString(e_));            \
+    }                                                                               \
+  } while (0)
+
+namespace {
+constexpr int kPredictChunk = 65536;   // rows per inference chunk
+constexpr int kMaxTrainBatch = 65536;
+
+__global__ void gather_rows_kernel(const __nv_bfloat16 *X, const float *t, const int64_t *idx,
+                                   int64_t n_src, int rows, int rows_valid, __nv_bfloat16 *Xb,
+                                   float *tb, float t_mean, float t_inv_std, float t_clip) {
+  // one warp per row: 128 bf16 = 256 bytes = 32 lanes x 8 bytes
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (r >= rows) return;
+  uint2 v = make_uint2(0, 0);
+  float tv = 0.0f;
+  if (r < rows_valid) {
+    const int64_t src = idx ? idx[r] : r;
+    if (src < n_src) {
+      v = reinterpret_cast<const uint2 *>(X + src * FEATURES)[lane];
+      if (t) tv = (fminf(t[src], t_clip) - t_mean) * t_inv_std;
+    }
+  }
+  reinterpret_cast<uint2 *>(Xb + (int64_t)r * FEATURES)[lane] = v;
+  if (lane == 0 && tb) tb[r] = tv;
+}
+
+// mean and sum of squares of min(t, clip) (double accumulation, one block)
+__global__ void target_stats_kernel(const float *t, int64_t n, float clip, double *out) {
+  __shared__ double s1[256], s2[256];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = fminf(t[i], clip);
+    a += v;
+    b += v * v;
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s1[0];
+    out[1] = s2[0];
+  }
+}
+
+__global__ void destandardize_kernel(const float *y, int n, float mean, float std, float *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = y[i] * std + mean;
+}
+}  // namespace
+
+struct dock_surrogate {
+  int device = 0;
+  float *p = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;   // FP32 masters, Adam, grads
+  __nv_bfloat16 *w16[3] = {nullptr, nullptr, nullptr};            // W1..W3 [in][out]
+  __nv_bfloat16 *wt16[3] = {nullptr, nullptr, nullptr};           // W1..W3 [out][in]
+  // batch workspace
+  int cap = 0;
+  __nv_bfloat16 *X = nullptr, *H[3] = {nullptr, nullptr, nullptr}, *dZ[3] = {nullptr, nullptr, nullptr};
+  float *Z[3] = {nullptr, nullptr, nullptr}, *y = nullptr, *t = nullptr, *part = nullptr,
+        *outg = nullptr;
+  int64_t *idx = nullptr;
+  double *stats = nullptr;
+  int step = 0;
+  float t_mean = 0.0f, t_std = 1.0f, t_clip = 1e30f;
+  ~dock_surrogate() {
+    for (float *q : {p, m, v, g, y, t, part, outg}) if (q) cudaFree(q);
+    for (int l = 0; l < 3; ++l) {
+      if (w16[l]) cudaFree(w16[l]);
+      if (wt16[l]) cudaFree(wt16[l]);
+      if (H[l]) cudaFree(H[l]);
+      if (dZ[l]) cudaFree(dZ[l]);
+      if (Z[l]) cudaFree(Z[l]);
+    }
+    if (X) cudaFree(X);
+    if (idx) cudaFree(idx);
+    if (stats) cudaFree(stats);
+  }
+};
+
+static const int kIn[3] = {FEATURES, HIDDEN, HIDDEN};
+static const int kOffW[3] = {mlp::OFF_W1, mlp::OFF_W2, mlp::OFF_W3};
+static const int kOffB[3] = {mlp::OFF_B1, mlp::OFF_B2, mlp::OFF_B3};
+static const int kBwdBlocks = 128;
+
+static int ensure_workspace(dock_surrogate *S, int rows) {
+  if (rows <= S->cap) return DOCK_OK;
+  if (S->X) cudaFree(S->X);
+  for (int l = 0; l < 3; ++l) {
+    if (S->H[l]) cudaFree(S->H[l]);
+    if (S->dZ[l]) cudaFree(S->dZ[l]);
+    if (S->Z[l]) cudaFree(S->Z[l]);
+    S->H[l] = S->dZ[l] = nullptr;
+    S->Z[l] = nullptr;
+  }
+  for (float **q : {&S->y, &S->t}) {
+    if (*q) cudaFree(*q);
+    *q = nullptr;
+  }
+  S->cap = 0;
+  SCU(cudaMalloc(&S->X, sizeof(__nv_bfloat16) * (size_t)rows * FEATURES));
+  for (int l = 0; l < 3; ++l) {
+    SCU(cudaMalloc(&S->H[l], sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
+    SCU(cudaMalloc(&S->dZ[l], sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
+    SCU(cudaMalloc(&S->Z[l], sizeof(float) * (size_t)rows * HIDDEN));
+  }
+  SCU(cudaMalloc(&S->y, sizeof(float) * rows));
+  SCU(cudaMalloc(&S->t, sizeof(float) * rows));
+  S->cap = rows;
+  return DOCK_OK;
+}
+
+static int refresh_bf16(dock_surrogate *S, cudaStream_t s) {
+  for (int l = 0; l < 3; ++l)
+    SCU(mlp::cast_weights(S->p + kOffW[l], kIn[l], HIDDEN, S->w16[l], S->wt16[l], s));
+  return DOCK_OK;
+}
+
+// Forward pass of `rows` rows already in S->X (rows a multiple of 128).
+// keep = true keeps FP32 pre-activations for the backward pass.
+static int forward(dock_surrogate *S, int rows, bool keep, cudaStream_t s) {
+  const __nv_bfloat16 *in = S->X;
+  for (int l = 0; l < 3; ++l) {
+    mlp::Epilogue ep{};
+    ep.c32 = keep ? S->Z[l] : nullptr;
+    ep.c16 = S->H[l];
+    ep.bias = S->p + kOffB[l];
+    ep.ldc = HIDDEN;
+    SCU(mlp::gemm_nt(in, kIn[l], S->wt16[l], kIn[l], rows, HIDDEN, kIn[l], mlp::EPI_BIAS_GELU, ep, s));
+    in = S->H[l];
+  }
+  SCU(mlp::out_layer(S->H[2], S->p + mlp::OFF_W4, S->p + mlp::OFF_B4, rows, S->y, s));
+  return DOCK_OK;
+}
+
+// Gradients of loss = mean over the first n rows of (y - t)^2 into S->g
+// (rows >= n padded: contribute nothing). Needs forward(keep = true).
+static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
+  SCU(mlp::out_layer_bwd(S->y, S->t, n, rows, S->H[2], S->Z[2], S->p + mlp::OFF_W4, S->dZ[2],
+                         S->part, kBwdBlocks, S->outg, s));
+  SCU(cudaMemcpyAsync(S->g + mlp::OFF_W4, S->outg, sizeof(float) * (HIDDEN + 1),
+                      cudaMemcpyDeviceToDevice, s));
+  for (int l = 2; l >= 0; --l) {
+    const __nv_bfloat16 *act_in = l ? S->H[l - 1] : S->X;
+    // dW_l = act_in^T dZ_l ; db_l = column sums of dZ_l
+    SCU(mlp::gemm_tt_f32(act_in, kIn[l], S->dZ[l], HIDDEN, kIn[l], HIDDEN, rows, S->g + kOffW[l],
+                         HIDDEN, s));
+    SCU(mlp::colsum(S->dZ[l], rows, HIDDEN, S->g + kOffB[l], s));
+    if (l) {
+      // dZ_{l-1} = (dZ_l W_l^T) * gelu'(Z_{l-1})
+      mlp::Epilogue ep{};
+      ep.c16 = S->dZ[l - 1];
+      ep.zin = S->Z[l - 1];
+      ep.ldc = HIDDEN;
+      SCU(mlp::gemm_nt(S->dZ[l], HIDDEN, S->w16[l], HIDDEN, rows, HIDDEN, HIDDEN, mlp::EPI_GELU_BWD,
+                       ep, s));
+    }
+  }
+  return DOCK_OK;
+}
+
+extern "C" int dock_surrogate_create(uint64_t seed, void *stream, dock_surrogate **out) {
+  if (!out) return sfail(DOCK_EINVAL, "dock_surrogate_create: NULL out");
+  *out = nullptr;
+  std::unique_ptr<dock_surrogate> S(new dock_surrogate());
+  SCU(cudaGetDevice(&S->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  for (float **q : {&S->p, &S->m, &S->v, &S->g}) SCU(cudaMalloc(q, sizeof(float) * N_PARAMS));
+  SCU(cudaMalloc(&S->part, sizeof(float) * kBwdBlocks * (HIDDEN + 2)));
+  SCU(cudaMalloc(&S->outg, sizeof(float) * (HIDDEN + 2)));
+  SCU(cudaMalloc(&S->stats, sizeof(double) * 2));
+  for (int l = 0; l < 3; ++l) {
+    SCU(cudaMalloc(&S->w16[l], sizeof(__nv_bfloat16) * kIn[l] * HIDDEN));
+    SCU(cudaMalloc(&S->wt16[l], sizeof(__nv_bfloat16) * kIn[l] * HIDDEN));
+  }
+  // He-normal weights, zero biases (host draw from the seed, one upload)
+  std::vector<float> h(N_PARAMS, 0.0f);
+  std::mt19937_64 rng(seed);
+  for (int l = 0; l < 3; ++l) {
+    std::normal_distribution<float> nd(0.0f, std::sqrt(2.0f / kIn[l]));
+    for (int i = 0; i < kIn[l] * HIDDEN; ++i) h[kOffW[l] + i] = nd(rng);
+  }
+  std::normal_distribution<float> nd4(0.0f, std::sqrt(1.0f / HIDDEN));
+  for (int i = 0; i < HIDDEN; ++i) h[mlp::OFF_W4 + i] = nd4(rng);
+  SCU(cudaMemcpyAsync(S->p, h.data(), sizeof(float) * N_PARAMS, cudaMemcpyHostToDevice, s));
+  SCU(cudaMemsetAsync(S->m, 0, sizeof(float) * N_PARAMS, s));
+  SCU(cudaMemsetAsync(S->v, 0, sizeof(float) * N_PARAMS, s));
+  int st = refresh_bf16(S.get(), s);
+  if (st != DOCK_OK) return st;
+  SCU(cudaStreamSynchronize(s));
+  *out = S.release();
+  return DOCK_OK;
+}
+
+extern "C" void dock_surrogate_destroy(dock_surrogate *S) { delete S; }
+
+extern "C" int dock_surrogate_set_params(dock_surrogate *S, const float *params, float t_mean,
+                                         float t_std, float t_clip, void *stream) {
+  if (!S || !params) return sfail(DOCK_EINVAL, "dock_surrogate_set_params: NULL argument");
+  if (!(t_std > 0.0f)) return sfail(DOCK_EINVAL, "dock_surrogate_set_params: t_std <= 0");
+  SCU(cudaSetDevice(S->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  SCU(cudaMemcpyAsync(S->p, params, sizeof(float) * N_PARAMS, cudaMemcpyHostToDevice, s));
+  S->t_mean = t_mean;
+  S->t_std = t_std;
+  S->t_clip = t_clip;
+  int st = refresh_bf16(S, s);
+  if (st != DOCK_OK) return st;
+  SCU(cudaStreamSynchronize(s));
+  return DOCK_OK;
+}
+
+extern "C" int dock_surrogate_get_params(const dock_surrogate *S, float *params, float *t_mean,
+                                         float *t_std, float *t_clip) {
+  if (!S) return sfail(DOCK_EINVAL, "dock_surrogate_get_params: NULL surrogate");
+  SCU(cudaSetDevice(S->device));
+  if (params) SCU(cudaMemcpy(params, S->p, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToHost));
+  if (t_mean) *t_mean = S->t_mean;
+  if (t_std) *t_std = S->t_std;
+  if (t_clip) *t_clip = S->t_clip;
+  return DOCK_OK;
+}
+
+int dk_surrogate_predict_raw(dock_surrogate *S, const uint16_t *features, int64_t n, float *out,
+                             int destandardize, cudaStream_t s) {
+  const __nv_bfloat16 *F = reinterpret_cast<const __nv_bfloat16 *>(features);
+  int st = ensure_workspace(S, kPredictChunk);
+  if (st != DOCK_OK) return st;
+  for (int64_t r0 = 0; r0 < n; r0 += kPredictChunk) {
+    const int rows_valid = (int)std::min<int64_t>(kPredictChunk, n - r0);
+    const int rows = (rows_valid + 127) / 128 * 128;
+    gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(F + r0 * FEATURES, nullptr, nullptr,
+                                                               n - r0, rows, rows_valid, S->X,
+                                                               nullptr, 0.f, 1.f, 0.f);
+    SCU(cudaGetLastError());
+    if ((st = forward(S, rows, false, s)) != DOCK_OK) return st;
+    if (destandardize)
+      destandardize_kernel<<<(rows_valid + 255) / 256, 256, 0, s>>>(S->y, rows_valid, S->t_mean,
+                                                                    S->t_std, out + r0);
+    else
+      SCU(cudaMemcpyAsync(out + r0, S->y, sizeof(float) * rows_valid, cudaMemcpyDeviceToDevice, s));
+    SCU(cudaGetLastError());
+  }
+  return DOCK_OK;
+}
+
+extern "C" int dock_surrogate_predict(dock_surrogate *S, const uint16_t *features, int64_t n,
+                                      float *out, void *stream) {
+  if (!S || (n > 0 && (!features || !out))) return sfail(DOCK_EINVAL, "dock_surrogate_predict: NULL");
+  if (n < 0) return sfail(DOCK_EINVAL, "dock_surrogate_predict: n < 0");
+  SCU(cudaSetDevice(S->device));
+  return dk_surrogate_predict_raw(S, features, n, out, 1, (cudaStream_t)stream);
+}
+
+extern "C" int dock_surrogate_gradients(dock_surrogate *S, const uint16_t *features,
+                                        const float *targets, int32_t n, float *grad, float *loss,
+                                        void *stream) {
+  if (!S || !features || !targets || !grad) return sfail(DOCK_EINVAL, "dock_surrogate_gradients: NULL");
+  if (n < 1 || n > kMaxTrainBatch) return sfail(DOCK_EINVAL, "dock_surrogate_gradients: n %d", n);
+  SCU(cudaSetDevice(S->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int rows = (n + 127) / 128 * 128;
+  int st = ensure_workspace(S, rows);
+  if (st != DOCK_OK) return st;
+  // targets used as given (identity standardisation)
+  gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(
+      reinterpret_cast<const __nv_bfloat16 *>(features), targets, nullptr, n, rows, n, S->X, S->t,
+      0.0f, 1.0f, 3.0e38f);
+  SCU(cudaGetLastError());
+  if ((st = forward(S, rows, true, s)) != DOCK_OK) return st;
+  if ((st = backward(S, rows, n, s)) != DOCK_OK) return st;
+  SCU(cudaMemcpyAsync(grad, S->g, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToDevice, s));
+  if (loss) {
+    SCU(cudaStreamSynchronize(s));
+    float ls = 0.0f;
+    SCU(cudaMemcpy(&ls, S->outg + HIDDEN + 1, sizeof(float), cudaMemcpyDeviceToHost));
+    *loss = ls / n;
+  }
+  return DOCK_OK;
+}
+
+extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features, const float *scores,
+                                    int64_t n, const dock_train_params *tp, float *loss_per_epoch,
+                                    void *stream) {
+  if (!S || !features || !scores || !tp) return sfail(DOCK_EINVAL, "dock_surrogate_train: NULL");
+  if (n < 2 || tp->epochs < 1 || tp->batch < 128 || tp->batch > kMaxTrainBatch || tp->batch % 128 ||
+      !(tp->lr > 0.0f))
+    return sfail(DOCK_EINVAL, "dock_surrogate_train: bad sizes or learning rate");
+  SCU(cudaSetDevice(S->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = ensure_workspace(S, tp->batch);
+  if (st != DOCK_OK) return st;
+  // target standardisation over the training set: min(score, clip), then mean / std
+  const float clip = tp->score_clip;
+  target_stats_kernel<<<1, 256, 0, s>>>(scores, n, clip, S->stats);
+  SCU(cudaGetLastError());
+  double st2[2];
+  SCU(cudaMemcpyAsync(st2, S->stats, sizeof st2, cudaMemcpyDeviceToHost, s));
+  SCU(cudaStreamSynchronize(s));
+  const double mean = st2[0] / n, var = std::max(st2[1] / n - mean * mean, 1e-12);
+  S->t_mean = (float)mean;
+  S->t_std = (float)std::sqrt(var);
+  S->t_clip = clip;
+  // one shuffled order for the run, drawn from the seed
+  std::vector<int64_t> perm((size_t)n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::mt19937_64 rng(tp->seed);
+  std::shuffle(perm.begin(), perm.end(), rng);
+  if (S->idx) cudaFree(S->idx);
+  S->idx = nullptr;
+  SCU(cudaMalloc(&S->idx, sizeof(int64_t) * n));
+  SCU(cudaMemcpyAsync(S->idx, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+  const __nv_bfloat16 *F = reinterpret_cast<const __nv_bfloat16 *>(features);
+  const int B = tp->batch;
+  const int64_t steps_per_epoch = (n + B - 1) / B;
+  for (int ep = 0; ep < tp->epochs; ++ep) {
+    double ep_loss = 0.0;
+    for (int64_t b = 0; b < steps_per_epoch; ++b) {
+      const int64_t r0 = b * B;
+      const int valid = (int)std::min<int64_t>(B, n - r0);
+      const int rows = (valid + 127) / 128 * 128;
+      gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(
+          F, scores, S->idx + r0, n, rows, valid, S->X, S->t, S->t_mean, 1.0f / S->t_std, clip);
+      SCU(cudaGetLastError());
+      if ((st = forward(S, rows, true, s)) != DOCK_OK) return st;
+      if ((st = backward(S, rows, valid, s)) != DOCK_OK) return st;
+      SCU(mlp::adam(S->p, S->m, S->v, S->g, N_PARAMS, tp->lr, ++S->step, s));
+      if ((st = refresh_bf16(S, s)) != DOCK_OK) return st;
+      if (loss_per_epoch && (b == steps_per_epoch - 1 || (b & 63) == 0)) {
+        float ls = 0.0f;
+        SCU(cudaMemcpyAsync(&ls, S->outg + HIDDEN + 1, sizeof(float), cudaMemcpyDeviceToHost, s));
+        SCU(cudaStreamSynchronize(s));
+        ep_loss = ls / valid;
+      }
+    }
+    if (loss_per_epoch) loss_per_epoch[ep] = (float)ep_loss;
+  }
+  SCU(cudaStreamSynchronize(s));
+  return DOCK_OK;
+}

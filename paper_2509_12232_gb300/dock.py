@@ -54,7 +54,18 @@ class dock_search_params(C.Structure):
     _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("p_cross", C.c_float),
                 ("p_mut", C.c_float), ("seed", C.c_uint64), ("lanes_per_pose", C.c_int32),
                 ("use_graph", C.c_int32), ("timeout_ns", C.c_uint64),
-                ("trace_genotypes", C.c_void_p), ("trace_scores", C.c_void_p)]
+                ("trace_genotypes", C.c_void_p), ("trace_scores", C.c_void_p),
+                ("mode", C.c_int32), ("candidates", C.c_int32), ("keep", C.c_int32),
+                ("surrogate", C.c_void_p)]
+
+
+class dock_train_params(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float),
+                ("score_clip", C.c_float), ("seed", C.c_uint64)]
+
+
+DOCK_MODE_PLAIN, DOCK_MODE_SURROGATE = 0, 1
+DOCK_N_FEATURES, DOCK_MLP_N_PARAMS = 128, 164865
 
 
 class dock_result(C.Structure):
@@ -103,9 +114,25 @@ def lib():
         P_i64 = C.POINTER(C.c_int64)
         L.dock_ligands_info.argtypes = [vp, P_i32, P_i64, P_i64, P_i64, P_i64, P_i64]
         L.dock_batch_noalloc.argtypes = [vp, vp, C.POINTER(dock_search_params), vp, vp]
+        L.dock_features.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp, vp]
+        L.dock_features_population.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp]
+        L.dock_surrogate_create.argtypes = [C.c_uint64, vp, C.POINTER(vp)]
+        L.dock_surrogate_destroy.argtypes = [vp]
+        L.dock_surrogate_destroy.restype = None
+        L.dock_surrogate_set_params.argtypes = [vp, vp, C.c_float, C.c_float, C.c_float, vp]
+        L.dock_surrogate_get_params.argtypes = [vp, vp, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                                C.POINTER(C.c_float)]
+        L.dock_surrogate_predict.argtypes = [vp, vp, C.c_int64, vp, vp]
+        L.dock_surrogate_gradients.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_float), vp]
+        L.dock_surrogate_train.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(dock_train_params), vp,
+                                           vp]
         for name in ("dock_create_pocket", "dock_pocket_grid", "dock_load_ligands", "dock_batch",
                      "dock_results", "dock_job_population", "dock_job_kernel_time", "dock_score",
-                     "dock_ligands_info", "dock_batch_noalloc"):
+                     "dock_ligands_info", "dock_batch_noalloc", "dock_features",
+                     "dock_features_population", "dock_surrogate_create",
+                     "dock_surrogate_set_params", "dock_surrogate_get_params",
+                     "dock_surrogate_predict", "dock_surrogate_gradients",
+                     "dock_surrogate_train"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -257,12 +284,18 @@ def dock_ligands_info(ligands: Ligands) -> dict:
 
 def dock_batch(pocket: Pocket, ligands: Ligands, pop: int, generations: int, p_cross=0.8,
                p_mut=0.02, seed=0, lanes_per_pose=0, use_graph=1, timeout_ns=0,
-               trace_genotypes=None, trace_scores=None, stream=None) -> Job:
+               trace_genotypes=None, trace_scores=None, stream=None, surrogate=None,
+               candidates=0, keep=0) -> Job:
+    """Plain search, or the surrogate pre-screened search when `surrogate` is
+    given (`candidates` children per ligand and generation, `keep` of them
+    scored exactly)."""
+    mode = DOCK_MODE_SURROGATE if surrogate is not None else DOCK_MODE_PLAIN
     sp = dock_search_params(pop, generations, p_cross, p_mut, seed, lanes_per_pose, use_graph,
-                            timeout_ns, _dptr(trace_genotypes), _dptr(trace_scores))
+                            timeout_ns, _dptr(trace_genotypes), _dptr(trace_scores), mode,
+                            candidates, keep, surrogate.handle if surrogate is not None else None)
     h = C.c_void_p()
     check(lib().dock_batch(pocket.handle, ligands.handle, C.byref(sp), _stream(stream), C.byref(h)))
-    return Job(h, ligands.n_ligands, keep=(pocket, ligands))
+    return Job(h, ligands.n_ligands, keep=(pocket, ligands, surrogate))
 
 
 def dock_batch_noalloc(pocket: Pocket, ligands: Ligands, results, pop: int, generations: int,
@@ -273,7 +306,8 @@ def dock_batch_noalloc(pocket: Pocket, ligands: Ligands, results, pop: int, gene
     of n_ligands dock_result records (RESULT_DTYPE.itemsize bytes each).
     Asynchronous on stream."""
     sp = dock_search_params(pop, generations, p_cross, p_mut, seed, 0, 0, timeout_ns,
-                            _dptr(trace_genotypes), _dptr(trace_scores))
+                            _dptr(trace_genotypes), _dptr(trace_scores), DOCK_MODE_PLAIN, 0, 0,
+                            None)
     check(lib().dock_batch_noalloc(pocket.handle, ligands.handle, C.byref(sp), _dptr(results),
                                    _stream(stream)))
 
@@ -311,3 +345,78 @@ def dock_score(pocket: Pocket, ligands: Ligands, pose_ligand, genotypes, scores=
 
 def version() -> str:
     return lib().dock_version().decode()
+
+
+def dock_features(pocket: Pocket, ligands: Ligands, pose_ligand, genotypes, features, scores=None,
+                  stream=None):
+    """Features (device uint16/bf16 [n][128]) and optional exact scores of
+    genotypes ([n][23] device) posed for ligands pose_ligand ([n] device)."""
+    n = int(genotypes.shape[0])
+    check(lib().dock_features(pocket.handle, ligands.handle, _dptr(pose_ligand), _dptr(genotypes), n,
+                              _dptr(features), _dptr(scores), _stream(stream)))
+
+
+def dock_features_population(pocket: Pocket, ligands: Ligands, pop: int, genotypes, features,
+                             scores=None, stream=None):
+    check(lib().dock_features_population(pocket.handle, ligands.handle, pop, _dptr(genotypes),
+                                         _dptr(features), _dptr(scores), _stream(stream)))
+
+
+class Surrogate:
+    def __init__(self, handle):
+        self.handle = handle
+
+    def close(self):
+        if self.handle:
+            lib().dock_surrogate_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dock_surrogate_create(seed=0, stream=None) -> Surrogate:
+    h = C.c_void_p()
+    check(lib().dock_surrogate_create(seed, _stream(stream), C.byref(h)))
+    return Surrogate(h)
+
+
+def dock_surrogate_set_params(s: Surrogate, params, t_mean=0.0, t_std=1.0, t_clip=3.0e38, stream=None):
+    p = _c(params, np.float32)
+    assert p.shape == (DOCK_MLP_N_PARAMS,)
+    check(lib().dock_surrogate_set_params(s.handle, p.ctypes.data_as(C.c_void_p), t_mean, t_std, t_clip,
+                                          _stream(stream)))
+
+
+def dock_surrogate_get_params(s: Surrogate):
+    p = np.zeros(DOCK_MLP_N_PARAMS, np.float32)
+    m, sd, c = C.c_float(), C.c_float(), C.c_float()
+    check(lib().dock_surrogate_get_params(s.handle, p.ctypes.data_as(C.c_void_p), C.byref(m),
+                                          C.byref(sd), C.byref(c)))
+    return p, m.value, sd.value, c.value
+
+
+def dock_surrogate_predict(s: Surrogate, features, out, stream=None):
+    n = int(features.shape[0])
+    check(lib().dock_surrogate_predict(s.handle, _dptr(features), n, _dptr(out), _stream(stream)))
+
+
+def dock_surrogate_gradients(s: Surrogate, features, targets, grad, stream=None) -> float:
+    n = int(features.shape[0])
+    loss = C.c_float()
+    check(lib().dock_surrogate_gradients(s.handle, _dptr(features), _dptr(targets), n, _dptr(grad),
+                                         C.byref(loss), _stream(stream)))
+    return loss.value
+
+
+def dock_surrogate_train(s: Surrogate, features, scores, epochs=2, batch=4096, lr=1e-3,
+                         score_clip=20.0, seed=0, stream=None) -> np.ndarray:
+    n = int(features.shape[0])
+    tp = dock_train_params(epochs, batch, lr, score_clip, seed)
+    losses = np.zeros(epochs, np.float32)
+    check(lib().dock_surrogate_train(s.handle, _dptr(features), _dptr(scores), n, C.byref(tp),
+                                     losses.ctypes.data_as(C.c_void_p), _stream(stream)))
+    return losses

@@ -49,8 +49,32 @@ def test_binding_raises_without_library(tmp_path, monkeypatch):
         dock.lib()
 
 
-def test_struct_sizes_match_header():
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C compiler
+    gives the header's structs."""
+    import subprocess
     from paper_2509_12232_gb300 import dock
+    structs = {
+        "dock_type_params": dock.dock_type_params,
+        "dock_pocket_desc": dock.dock_pocket_desc,
+        "dock_ligand_batch": dock.dock_ligand_batch,
+        "dock_search_params": dock.dock_search_params,
+        "dock_result": dock.dock_result,
+        "dock_train_params": dock.dock_train_params,
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dock.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (name, f)]) == getattr(cls, f).offset, (name, f)
     assert ctypes.sizeof(dock.dock_result) == dock.RESULT_DTYPE.itemsize
-    assert ctypes.sizeof(dock.dock_type_params) == 28
-    assert ctypes.sizeof(dock.dock_search_params) == 56
