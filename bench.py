@@ -216,12 +216,104 @@ def cpu_baseline(budget_s):
                 n, WORKLOAD, w.pop, w.generations, dt)}
 
 
+def run_surrogate(args, rank, world):
+    """Surrogate-pre-screened vs plain exact search on the same GPU and ligands
+    (large-screen per-ligand settings: c2 size mix, 10,000-atom pocket,
+    2,048 poses x 40 generations, 4,096 candidates, 410 kept), on a sample of
+    args.ligands ligands. Training (per pocket, on ~10M exact pairs of
+    training ligands drawn with another seed) is timed separately."""
+    import torch
+    from paper_2509_12232_gb300 import build, dock, synth
+    torch.cuda.set_device(local_rank := env_rank()[2])
+    build.build()
+    stream = torch.cuda.current_stream()
+    w = synth.WORKLOADS["c5"]
+    pk = synth.make_pocket(w.pocket_atoms, w.radius, seed=0)
+    pocket = dock.dock_create_pocket(pk.x, pk.y, pk.z, pk.q, pk.type, pk.center, pk.radius,
+                                     pk.spacing, synth.TYPE_PARAMS, stream=stream)
+
+    def ligand_set(n, seed, id_base):
+        rng = np.random.Generator(np.random.Philox(seed))
+        na, nt = synth.ligand_sizes(rng, "uniform", n)
+        ls = synth.make_ligands(rng, na, nt, id_base=id_base)
+        return ls, dock.dock_load_ligands(pocket, ls.atom_off, ls.x, ls.y, ls.z, ls.q, ls.type,
+                                          ls.parent, ls.tors_off, ls.tors_b, ls.ligand_id,
+                                          stream=stream)
+    # training pairs: every pose of plain GA trajectories of training ligands
+    t0 = time.perf_counter()
+    n_tr, pop_tr, gens_tr = 512, 1024, 20
+    _, gl_tr = ligand_set(n_tr, 7777, 10 ** 7)
+    goff = gl_tr.geno_offsets(pop_tr)
+    tot = int(goff[-1])
+    tg = torch.zeros(gens_tr * tot, dtype=torch.float32, device="cuda")
+    job = dock.dock_batch(pocket, gl_tr, pop_tr, gens_tr, seed=1, trace_genotypes=tg, stream=stream)
+    dock.dock_results(job)
+    rows = n_tr * pop_tr
+    F = torch.zeros(gens_tr * rows, 128, dtype=torch.int16, device="cuda")
+    Y = torch.zeros(gens_tr * rows, dtype=torch.float32, device="cuda")
+    for g in range(gens_tr):
+        dock.dock_features_population(pocket, gl_tr, pop_tr, tg[g * tot:(g + 1) * tot],
+                                      F[g * rows:(g + 1) * rows], Y[g * rows:(g + 1) * rows])
+    del tg
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    S = dock.dock_surrogate_create(seed=2)
+    t0 = time.perf_counter()
+    losses = dock.dock_surrogate_train(S, F, Y, epochs=3, batch=4096, lr=1e-3, score_clip=100.0)
+    t_train = time.perf_counter() - t0
+    del F, Y
+    # evaluation ligands
+    n = args.ligands or 1000
+    ls, gl = ligand_set(n, 1000, 0)
+    common = dict(seed=0, stream=stream)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            j = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1000.0, j
+    plain_s, jp = timed(lambda: dock.dock_batch(pocket, gl, w.pop, w.generations, **common), args.steps)
+    rp = dock.dock_results(jp)
+    sur_s, js = timed(lambda: dock.dock_batch(pocket, gl, w.pop, w.generations, surrogate=S,
+                                              candidates=2 * w.pop, keep=410, **common), args.steps)
+    rs = dock.dock_results(js)
+    diff = rs["best_fp64"][:, 0] - rp["best_fp64"][:, 0]
+    line = {"metric": "ligands/s, surrogate-pre-screened GA vs plain exact GA (2,048 poses x 40 "
+                      "generations; 4,096 candidates per generation, 410 scored exactly)",
+            "value": round(n / sur_s, 2), "unit": "ligands/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": 1, "ms_per_step": round(sur_s * 1000, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": "%d ligands (10-60 atoms, 0-12 torsions) vs a 10,000-atom pocket "
+                                   "(20 A cavity, 107^3 grid)" % n},
+            "plain_ligands_per_s": round(n / plain_s, 2),
+            "surrogate_over_plain": round(plain_s / sur_s, 3),
+            "top1_fp64_surrogate_minus_plain": {
+                "median": round(float(np.median(diff)), 4),
+                "frac_within_0.1": round(float(np.mean(np.abs(diff) <= 0.1)), 4),
+                "frac_surrogate_better_or_within_0.1": round(float(np.mean(diff <= 0.1)), 4)},
+            "exact_evals_per_ligand": {"plain": int(rp["exact_evals"][0]),
+                                       "surrogate": int(rs["exact_evals"][0])},
+            "surrogate_evals_per_ligand": int(rs["surrogate_evals"][0]),
+            "training": {"pairs": gens_tr * rows, "data_seconds": round(t_data, 2),
+                         "train_seconds": round(t_train, 2),
+                         "loss_per_epoch": [round(float(x), 4) for x in losses]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="plain", choices=["plain", "surrogate"],
+                    help="surrogate: pre-screened vs plain comparison (its own JSON line)")
     ap.add_argument("--ref-ligands-per-core", type=int, default=1)
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -232,6 +324,8 @@ def main():
     rank, world, local = env_rank()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.mode == "surrogate":
+        return run_surrogate(args, rank, world)
 
     import torch
     import torch.distributed as dist
