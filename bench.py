@@ -350,6 +350,9 @@ def main():
              ligs.tors_b, ligs.ligand_id)
     gl = dock.dock_load_ligands(pocket, *largs, stream=stream)
     info = dock.dock_ligands_info(gl)
+    # launch shape of the search kernel: measured on this ligand set (set-up, not timed)
+    tune = dock.dock_autotune(pocket, gl, w.pop, 4, stream=stream)
+    shape = tune["table"][tune["best"]]
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
 
     def step():
@@ -438,7 +441,10 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": DESCR, "l2": "flushed between steps (256 MiB write)",
-                       "ligands_per_gpu": w.n_ligands, "pop": w.pop, "generations": w.generations},
+                       "ligands_per_gpu": w.n_ligands, "pop": w.pop, "generations": w.generations,
+                       "launch_shape": {"threads": shape["threads"],
+                                        "atoms_per_lane": shape["atoms_per_lane"],
+                                        "picked_by": "dock_autotune"}},
             "poses_scored_per_s": round(poses_per_step / (ms_step / 1000.0), 1),
             "roofline": roof,
             "e2e": {"value": round(total_ligands / e2e_s, 2), "unit": "ligands/s",

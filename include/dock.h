@@ -336,6 +336,31 @@ int dock_surrogate_train(dock_surrogate *surrogate, const uint16_t *features,
                          const float *scores, int64_t n, const dock_train_params *params,
                          float *loss_per_epoch, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Autotuner of the search kernel's launch shape                             */
+/* ------------------------------------------------------------------------ */
+#define DOCK_TUNE_MAX 16
+typedef struct {
+  int32_t n;                               /* shapes measured                */
+  int32_t threads[DOCK_TUNE_MAX];          /* CTA threads                    */
+  int32_t atoms_per_lane[DOCK_TUNE_MAX];   /* shared-memory atoms per lane   */
+  float ms_per_generation[DOCK_TUNE_MAX];  /* device time of one GA generation
+                                              (best of two short searches)    */
+  int32_t best;                            /* index of the chosen shape       */
+} dock_tune_table;
+
+/* Times the plain search on this ligand set for each candidate launch shape
+ * (CTA threads in {64, 128} x shared-memory atoms per lane in {8 .. 32}; a
+ * ligand of n atoms then runs with the smallest L in {1, 2, 4, 8} lanes per
+ * pose with L * atoms_per_lane >= n), picks the fastest (ties to the earlier
+ * shape), records the table and keeps the pick on the ligand set: later
+ * dock_batch calls with lanes_per_pose = 0 use it. Runs short searches
+ * (min(max(generations, 2), 4) generations) on stream and waits for them;
+ * results do not depend on the shape beyond FP32 summation order.
+ * Errors: DOCK_EINVAL (surrogate mode or forced lanes), DOCK_ENOMEM, DOCK_ECUDA. */
+int dock_autotune(dock_pocket *pocket, dock_ligands *ligands, const dock_search_params *params,
+                  void *stream, dock_tune_table *table);
+
 /* Profiling aid: device time of the search-kernel launches of a job enqueued
  * while the environment variable DOCK_PROFILE_LAUNCHES was set (CUDA events
  * around each generation's launch on the job's stream; no graph). Waits for

@@ -462,6 +462,10 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   cudaStream_t s = (cudaStream_t)stream;
   const int nl = L->n_ligands, pop = sp->pop, gens = sp->generations;
   LaunchCfg cfg;
+  if (L->tuned_threads) {
+    cfg.threads = L->tuned_threads;
+    cfg.atoms_per_lane = L->tuned_apl;
+  }
   if (const char *e = getenv("DOCK_THREADS")) cfg.threads = atoi(e);
   if (const char *e = getenv("DOCK_ATOMS_PER_LANE")) cfg.atoms_per_lane = atoi(e);
   if (forced) cfg.atoms_per_lane = std::max(cfg.atoms_per_lane, (L->max_atoms + forced - 1) / forced);
@@ -567,7 +571,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   J->generations = gens;
   J->final_buf = (gens - 1) & 1;
   CU(cudaEventCreateWithFlags(&J->done, cudaEventDisableTiming));
-  const bool profile = getenv("DOCK_PROFILE_LAUNCHES") != nullptr;
+  const bool profile = getenv("DOCK_PROFILE_LAUNCHES") != nullptr || L->profiling;
 
   SearchArgs A;
   A.ligs = L->d_info;
@@ -960,5 +964,77 @@ extern "C" int dock_features_population(dock_pocket *P, dock_ligands *L, int32_t
   CU(launch_features(F, s));
   // the offsets buffer is reused by later calls: finish before returning
   CU(cudaStreamSynchronize(s));
+  return DOCK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+extern "C" int dock_autotune(dock_pocket *P, dock_ligands *L, const dock_search_params *sp,
+                             void *stream, dock_tune_table *table) {
+  if (!P || !L || !sp || !table) return fail(DOCK_EINVAL, "dock_autotune: NULL argument");
+  if (sp->mode != DOCK_MODE_PLAIN || sp->lanes_per_pose != 0)
+    return fail(DOCK_EINVAL, "dock_autotune: tunes the plain search with lanes_per_pose = 0");
+  CU(cudaSetDevice(L->device));
+  // candidate shapes: CTA threads x shared-memory atoms per lane
+  static const int kThreads[] = {64, 128};
+  static const int kApl[] = {8, 12, 16, 24, 32};
+  dock_tune_table T;
+  memset(&T, 0, sizeof T);
+  const int old_t = L->tuned_threads, old_a = L->tuned_apl;
+  dock_search_params q = *sp;
+  q.generations = std::min(std::max(sp->generations, 2), 4);
+  q.use_graph = 0;
+  q.trace_genotypes = nullptr;
+  q.trace_scores = nullptr;
+  q.timeout_ns = 0;
+  for (int ti = 0; ti < 2; ++ti)
+    for (int ai = 0; ai < 5; ++ai) {
+      const int apl = kApl[ai], thr = kThreads[ti];
+      if (8 * apl < L->max_atoms || search_smem_bytes(thr, apl) > 200 * 1024) continue;
+      L->tuned_threads = thr;
+      L->tuned_apl = apl;
+      L->profiling = true;
+      // time generations >= 1 (GA steps) of a short search, best of two runs
+      double best = 1e30;
+      for (int rep = 0; rep < 2; ++rep) {
+        dock_job *J = nullptr;
+        L->profiling = true;
+        int st = dock_batch(P, L, &q, stream, &J);
+        if (st != DOCK_OK) {
+          L->profiling = false;
+          L->tuned_threads = old_t;
+          L->tuned_apl = old_a;
+          return st;
+        }
+        double ms = 0;
+        int32_t n = 0;
+        st = dock_job_kernel_time(J, &ms, &n);
+        dock_job_destroy(J);
+        L->profiling = false;
+        if (st != DOCK_OK) {
+          L->tuned_threads = old_t;
+          L->tuned_apl = old_a;
+          return st;
+        }
+        if (n > 0) best = std::min(best, ms / n);
+      }
+      if (T.n < DOCK_TUNE_MAX) {
+        T.threads[T.n] = thr;
+        T.atoms_per_lane[T.n] = apl;
+        T.ms_per_generation[T.n] = (float)best;
+        ++T.n;
+      }
+    }
+  L->tuned_threads = old_t;
+  L->tuned_apl = old_a;
+  if (T.n == 0) return fail(DOCK_EINVAL, "dock_autotune: no launch shape fits these ligands");
+  // the pick: fastest measured shape, ties to the earlier entry
+  T.best = 0;
+  for (int i = 1; i < T.n; ++i)
+    if (T.ms_per_generation[i] < T.ms_per_generation[T.best]) T.best = i;
+  L->tuned_threads = T.threads[T.best];
+  L->tuned_apl = T.atoms_per_lane[T.best];
+  *table = T;
   return DOCK_OK;
 }

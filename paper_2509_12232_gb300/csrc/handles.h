@@ -125,6 +125,8 @@ struct dock_ligands {
   int device = 0;
   int n_ligands = 0;
   int max_atoms = 0;
+  int tuned_threads = 0, tuned_apl = 0;  // launch shape chosen by dock_autotune (0: defaults)
+  bool profiling = false;                 // time each generation's launch (autotuner)
   std::vector<LigInfo> info;
   LigInfo *d_info = nullptr;
   float4 *d_atoms = nullptr;      // centred

@@ -59,6 +59,15 @@ class dock_search_params(C.Structure):
                 ("surrogate", C.c_void_p)]
 
 
+DOCK_TUNE_MAX = 16
+
+
+class dock_tune_table(C.Structure):
+    _fields_ = [("n", C.c_int32), ("threads", C.c_int32 * DOCK_TUNE_MAX),
+                ("atoms_per_lane", C.c_int32 * DOCK_TUNE_MAX),
+                ("ms_per_generation", C.c_float * DOCK_TUNE_MAX), ("best", C.c_int32)]
+
+
 class dock_train_params(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float),
                 ("score_clip", C.c_float), ("seed", C.c_uint64)]
@@ -115,6 +124,8 @@ def lib():
         L.dock_ligands_info.argtypes = [vp, P_i32, P_i64, P_i64, P_i64, P_i64, P_i64]
         L.dock_batch_noalloc.argtypes = [vp, vp, C.POINTER(dock_search_params), vp, vp]
         L.dock_features.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp, vp]
+        L.dock_autotune.argtypes = [vp, vp, C.POINTER(dock_search_params), vp,
+                                    C.POINTER(dock_tune_table)]
         L.dock_features_population.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp]
         L.dock_surrogate_create.argtypes = [C.c_uint64, vp, C.POINTER(vp)]
         L.dock_surrogate_destroy.argtypes = [vp]
@@ -132,7 +143,7 @@ def lib():
                      "dock_features_population", "dock_surrogate_create",
                      "dock_surrogate_set_params", "dock_surrogate_get_params",
                      "dock_surrogate_predict", "dock_surrogate_gradients",
-                     "dock_surrogate_train"):
+                     "dock_surrogate_train", "dock_autotune"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -420,3 +431,16 @@ def dock_surrogate_train(s: Surrogate, features, scores, epochs=2, batch=4096, l
     check(lib().dock_surrogate_train(s.handle, _dptr(features), _dptr(scores), n, C.byref(tp),
                                      losses.ctypes.data_as(C.c_void_p), _stream(stream)))
     return losses
+
+
+def dock_autotune(pocket: Pocket, ligands: Ligands, pop: int, generations: int, seed=0,
+                  stream=None) -> dict:
+    """Measure the search kernel's launch shapes on this ligand set and keep
+    the fastest for later dock_batch calls; returns the measured table."""
+    sp = dock_search_params(pop, generations, 0.8, 0.02, seed, 0, 0, 0, None, None,
+                            DOCK_MODE_PLAIN, 0, 0, None)
+    t = dock_tune_table()
+    check(lib().dock_autotune(pocket.handle, ligands.handle, C.byref(sp), _stream(stream), C.byref(t)))
+    rows = [dict(threads=t.threads[i], atoms_per_lane=t.atoms_per_lane[i],
+                 ms_per_generation=t.ms_per_generation[i]) for i in range(t.n)]
+    return dict(table=rows, best=t.best)

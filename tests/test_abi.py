@@ -61,6 +61,7 @@ def test_struct_layouts_match_header(tmp_path):
         "dock_search_params": dock.dock_search_params,
         "dock_result": dock.dock_result,
         "dock_train_params": dock.dock_train_params,
+        "dock_tune_table": dock.dock_tune_table,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dock.h"', "int main(void) {"]
     for name, cls in structs.items():
