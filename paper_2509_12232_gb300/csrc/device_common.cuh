@@ -205,6 +205,81 @@ __device__ __forceinline__ void ga_child(float (&g)[DOCK_MAX_GENES], int k, int 
   if (qmut) quat_normalize(g[3], g[4], g[5], g[6]);
 }
 
+// The same child computed by the L lanes of a group together: the Philox
+// blocks of slot 0 (tournaments, crossover) and slots 1..3 (mutation
+// decisions) are spread over the lanes and exchanged by shuffles; every lane
+// ends with the full genotype, bit-identical to ga_child.
+__device__ __forceinline__ void ga_child_group(float (&g)[DOCK_MAX_GENES], int k, int P,
+                                               const float *prev, const float *score,
+                                               uint64_t thr_c, uint64_t thr_m, uint64_t seed,
+                                               uint64_t lig, uint32_t gen, uint32_t ind, int lane,
+                                               int L, unsigned gmask) {
+  const int G = 7 + k, B = 4 + k;
+  const int nslots = 1 + (G + 7) / 8;  // slot 0 + mutation slots
+  // this lane's slots: lane, lane + L, ... (< nslots)
+  uint32_t tw[7] = {0, 0, 0, 0, 0, 0, 0};
+  uint32_t mask = 0;
+  for (int sl = lane; sl < nslots; sl += L) {
+    const Words8 w = rng_words(seed, lig, gen, ind, (uint32_t)sl);
+    if (sl == 0) {
+#pragma unroll
+      for (int i = 0; i < 7; ++i) tw[i] = w.w[i];
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int gi = (sl - 1) * 8 + e;
+        if (gi < G && (uint64_t)w.w[e] < thr_m) mask |= 1u << gi;
+      }
+    }
+  }
+  // slot 0 lives on lane 0 of the group; the mask bits are spread over lanes
+#pragma unroll
+  for (int i = 0; i < 7; ++i) tw[i] = __shfl_sync(gmask, tw[i], 0, L);
+  for (int o = 1; o < L; o <<= 1) mask |= __shfl_xor_sync(gmask, mask, o, L);
+  const int a1 = pick(tw[0], P), a2 = pick(tw[1], P), b1 = pick(tw[2], P), b2 = pick(tw[3], P);
+  const int pa = better(score, a1, a2) ? a1 : a2;
+  const int pb = better(score, b1, b2) ? b1 : b2;
+  int lo = 0, hi = 0;
+  if ((uint64_t)tw[4] < thr_c) {
+    const int c1 = pick(tw[5], B + 1), c2 = pick(tw[6], B + 1);
+    lo = min(c1, c2);
+    hi = max(c1, c2);
+  }
+  const float *A = prev + (int64_t)pa * G, *Bp = prev + (int64_t)pb * G;
+#pragma unroll
+  for (int e = 0; e < DOCK_MAX_GENES; ++e) {
+    float v = 0.0f;
+    if (e < G) {
+      const int blk = gene_block(e);
+      const float *src = (blk >= lo && blk < hi) ? Bp : A;
+      v = __ldg(src + e);
+    }
+    g[e] = v;
+  }
+  bool qmut = false;
+#pragma unroll 1
+  while (mask) {
+    const int e = __ffs(mask) - 1;
+    mask &= mask - 1;
+    float z = rng_normal(seed, lig, gen, ind, 4 + 2 * e);
+    float sigma = e < 3 ? 1.0f : (e < 7 ? 0.1f : 0.5f);
+    float d = __fmul_rn(sigma, z);
+    qmut |= (e >= 3 && e < 7);
+#pragma unroll
+    for (int ee = 0; ee < DOCK_MAX_GENES; ++ee) {
+      if (ee == e) {
+        float v = __fadd_rn(g[ee], d);
+        if (ee >= 7) {
+          if (v > kPiF) v = __fadd_rn(v, -kTwoPiF);
+          else if (v < -kPiF) v = __fadd_rn(v, kTwoPiF);
+        }
+        g[ee] = v;
+      }
+    }
+  }
+  if (qmut) quat_normalize(g[3], g[4], g[5], g[6]);
+}
+
 // ---------------------------------------------------------------------------
 // Compensated sums
 // ---------------------------------------------------------------------------
@@ -279,9 +354,12 @@ __device__ __forceinline__ float pair_energy(float r2, const float (&rec)[8]) {
 
 
 // Grid lookup of M_t + q E + |q| D split in two halves so other work can run
-// while the loads are in flight: grid_issue computes the cell and issues the
-// two 32-byte (x, y)-cell loads (planes z and z+1), grid_finish interpolates.
-// A point outside the grid box (faces count as inside) gives EOUT.
+// while the loads are in flight: grid_issue computes the cell and fetches the
+// two 32-byte (x, y)-cell records (planes z and z+1) through the texture path
+// (point fetches of float4 elements, no filtering: the interpolation is done
+// here in FP32), which keeps the gathers off the load/store pipe that the
+// coordinate and pair-record traffic uses; grid_finish interpolates. A point
+// outside the grid box (faces count as inside) gives EOUT.
 struct Lookup {
   float c0[8], c1[8];
   float fx, fy, fz, q;
@@ -302,9 +380,14 @@ __device__ __forceinline__ Lookup grid_issue(const GridView &G, int t, float q, 
     L.fz = uz - (float)iz;
     const int nc = G.n - 1;
     const int sg = q < 0.0f ? 1 : 0;
-    const float *base = G.xycell + ((((int64_t)(2 * t + sg) * G.n + iz) * nc + iy) * nc + ix) * 8;
-    ld8(base, L.c0);
-    ld8(base + (int64_t)nc * nc * 8, L.c1);
+    const int e = (int)((((int64_t)(2 * t + sg) * G.n + iz) * nc + iy) * nc + ix) * 2;
+    const int ez = e + nc * nc * 2;
+    const float4 a0 = tex1Dfetch<float4>(G.xytex, e), a1 = tex1Dfetch<float4>(G.xytex, e + 1);
+    const float4 b0 = tex1Dfetch<float4>(G.xytex, ez), b1 = tex1Dfetch<float4>(G.xytex, ez + 1);
+    L.c0[0] = a0.x; L.c0[1] = a0.y; L.c0[2] = a0.z; L.c0[3] = a0.w;
+    L.c0[4] = a1.x; L.c0[5] = a1.y; L.c0[6] = a1.z; L.c0[7] = a1.w;
+    L.c1[0] = b0.x; L.c1[1] = b0.y; L.c1[2] = b0.z; L.c1[3] = b0.w;
+    L.c1[4] = b1.x; L.c1[5] = b1.y; L.c1[6] = b1.z; L.c1[7] = b1.w;
   }
   return L;
 }

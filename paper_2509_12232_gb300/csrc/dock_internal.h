@@ -44,6 +44,7 @@ struct Item {
 
 struct GridView {
   const float4 *maps;   // [n_types][n][n][n] {M_t, E, D, 0}
+  cudaTextureObject_t xytex;  // the xycell records as a linear float4 texture (2 per record)
   const float *xycell;  // [n_types][2][n][n-1][n-1] (x, y)-cell records, 8 floats, 32-byte
                         // aligned: {M, F} at (x,y), (x+1,y), (x,y+1), (x+1,y+1) with
                         // F = E + D (sign 0, for q >= 0) or E - D (sign 1, q < 0), so

@@ -137,8 +137,9 @@ __global__ void __launch_bounds__(kFeatThreads) feat_kernel(const FeatArgs A) {
     if (c >= A.candidates) return;
     row = (int64_t)lig * A.candidates + c;
     const LigInfo li = A.ligs[lig];
-    ga_child(g, li.k, A.pop, A.geno_prev + A.geno_off[lig], A.score_prev + (int64_t)lig * A.pop,
-             A.thr_cross, A.thr_mut, A.seed, li.ligand_id, (uint32_t)A.gen, (uint32_t)c);
+    ga_child_group(g, li.k, A.pop, A.geno_prev + A.geno_off[lig],
+                   A.score_prev + (int64_t)lig * A.pop, A.thr_cross, A.thr_mut, A.seed,
+                   li.ligand_id, (uint32_t)A.gen, (uint32_t)c, lane, kFeatL, group_mask(kFeatL));
     float *out = A.cand_geno + row * DOCK_MAX_GENES;
 #pragma unroll
     for (int e = 0; e < DOCK_MAX_GENES; ++e)

@@ -47,12 +47,14 @@ struct dock_pocket {
   int n_prot = 0;
   float4 *d_maps = nullptr;
   float *d_xycell = nullptr;  // (x, y)-cell records of the FP32 scorer
+  cudaTextureObject_t xytex = 0;  // d_xycell as a linear float4 texture
   float2 *d_fpm = nullptr;    // per node {E + D, E - D}
   int n = 0;
   double ox = 0, oy = 0, oz = 0, h = 0;
   float center[3] = {0, 0, 0};
   float radius = 0;
   ~dock_pocket() {
+    if (xytex) cudaDestroyTextureObject(xytex);
     dfree(d_params);
     dfree(d_prot);
     dfree(d_ptype);
@@ -66,6 +68,7 @@ inline GridView grid_view(const dock_pocket *p) {
   GridView g;
   g.maps = p->d_maps;
   g.xycell = p->d_xycell;
+  g.xytex = p->xytex;
   g.n = p->n;
   g.ox = (float)p->ox;
   g.oy = (float)p->oy;

@@ -66,8 +66,9 @@ __global__ void __launch_bounds__(128, 5) search_kernel(const SearchArgs A) {
 #pragma unroll
         for (int e = 0; e < DOCK_MAX_GENES; ++e) g[e] = e < G ? src[e] : 0.0f;
       } else {
-        ga_child(g, li.k, A.pop, A.geno_prev + goff, A.score_prev + soff, A.thr_cross, A.thr_mut,
-                 A.seed, li.ligand_id, (uint32_t)A.gen, (uint32_t)ind);
+        ga_child_group(g, li.k, A.pop, A.geno_prev + goff, A.score_prev + soff, A.thr_cross,
+                       A.thr_mut, A.seed, li.ligand_id, (uint32_t)A.gen, (uint32_t)ind, lane, L,
+                       group_mask(L));
       }
       float *gout = A.geno_next + goff + (int64_t)ind * G;
 #pragma unroll
