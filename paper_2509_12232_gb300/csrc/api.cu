@@ -292,12 +292,13 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
       const double si = (double)tp[ti].solpar + kHQasp * std::fabs(qi);
       const double sj = (double)tp[tj].solpar + kHQasp * std::fabs(qj);
       H.pair_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
-      const uint32_t ij = (uint32_t)i | ((uint32_t)j << 16);
-      float ijf;
-      std::memcpy(&ijf, &ij, 4);
+      const uint32_t oi = 16u * (uint32_t)i, oj = 16u * (uint32_t)j;
+      float oif, ojf;
+      std::memcpy(&oif, &oi, 4);
+      std::memcpy(&ojf, &oj, 4);
       const float rec[8] = {(float)c12, (float)c6, (float)c10, (float)(w * kHEmax),
                             (float)(kHWElec * kHCoulomb * qi * qj),
-                            (float)(kHWSol * (si * tp[tj].vol + sj * tp[ti].vol)), ijf, 0.0f};
+                            (float)(kHWSol * (si * tp[tj].vol + sj * tp[ti].vol)), oif, ojf};
       H.pair_rec.insert(H.pair_rec.end(), rec, rec + 8);
     }
 }
@@ -449,6 +450,38 @@ struct dock_job {
 };
 
 
+// The launches of one search generation, one per lanes-per-pose group (items
+// [begin, begin + count) of the item list): the first on q, the others on the
+// workspace's side streams, forked from q and joined back, so a group's CTAs
+// take over SMs as the previous group's queue drains.
+struct LaunchGroup {
+  int32_t L, begin, count, blocks;
+};
+
+static cudaError_t enqueue_search(Workspace &W, const SearchArgs &a, const std::vector<LaunchGroup> &groups,
+                                  int threads, cudaStream_t q) {
+  cudaError_t e = cudaSuccess;
+  auto one = [&](size_t i, cudaStream_t st) {
+    SearchArgs b = a;
+    b.items = a.items + groups[i].begin;
+    b.n_items = groups[i].count;
+    b.counter = a.counter + i;
+    return launch_search(b, groups[i].blocks, threads, groups[i].L, st);
+  };
+  if (groups.empty()) return cudaSuccess;
+  if (groups.size() == 1) return one(0, q);
+  if ((e = cudaEventRecord(W.fork, q)) != cudaSuccess) return e;
+  for (size_t i = 1; i < groups.size(); ++i) {
+    if ((e = cudaStreamWaitEvent(W.side[i - 1], W.fork, 0)) != cudaSuccess) return e;
+    if ((e = one(i, W.side[i - 1])) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(W.join[i - 1], W.side[i - 1])) != cudaSuccess) return e;
+  }
+  if ((e = one(0, q)) != cudaSuccess) return e;
+  for (size_t i = 1; i < groups.size(); ++i)
+    if ((e = cudaStreamWaitEvent(q, W.join[i - 1], 0)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
 // Launch configuration of the search kernel: threads per CTA and the smem
 // capacity in atoms per lane; a ligand of n atoms runs with the smallest
 // L in {1, 2, 4, 8} with L * atoms_per_lane >= n.
@@ -516,10 +549,18 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     const float cost = (float)(I.n_pairs + 6 * I.n + 12 * I.k) / Ln + 60.0f;
     for (int t = 0; t < tiles; ++t) items.push_back({cost, Item{l, (int16_t)t, (int8_t)Ln, 0}});
   }
-  std::stable_sort(items.begin(), items.end(),
-                   [](const Keyed &a, const Keyed &b) { return a.cost > b.cost; });
+  // grouped by lanes per pose (one launch per group), largest first in a group
+  std::stable_sort(items.begin(), items.end(), [](const Keyed &a, const Keyed &b) {
+    return a.it.lanes != b.it.lanes ? a.it.lanes > b.it.lanes : a.cost > b.cost;
+  });
   std::vector<Item> host_items(items.size());
   for (size_t i = 0; i < items.size(); ++i) host_items[i] = items[i].it;
+  std::vector<LaunchGroup> groups;
+  for (size_t i = 0; i < host_items.size(); ++i) {
+    if (groups.empty() || groups.back().L != host_items[i].lanes)
+      groups.push_back(LaunchGroup{host_items[i].lanes, (int32_t)i, 0, 0});
+    ++groups.back().count;
+  }
   const size_t n_scores = (size_t)nl * pop;
   // workspace: grown on demand and reused by later batches on this ligand set
   if ((size_t)total_genes > W.geno_cap || !W.geno[0]) {
@@ -544,11 +585,18 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     CU(dalloc(&W.best, (size_t)gens * nl));
     W.best_cap = (size_t)gens * nl;
   }
-  if ((size_t)gens > W.gen_cap || !W.counters) {
+  if ((size_t)gens * 4 > W.gen_cap || !W.counters) {
     dfree(W.counters);
     W.gen_cap = 0;
-    CU(dalloc(&W.counters, (size_t)gens));
-    W.gen_cap = (size_t)gens;
+    CU(dalloc(&W.counters, (size_t)gens * 4));
+    W.gen_cap = (size_t)gens * 4;
+  }
+  if (groups.size() > 1 && !W.fork) {
+    for (int i = 0; i < 3; ++i) {
+      CU(cudaStreamCreateWithFlags(&W.side[i], cudaStreamNonBlocking));
+      CU(cudaEventCreateWithFlags(&W.join[i], cudaEventDisableTiming));
+    }
+    CU(cudaEventCreateWithFlags(&W.fork, cudaEventDisableTiming));
   }
   if (host_items.size() > W.item_cap || !W.items) {
     dfree(W.items);
@@ -571,13 +619,14 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   CU(cudaMemcpyAsync(W.geno_off, goff.data(), sizeof(int64_t) * nl, cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(W.items, host_items.data(), sizeof(Item) * host_items.size(),
                      cudaMemcpyHostToDevice, s));
-  const int smem = search_smem_bytes(cfg.threads, cfg.atoms_per_lane);
-  int per_sm = 0, n_sm = 0;
-  CU(search_occupancy(cfg.threads, smem, &per_sm));
+  int n_sm = 0;
   CU(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, L->device));
-  if (per_sm < 1) return fail(DOCK_EINVAL, "dock_batch: launch shape does not fit an SM");
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm,
-                                                                   (int64_t)host_items.size()));
+  for (LaunchGroup &gr : groups) {
+    int per_sm = 0;
+    CU(search_occupancy(cfg.threads, gr.L, cfg.atoms_per_lane, &per_sm));
+    if (per_sm < 1) return fail(DOCK_EINVAL, "dock_batch: launch shape does not fit an SM");
+    gr.blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, gr.count));
+  }
 
   dock_job *J = new dock_job();
   std::unique_ptr<dock_job> jguard(J);
@@ -712,7 +761,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   };
 
   auto enqueue = [&](cudaStream_t q) -> int {
-    CU(cudaMemsetAsync(W.counters, 0, sizeof(uint32_t) * gens, q));
+    CU(cudaMemsetAsync(W.counters, 0, sizeof(uint32_t) * gens * 4, q));
     CU(cudaMemsetAsync(W.best, 0xFF, sizeof(unsigned long long) * (size_t)gens * nl, q));
     CU(cudaMemsetAsync(W.status, 0, sizeof(int32_t), q));
     CU(cudaMemsetAsync(W.lig_status, 0, sizeof(int32_t) * (size_t)nl, q));
@@ -720,7 +769,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     for (int g = 0; g < gens; ++g) {
       SearchArgs a = A;
       a.gen = g;
-      a.counter = W.counters + g;
+      a.counter = W.counters + (size_t)g * 4;
       a.geno_prev = W.geno[(g + 1) & 1];
       a.geno_next = W.geno[g & 1];
       a.score_prev = W.score[(g + 1) & 1];
@@ -737,10 +786,10 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
         J->ev.push_back(e0);
         J->ev.push_back(e1);
         CU(cudaEventRecord(e0, q));
-        CU(launch_search(a, blocks, cfg.threads, q));
+        CU(enqueue_search(W, a, groups, cfg.threads, q));
         CU(cudaEventRecord(e1, q));
       } else {
-        CU(launch_search(a, blocks, cfg.threads, q));
+        CU(enqueue_search(W, a, groups, cfg.threads, q));
       }
       if (sp->trace_genotypes && total_genes)
         CU(cudaMemcpyAsync(sp->trace_genotypes + (size_t)g * total_genes, W.geno[g & 1],
@@ -766,7 +815,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     put(&A, sizeof A);
     put(&F, sizeof F);
     put(&gens, sizeof gens);
-    put(&blocks, sizeof blocks);
+    put(groups.data(), sizeof(LaunchGroup) * groups.size());
     put(&cfg, sizeof cfg);
     put(&sp->trace_genotypes, sizeof(void *));
     put(&sp->trace_scores, sizeof(void *));

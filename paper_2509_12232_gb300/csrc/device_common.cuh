@@ -209,11 +209,12 @@ __device__ __forceinline__ void ga_child(float (&g)[DOCK_MAX_GENES], int k, int 
 // blocks of slot 0 (tournaments, crossover) and slots 1..3 (mutation
 // decisions) are spread over the lanes and exchanged by shuffles; every lane
 // ends with the full genotype, bit-identical to ga_child.
+template <int L>
 __device__ __forceinline__ void ga_child_group(float (&g)[DOCK_MAX_GENES], int k, int P,
                                                const float *prev, const float *score,
                                                uint64_t thr_c, uint64_t thr_m, uint64_t seed,
                                                uint64_t lig, uint32_t gen, uint32_t ind, int lane,
-                                               int L, unsigned gmask) {
+                                               unsigned gmask) {
   const int G = 7 + k, B = 4 + k;
   const int nslots = 1 + (G + 7) / 8;  // slot 0 + mutation slots
   // this lane's slots: lane, lane + L, ... (< nslots)
@@ -235,6 +236,7 @@ __device__ __forceinline__ void ga_child_group(float (&g)[DOCK_MAX_GENES], int k
   // slot 0 lives on lane 0 of the group; the mask bits are spread over lanes
 #pragma unroll
   for (int i = 0; i < 7; ++i) tw[i] = __shfl_sync(gmask, tw[i], 0, L);
+#pragma unroll
   for (int o = 1; o < L; o <<= 1) mask |= __shfl_xor_sync(gmask, mask, o, L);
   const int a1 = pick(tw[0], P), a2 = pick(tw[1], P), b1 = pick(tw[2], P), b2 = pick(tw[3], P);
   const int pa = better(score, a1, a2) ? a1 : a2;
@@ -344,7 +346,8 @@ __device__ __forceinline__ float pair_energy(float r2, const float (&rec)[8]) {
   const float r = r2c * ir;
   const float ir4 = ir2 * ir2;
   const float ir6 = ir4 * ir2;
-  const float disp = fminf(rec[0] * (ir6 * ir6) - rec[1] * ir6 - rec[2] * (ir6 * ir4), rec[3]);
+  // c12 r^-12 - c6 r^-6 - c10 r^-10 = r^-6 (c12 r^-6 - (c6 + c10 r^-4))
+  const float disp = fminf(ir6 * fmaf(rec[0], ir6, -fmaf(rec[2], ir4, rec[1])), rec[3]);
   const float onek = 1.0f + dK * ex2_ftz(kLb * r);
   const float elec = rec[4] * onek * rcp_ftz((dA * onek + dB) * r);
   const float des = rec[5] * ex2_ftz(kS * r2c);

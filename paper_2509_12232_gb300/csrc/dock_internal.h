@@ -38,7 +38,8 @@ struct Item {
 
 // pair_idx (u32, FP64 path): bits 0-7 atom i, 8-15 atom j, 16 H-bond flag.
 // pair_rec (FP32 path): 8 floats per pair, 32-byte aligned, weights folded in:
-// {c12, c6, c10, cap, qq, ds, bits(i | j << 16), 0} for
+// {c12, c6, c10, cap, qq, ds, bits(16 i), bits(16 j)} (the atoms' byte offsets
+// in a pose's coordinate slot) for
 // E = min(c12 r^-12 - c6 r^-6 - c10 r^-10, cap) + qq / (eps(r) r) + ds exp(-r^2 / 2 sigma^2),
 // c6 = 0 for an H-bond (12-10) pair and c10 = 0 otherwise; cap = w * EMAX.
 
@@ -128,7 +129,9 @@ cudaError_t launch_grid_build_impl(const float4 *prot, const uint8_t *ptype, int
                                    const dock_type_params *params_dev, int n_types, int n,
                                    double ox, double oy, double oz, double h, float4 *maps,
                                    float2 *fpm, cudaStream_t s);
-cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStream_t s);
+// One launch of the search kernel instantiated for L lanes per pose; every
+// item of a.items has a.items[i].lanes == L.
+cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, int L, cudaStream_t s);
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int n_ligands, int pop,
                                  const int64_t *geno_off, const float *genos, const float *scores,

@@ -22,11 +22,11 @@ __device__ __forceinline__ float sel16(const float (&g)[DOCK_MAX_GENES], int j) 
   return v;
 }
 
-// Features of the pose in column `col` by the 8 lanes of a group, into the
+// Features of the pose in `slot` by the 8 lanes of a group, into the
 // group's shared row f[128] (FP32), deterministic: counts by ballots, shell
 // charge sums by shuffle trees in a fixed order.
 __device__ __forceinline__ void pose_features(const float (&g)[DOCK_MAX_GENES], const LigView &V,
-                                              const float4 *col, int SP, int lane, unsigned gmask,
+                                              const float4 *slot, int lane, unsigned gmask,
                                               float cx, float cy, float cz, float radius, float *f) {
   const float inv_w = 8.0f / radius;
   float cnt[7];
@@ -38,7 +38,7 @@ __device__ __forceinline__ void pose_features(const float (&g)[DOCK_MAX_GENES], 
     int bin = -1, sh = -1;
     float q = 0.0f;
     if (a < V.n) {
-      const float4 p = col[a * SP];
+      const float4 p = slot[a];
       const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
       sh = min((int)(sqrtf(dx * dx + dy * dy + dz * dz) * inv_w), 7);
       const int t = V.types[a];
@@ -124,10 +124,9 @@ struct FeatArgs {
 
 template <bool FROM_GA>
 __global__ void __launch_bounds__(kFeatThreads) feat_kernel(const FeatArgs A) {
-  __shared__ float4 s_col[kFeatApl * (kFeatThreads + 8)];
+  __shared__ float4 s_col[slots_bytes(kFeatThreads, kFeatL, kFeatApl) / 16];
   __shared__ float s_f[kFeatSlots][DOCK_N_FEATURES];
   const int lane = threadIdx.x & (kFeatL - 1), slot = threadIdx.x / kFeatL;
-  const int SP = plane_stride(kFeatThreads, kFeatL);
   int lig;
   int64_t row;
   float g[DOCK_MAX_GENES];
@@ -137,9 +136,10 @@ __global__ void __launch_bounds__(kFeatThreads) feat_kernel(const FeatArgs A) {
     if (c >= A.candidates) return;
     row = (int64_t)lig * A.candidates + c;
     const LigInfo li = A.ligs[lig];
-    ga_child_group(g, li.k, A.pop, A.geno_prev + A.geno_off[lig],
-                   A.score_prev + (int64_t)lig * A.pop, A.thr_cross, A.thr_mut, A.seed,
-                   li.ligand_id, (uint32_t)A.gen, (uint32_t)c, lane, kFeatL, group_mask(kFeatL));
+    ga_child_group<kFeatL>(g, li.k, A.pop, A.geno_prev + A.geno_off[lig],
+                           A.score_prev + (int64_t)lig * A.pop, A.thr_cross, A.thr_mut, A.seed,
+                           li.ligand_id, (uint32_t)A.gen, (uint32_t)c, lane,
+                           group_mask<kFeatL>());
     float *out = A.cand_geno + row * DOCK_MAX_GENES;
 #pragma unroll
     for (int e = 0; e < DOCK_MAX_GENES; ++e)
@@ -165,11 +165,11 @@ __global__ void __launch_bounds__(kFeatThreads) feat_kernel(const FeatArgs A) {
   }
   const LigInfo li = A.ligs[lig];
   const LigView V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors);
-  const unsigned gmask = group_mask(kFeatL);
-  float4 *col = s_col + slot;
-  apply_pose(g, V, A.moves, A.cx, A.cy, A.cz, col, SP, lane, kFeatL, gmask);
+  const unsigned gmask = group_mask<kFeatL>();
+  float4 *sl = s_col + slot * slot_stride(kFeatL, kFeatApl);
+  apply_pose<kFeatL>(g, V, A.moves, A.cx, A.cy, A.cz, sl, lane, gmask);
   float *f = s_f[slot];
-  pose_features(g, V, col, SP, lane, gmask, A.cx, A.cy, A.cz, A.radius, f);
+  pose_features(g, V, sl, lane, gmask, A.cx, A.cy, A.cz, A.radius, f);
   __syncwarp(gmask);
   // 128 values -> BF16, 16 per lane (two 16-byte stores)
   __nv_bfloat16 *out = A.features + row * DOCK_N_FEATURES + lane * 16;
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kFeatThreads) feat_kernel(const FeatArgs A) {
   reinterpret_cast<uint4 *>(out)[0] = make_uint4(w[0], w[1], w[2], w[3]);
   reinterpret_cast<uint4 *>(out)[1] = make_uint4(w[4], w[5], w[6], w[7]);
   if (!FROM_GA && A.scores) {
-    const float sc = score_posed(V, A.grid, col, SP, lane, kFeatL, gmask, nullptr);
+    const float sc = score_posed<kFeatL>(V, A.grid, sl, lane, gmask, nullptr);
     if (lane == 0) A.scores[row] = sc;
   }
 }

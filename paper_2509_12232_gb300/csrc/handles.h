@@ -18,7 +18,7 @@ int dk_surrogate_predict_raw(dock_surrogate *S, const uint16_t *features, int64_
 namespace dk {
 // Records the message returned by dock_last_error() for this thread; returns st.
 int vset_error(int st, const char *fmt, va_list ap);
-cudaError_t search_occupancy(int threads, int smem, int *blocks_per_sm);
+cudaError_t search_occupancy(int threads, int L, int atoms_per_lane, int *blocks_per_sm);
 cudaError_t launch_set_deadline(uint64_t *deadline, uint64_t timeout_ns, cudaStream_t s);
 }  // namespace dk
 
@@ -97,6 +97,10 @@ struct Workspace {
   int32_t *kept_lig = nullptr;
   size_t feat_off_cap = 0;
   int64_t *feat_off = nullptr;  // genotype offsets for dock_features_population
+  // side streams and events: the per-lanes-per-pose launches of a generation
+  // run concurrently, forked from the caller's stream and joined back
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
   // cached graph
   cudaGraphExec_t graph = nullptr;
   std::vector<uint8_t> graph_key;
@@ -121,6 +125,11 @@ struct Workspace {
     dfree(kept_lig);
     dfree(feat_off);
     if (graph) cudaGraphExecDestroy(graph);
+    for (int i = 0; i < 3; ++i) {
+      if (side[i]) cudaStreamDestroy(side[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
   }
 };
 

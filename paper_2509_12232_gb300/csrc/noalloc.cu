@@ -34,13 +34,14 @@ int fail(int st, const char *fmt, ...) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Work items of all ligands in input order (no largest-first sort here), and
-// the genotype offsets; a single thread, at most DOCK_NOALLOC_MAX_LIGANDS
-// ligands.
+// Work items of all ligands, grouped by lanes per pose (8, 4, 2, 1; input
+// order within a group, group g starting at item group_begin[g]), and the
+// genotype offsets; a single thread, at most DOCK_NOALLOC_MAX_LIGANDS ligands.
 __global__ void noalloc_items_kernel(const LigInfo *ligs, int n_ligands, int pop, int threads,
-                                     int atoms_per_lane, Item *items, int64_t *geno_off) {
+                                     int atoms_per_lane, int4 group_begin, Item *items,
+                                     int64_t *geno_off) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  int it = 0;
+  int next[4] = {group_begin.x, group_begin.y, group_begin.z, group_begin.w};
   int64_t g = 0;
   for (int l = 0; l < n_ligands; ++l) {
     const LigInfo I = ligs[l];
@@ -48,8 +49,9 @@ __global__ void noalloc_items_kernel(const LigInfo *ligs, int n_ligands, int pop
     g += (int64_t)pop * (7 + I.k);
     int L = 1;
     while (L * atoms_per_lane < I.n && L < 8) L <<= 1;
+    const int grp = L == 8 ? 0 : (L == 4 ? 1 : (L == 2 ? 2 : 3));
     const int S = threads / L;
-    for (int t = 0; t * S < pop; ++t) items[it++] = Item{l, (int16_t)t, (int8_t)L, 0};
+    for (int t = 0; t * S < pop; ++t) items[next[grp]++] = Item{l, (int16_t)t, (int8_t)L, 0};
   }
 }
 
@@ -97,10 +99,13 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
   if (L->max_atoms > 8 * apl) apl = (L->max_atoms + 7) / 8;
   // sizes of the working buffers
   int64_t total_genes = 0, n_items = 0;
+  int64_t group_items[4] = {0, 0, 0, 0};  // lanes per pose 8, 4, 2, 1
   for (int l = 0; l < nl; ++l) {
     const LigInfo &I = L->info[l];
     total_genes += (int64_t)pop * (7 + I.k);
-    const int S = threads / lanes_for(I.n, apl, 0);
+    const int Ln = lanes_for(I.n, apl, 0);
+    const int S = threads / Ln;
+    group_items[Ln == 8 ? 0 : (Ln == 4 ? 1 : (Ln == 2 ? 2 : 3))] += (pop + S - 1) / S;
     n_items += (pop + S - 1) / S;
   }
   const size_t n_scores = (size_t)nl * pop;
@@ -110,7 +115,7 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
   const size_t o_sc0 = off; off = align256(off + sizeof(float) * n_scores);
   const size_t o_sc1 = off; off = align256(off + sizeof(float) * n_scores);
   const size_t o_best = off; off = align256(off + sizeof(unsigned long long) * (size_t)gens * nl);
-  const size_t o_cnt = off; off = align256(off + sizeof(uint32_t) * gens);
+  const size_t o_cnt = off; off = align256(off + sizeof(uint32_t) * gens * 4);
   const size_t o_items = off; off = align256(off + sizeof(Item) * n_items);
   const size_t o_goff = off; off = align256(off + sizeof(int64_t) * nl);
   const size_t o_stat = off; off = align256(off + sizeof(int32_t));
@@ -132,13 +137,23 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
   uint64_t *deadline = (uint64_t *)(S0 + o_dl);
   int32_t *lig_status = (int32_t *)(S0 + o_lst);
 
-  const int smem = search_smem_bytes(threads, apl);
-  int per_sm = 0, n_sm = 0;
-  if ((e = search_occupancy(threads, smem, &per_sm)) != cudaSuccess ||
-      (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, L->device)) != cudaSuccess)
+  // one launch per non-empty lanes-per-pose group, one after another
+  static const int kGroupL[4] = {8, 4, 2, 1};
+  int group_begin[4];
+  int group_blocks[4] = {0, 0, 0, 0};
+  int n_sm = 0;
+  if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, L->device)) != cudaSuccess)
     return fail(DOCK_ECUDA, "dock_batch_noalloc: %s", cudaGetErrorString(e));
-  if (per_sm < 1) return fail(DOCK_EINVAL, "dock_batch_noalloc: launch shape does not fit an SM");
-  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, n_items));
+  for (int g = 0, b = 0; g < 4; b += (int)group_items[g], ++g) {
+    group_begin[g] = b;
+    if (!group_items[g]) continue;
+    int per_sm = 0;
+    if ((e = search_occupancy(threads, kGroupL[g], apl, &per_sm)) != cudaSuccess)
+      return fail(DOCK_ECUDA, "dock_batch_noalloc: %s", cudaGetErrorString(e));
+    if (per_sm < 1) return fail(DOCK_EINVAL, "dock_batch_noalloc: launch shape does not fit an SM");
+    group_blocks[g] = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm,
+                                                                    group_items[g]));
+  }
   cudaStream_t s = (cudaStream_t)stream;
 
   SearchArgs A;
@@ -185,24 +200,32 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
       return fail(DOCK_ECUDA, "dock_batch_noalloc: %s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
   // the array keeps the previous call's contents: clear what starts at zero
-  NA_CU(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * gens, s));
+  NA_CU(cudaMemsetAsync(counters, 0, sizeof(uint32_t) * gens * 4, s));
   NA_CU(cudaMemsetAsync(best, 0xFF, sizeof(unsigned long long) * (size_t)gens * nl, s));
   NA_CU(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
   if (nl) NA_CU(cudaMemsetAsync(lig_status, 0, sizeof(int32_t) * nl, s));
-  noalloc_items_kernel<<<1, 32, 0, s>>>(L->d_info, nl, pop, threads, apl, items, goff);
+  noalloc_items_kernel<<<1, 32, 0, s>>>(
+      L->d_info, nl, pop, threads, apl,
+      make_int4(group_begin[0], group_begin[1], group_begin[2], group_begin[3]), items, goff);
   NA_CU(cudaGetLastError());
   if (sp->timeout_ns) NA_CU(launch_set_deadline(deadline, sp->timeout_ns, s));
   for (int g = 0; g < gens; ++g) {
     SearchArgs a = A;
     a.gen = g;
-    a.counter = counters + g;
     a.geno_prev = geno[(g + 1) & 1];
     a.geno_next = geno[g & 1];
     a.score_prev = score[(g + 1) & 1];
     a.score_next = score[g & 1];
     a.best_prev = g ? best + (size_t)(g - 1) * nl : nullptr;
     a.best_next = best + (size_t)g * nl;
-    NA_CU(launch_search(a, blocks, threads, s));
+    for (int gr = 0; gr < 4; ++gr) {
+      if (!group_items[gr]) continue;
+      SearchArgs b = a;
+      b.items = items + group_begin[gr];
+      b.n_items = (int32_t)group_items[gr];
+      b.counter = counters + (size_t)g * 4 + gr;
+      NA_CU(launch_search(b, group_blocks[gr], threads, kGroupL[gr], s));
+    }
     if (sp->trace_genotypes && total_genes)
       NA_CU(cudaMemcpyAsync(sp->trace_genotypes + (size_t)g * total_genes, geno[g & 1],
                             sizeof(float) * total_genes, cudaMemcpyDeviceToDevice, s));

@@ -1,22 +1,24 @@
 // Device functions of the pose (Algorithm 1) and score (Algorithm 2) shared
-// by the search, scoring and feature kernels.
+// by the search, scoring and feature kernels. L, the number of lanes that
+// share a pose, is a template parameter (1, 2, 4 or 8).
 #pragma once
 
 #include "device_common.cuh"
 
 namespace dk {
 
-// Coordinate rows: L * atoms_per_lane rows (atoms) by SP float4 columns (pose
-// slots). For L > 1 the stride SP is an odd multiple of 8 / L, so each
-// quarter-warp phase of a 16-byte shared load (2, 4 or 8 lanes of consecutive
-// atoms) touches distinct bank groups; rows * SP <= atoms_per_lane * (T + 8).
-__host__ __device__ __forceinline__ int plane_stride(int threads, int L) {
-  const int S = threads / L;
-  if (L == 1) return S;
-  const int w = 8 / L;
-  return ((S / w) & 1) ? S : S + w;
+// Coordinate slots in shared memory: pose slot s owns float4 rows
+// [s * SS, s * SS + L * apl), atom a at row a (byte offset 16 a), with
+// SS = (L * apl rounded up to 8) + (L mod 8). The 16-byte loads of a
+// quarter warp (8 / L slots x L lanes reading consecutive atoms of their own
+// slot) then fall on distinct bank groups.
+__host__ __device__ constexpr int slot_stride(int L, int apl) {
+  return ((L * apl + 7) & ~7) + (L & 7);
 }
 
+__host__ __device__ constexpr int slots_bytes(int threads, int L, int apl) {
+  return (threads / L) * slot_stride(L, apl) * 16;
+}
 
 struct LigView {
   const float4 *atoms;      // this ligand's atoms (centred) + charge
@@ -40,36 +42,42 @@ __device__ __forceinline__ LigView lig_view(const LigInfo &li, const float4 *ato
   return v;
 }
 
-// Pair terms in row-major pair order: the coordinates of atom i stay in
-// registers while consecutive pairs of a lane share it.
+__device__ __forceinline__ float4 slot_row(const float4 *slot, uint32_t byte_off) {
+  return *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(slot) + byte_off);
+}
+
+// Pair terms of one lane, pairs lane, lane + L, ... of the row-major list:
+// consecutive pairs of a lane mostly share atom i, whose coordinates stay in
+// registers. The record carries the byte offsets of both atoms in the slot.
+template <int L>
 struct PairWalker {
-  const LigView &V;
-  const float4 *col;
-  int SP;
-  int last_i = -1;
+  const float *rec;  // this lane's first record
+  const float4 *slot;
+  uint32_t last_i = 0xffffffffu;
   float4 ci;
-  __device__ __forceinline__ PairWalker(const LigView &v, const float4 *c, int sp)
-      : V(v), col(c), SP(sp) {}
-  __device__ __forceinline__ float term(int p) {
-    float rec[8];
-    ld8(V.pair_rec + (int64_t)p * 8, rec);
-    const uint32_t ij = __float_as_uint(rec[6]);
-    const int i = (int)(ij & 0xffffu);
-    if (i != last_i) {
-      ci = col[i * SP];
-      last_i = i;
+  __device__ __forceinline__ PairWalker(const LigView &v, const float4 *s, int lane)
+      : rec(v.pair_rec + lane * 8), slot(s) {}
+  // m: the lane's pair counter (pair lane + m L)
+  __device__ __forceinline__ float term(int m) {
+    float r[8];
+    ld8(rec + m * (8 * L), r);
+    const uint32_t oi = __float_as_uint(r[6]);
+    if (oi != last_i) {
+      ci = slot_row(slot, oi);
+      last_i = oi;
     }
-    const float4 b = col[(int)(ij >> 16) * SP];
+    const float4 b = slot_row(slot, __float_as_uint(r[7]));
     const float dx = ci.x - b.x, dy = ci.y - b.y, dz = ci.z - b.z;
-    return pair_energy(dx * dx + dy * dy + dz * dz, rec);
+    return pair_energy(dx * dx + dy * dy + dz * dz, r);
   }
 };
 
 // Algorithm 1 for one genotype by a group of L lanes: the posed coordinates
-// go to column `col` (stride SP) of the shared rows.
+// go to the pose's slot.
+template <int L>
 __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], const LigView &V,
                                            const uint8_t *moves, float cx, float cy, float cz,
-                                           float4 *col, int SP, int lane, int L, unsigned gmask) {
+                                           float4 *slot, int lane, unsigned gmask) {
   // ---- Algorithm 1: rigid motion about the ligand centroid ----------------
   float qw = g[3], qx = g[4], qy = g[5], qz = g[6];
   const float inv = rsqrt_ftz(qw * qw + qx * qx + qy * qy + qz * qz);
@@ -83,9 +91,9 @@ __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], con
   const float tx = cx + g[0], ty = cy + g[1], tz = cz + g[2];
   for (int a = lane; a < V.n; a += L) {
     const float4 p = __ldg(V.atoms + a);
-    col[a * SP] = make_float4(r00 * p.x + r01 * p.y + r02 * p.z + tx,
-                              r10 * p.x + r11 * p.y + r12 * p.z + ty,
-                              r20 * p.x + r21 * p.y + r22 * p.z + tz, 0.0f);
+    slot[a] = make_float4(r00 * p.x + r01 * p.y + r02 * p.z + tx,
+                          r10 * p.x + r11 * p.y + r12 * p.z + ty,
+                          r20 * p.x + r21 * p.y + r22 * p.z + tz, 0.0f);
   }
   __syncwarp(gmask);
   // ---- torsions root to leaf, each about the current bond axis ------------
@@ -93,7 +101,7 @@ __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], con
   for (int j = 0; j < DOCK_MAX_TORSIONS; ++j) {
     if (j < V.k) {
       const TorInfo T = V.tors[j];
-      const float4 pa = col[T.a * SP], pb = col[T.b * SP];
+      const float4 pa = slot[T.a], pb = slot[T.b];
       float ux = pb.x - pa.x, uy = pb.y - pa.y, uz = pb.z - pa.z;
       const float il = rsqrt_ftz(ux * ux + uy * uy + uz * uz);
       ux *= il; uy *= il; uz *= il;
@@ -106,51 +114,53 @@ __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], con
       const uint8_t *mv = moves + T.move_off;
       for (int m = lane; m < T.n_move; m += L) {
         const int at = mv[m];
-        const float4 p = col[at * SP];
+        const float4 p = slot[at];
         const float vx = p.x - pa.x, vy = p.y - pa.y, vz = p.z - pa.z;
-        col[at * SP] = make_float4(pa.x + m00 * vx + m01 * vy + m02 * vz,
-                                   pa.y + m10 * vx + m11 * vy + m12 * vz,
-                                   pa.z + m20 * vx + m21 * vy + m22 * vz, 0.0f);
+        slot[at] = make_float4(pa.x + m00 * vx + m01 * vy + m02 * vz,
+                               pa.y + m10 * vx + m11 * vy + m12 * vz,
+                               pa.z + m20 * vx + m21 * vy + m22 * vz, 0.0f);
       }
       __syncwarp(gmask);
     }
   }
 }
 
-// Algorithm 2 for the posed ligand in column `col`: every lane of the group
-// returns the same FP32 score.
-__device__ __forceinline__ float score_posed(const LigView &V, const GridView &G, float4 *col, int SP,
-                                             int lane, int L, unsigned gmask, float *coords_out) {
+// Algorithm 2 for the posed ligand in `slot`: every lane of the group returns
+// the same FP32 score.
+template <int L>
+__device__ __forceinline__ float score_posed(const LigView &V, const GridView &G,
+                                             const float4 *slot, int lane, unsigned gmask,
+                                             float *coords_out) {
   // ---- Algorithm 2: each grid lookup (inter-energy of one atom) is issued,
-  // ---- a share of the intra pairs runs while its loads are in flight, then
-  // ---- the lookup is interpolated ------------------------------------------
+  // ---- a share of the intra pairs (whole blocks of four) runs while its
+  // ---- loads are in flight, then the lookup is interpolated ----------------
   Kahan acc;
-  PairWalker W(V, col, SP);
+  PairWalker<L> W(V, slot, lane);
   const int na = V.n > lane ? (V.n - lane + L - 1) / L : 0;               // atoms lane + k L
   const int np_l = V.n_pairs > lane ? (V.n_pairs - lane + L - 1) / L : 0;  // pairs lane + m L
+  const int ppa = na > 0 ? (((np_l + na - 1) / na) + 3) & ~3 : 0;          // pairs per atom
   int m = 0;
   for (int k = 0; k < na; ++k) {
     const int a = lane + k * L;
-    const float4 pa = col[a * SP];
+    const float4 pa = slot[a];
     const Lookup lk = grid_issue(G, V.types[a], __ldg(&V.atoms[a].w), pa.x, pa.y, pa.z);
     if (coords_out) {
       coords_out[3 * a] = pa.x;
       coords_out[3 * a + 1] = pa.y;
       coords_out[3 * a + 2] = pa.z;
     }
-    const int m_end = (int)(((int64_t)(k + 1) * np_l) / na);
+    const int m_end = min(np_l, m + ppa);
     for (; m + 3 < m_end; m += 4) {
-      const int p = lane + m * L;
-      const float e0 = W.term(p), e1 = W.term(p + L);
-      const float e2 = W.term(p + 2 * L), e3 = W.term(p + 3 * L);
+      const float e0 = W.term(m), e1 = W.term(m + 1);
+      const float e2 = W.term(m + 2), e3 = W.term(m + 3);
       acc.add((e0 + e1) + (e2 + e3));
     }
-    for (; m < m_end; ++m) acc.add(W.term(lane + m * L));
     acc.add(grid_finish(lk));
   }
-  for (; m < np_l; ++m) acc.add(W.term(lane + m * L));
+  for (; m < np_l; ++m) acc.add(W.term(m));
   // ---- combine the group's compensated sums --------------------------------
   float s = acc.s, c = acc.c;
+#pragma unroll
   for (int off = 1; off < L; off <<= 1) {
     const float so = __shfl_xor_sync(gmask, s, off);
     const float co = __shfl_xor_sync(gmask, c, off);
@@ -163,15 +173,17 @@ __device__ __forceinline__ float score_posed(const LigView &V, const GridView &G
   return __fsub_rn(s, c);
 }
 
+template <int L>
 __device__ __forceinline__ float pose_and_score(const float (&g)[DOCK_MAX_GENES], const LigView &V,
                                                 const uint8_t *moves, const GridView &G, float cx,
-                                                float cy, float cz, float4 *col, int SP, int lane,
-                                                int L, unsigned gmask, float *coords_out) {
-  apply_pose(g, V, moves, cx, cy, cz, col, SP, lane, L, gmask);
-  return score_posed(V, G, col, SP, lane, L, gmask, coords_out);
+                                                float cy, float cz, float4 *slot, int lane,
+                                                unsigned gmask, float *coords_out) {
+  apply_pose<L>(g, V, moves, cx, cy, cz, slot, lane, gmask);
+  return score_posed<L>(V, G, slot, lane, gmask, coords_out);
 }
 
-__device__ __forceinline__ unsigned group_mask(int L) {
+template <int L>
+__device__ __forceinline__ unsigned group_mask() {
   if (L >= 32) return 0xffffffffu;
   const unsigned base = (threadIdx.x & 31) & ~(unsigned)(L - 1);
   return ((1u << L) - 1u) << base;
