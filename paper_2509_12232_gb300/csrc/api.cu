@@ -164,8 +164,9 @@ extern "C" int dock_pocket_grid(const dock_pocket *p, int32_t *n, float origin[3
 
 namespace {
 struct LigHost {
-  std::vector<uint32_t> pair_idx;
-  std::vector<float> pair_rec;   // 8 per pair
+  std::vector<uint32_t> pair_idx;  // pairs the poses change, then the pose-invariant ones
+  int n_var = 0;                   // pairs the poses change
+  std::vector<float> pair_rec;   // 8 per pair the poses change
   std::vector<TorInfo> tors;   // move_off relative to this ligand's moves
   std::vector<uint8_t> moves;
   double cent[3];
@@ -267,6 +268,21 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
       for (int ch : kids[a]) visit(ch);
     }
   }
+  // a pair's distance changes with a torsion that moves one of its atoms and
+  // not the other, unless the other lies on the torsion's axis
+  std::vector<uint8_t> moved((size_t)k * n, 0);
+  for (int t = 0; t < k; ++t)
+    for (int m = 0; m < H.tors[t].n_move; ++m) moved[(size_t)t * n + H.moves[H.tors[t].move_off + m]] = 1;
+  auto pose_invariant = [&](int i, int j) {
+    for (int t = 0; t < k; ++t) {
+      const uint8_t mi = moved[(size_t)t * n + i], mj = moved[(size_t)t * n + j];
+      if (mi == mj) continue;
+      const int still = mi ? j : i;
+      if (still != H.tors[t].a && still != H.tors[t].b) return false;
+    }
+    return true;
+  };
+  std::vector<uint32_t> inv_idx;
   const dock_type_params *tp = P->params.data();
   for (int i = 0; i < n; ++i)
     for (int j = i + 1; j < n; ++j) {
@@ -291,7 +307,12 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
       }
       const double si = (double)tp[ti].solpar + kHQasp * std::fabs(qi);
       const double sj = (double)tp[tj].solpar + kHQasp * std::fabs(qj);
-      H.pair_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
+      const uint32_t idx = (uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16);
+      if (pose_invariant(i, j)) {
+        inv_idx.push_back(idx);
+        continue;
+      }
+      H.pair_idx.push_back(idx);
       const uint32_t oi = 16u * (uint32_t)i, oj = 16u * (uint32_t)j;
       float oif, ojf;
       std::memcpy(&oif, &oi, 4);
@@ -301,6 +322,8 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
                             (float)(kHWSol * (si * tp[tj].vol + sj * tp[ti].vol)), oif, ojf};
       H.pair_rec.insert(H.pair_rec.end(), rec, rec + 8);
     }
+  H.n_var = (int)H.pair_idx.size();
+  H.pair_idx.insert(H.pair_idx.end(), inv_idx.begin(), inv_idx.end());
 }
 
 template <typename F>
@@ -346,24 +369,27 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   L->n_ligands = nl;
   L->info.resize((size_t)nl);
   const int n_atoms = nl ? b->atom_off[nl] : 0;
-  int64_t np = 0, nm = 0, nt = 0;
+  int64_t np = 0, nvar = 0, nm = 0, nt = 0;
   for (int l = 0; l < nl; ++l) {
     LigInfo &I = L->info[l];
     I.atom_off = b->atom_off[l];
     I.n = b->atom_off[l + 1] - b->atom_off[l];
     I.k = b->tors_off[l + 1] - b->tors_off[l];
     I.pair_off = (int32_t)np;
-    I.n_pairs = (int32_t)H[l].pair_idx.size();
+    I.n_pairs = H[l].n_var;
+    I.n_pairs_all = (int32_t)H[l].pair_idx.size();
+    I.intra_const = 0.0f;  // set on the device below
     I.tors_off = (int32_t)nt;
     I.ligand_id = b->ligand_id[l];
     for (auto &T : H[l].tors) T.move_off += (int32_t)nm;
-    np += I.n_pairs;
+    np += I.n_pairs_all;
+    nvar += I.n_pairs;
     nm += (int64_t)H[l].moves.size();
     nt += I.k;
     L->max_atoms = std::max(L->max_atoms, I.n);
   }
   if (np > INT32_MAX || nm > INT32_MAX) return fail(DOCK_EINVAL, "dock_load_ligands: batch too large");
-  L->total_pairs = np;
+  L->total_pairs = nvar;
   std::vector<float4> atoms((size_t)n_atoms), raw((size_t)n_atoms);
   std::vector<double> cent((size_t)nl * 3);
   std::vector<uint32_t> pidx((size_t)np);
@@ -407,6 +433,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   CU(up(L->d_pair_rec, prec.data(), sizeof(float) * 8 * np));
   CU(up(L->d_tors, tors.data(), sizeof(TorInfo) * nt));
   CU(up(L->d_moves, moves.data(), (size_t)nm));
+  CU(launch_intra_const(L->d_info, nl, L->d_atoms_raw, L->d_types, L->d_pair_idx, P->d_params, s));
   CU(cudaStreamSynchronize(s));
   L->total_atoms = n_atoms;
   L->total_tors = nt;

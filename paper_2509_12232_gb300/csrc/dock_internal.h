@@ -9,13 +9,20 @@
 namespace dk {
 
 // Per-ligand record, pop-independent (built by dock_load_ligands).
+// Included intra pairs come in two runs: the n_pairs pairs whose distance the
+// torsions change (pair_rec and pair_idx), then n_pairs_all - n_pairs pairs
+// whose distance no pose changes (pair_idx only: every torsion that separates
+// the two atoms has one of them on its axis). Their energy is one constant per
+// ligand, intra_const, summed in FP64 on the device by dock_load_ligands.
 struct LigInfo {
   int32_t atom_off;   // first atom in the atom arrays
   int32_t n;          // atoms
   int32_t k;          // torsions
   int32_t pair_off;   // first included intra pair
-  int32_t n_pairs;
+  int32_t n_pairs;    // pairs evaluated per pose
   int32_t tors_off;   // first torsion record
+  int32_t n_pairs_all;  // all included pairs (FP64 path)
+  float intra_const;    // energy of the pose-invariant pairs
   uint64_t ligand_id;
 };
 
@@ -129,6 +136,12 @@ cudaError_t launch_grid_build_impl(const float4 *prot, const uint8_t *ptype, int
                                    const dock_type_params *params_dev, int n_types, int n,
                                    double ox, double oy, double oz, double h, float4 *maps,
                                    float2 *fpm, cudaStream_t s);
+// Energy of each ligand's pose-invariant pairs (FP64 sum, stored rounded to
+// FP32 in ligs[l].intra_const); one warp per ligand.
+cudaError_t launch_intra_const(LigInfo *ligs, int n_ligands, const float4 *atoms_raw,
+                               const uint8_t *types, const uint32_t *pair_idx,
+                               const dock_type_params *params, cudaStream_t s);
+
 // One launch of the search kernel instantiated for L lanes per pose; every
 // item of a.items has a.items[i].lanes == L.
 cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, int L, cudaStream_t s);

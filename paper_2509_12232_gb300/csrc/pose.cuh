@@ -26,6 +26,7 @@ struct LigView {
   const float *pair_rec;    // 8 floats per pair
   const TorInfo *tors;
   int n, k, n_pairs;
+  float intra_const;  // energy of the pose-invariant pairs
 };
 
 __device__ __forceinline__ LigView lig_view(const LigInfo &li, const float4 *atoms,
@@ -39,6 +40,7 @@ __device__ __forceinline__ LigView lig_view(const LigInfo &li, const float4 *ato
   v.n = li.n;
   v.k = li.k;
   v.n_pairs = li.n_pairs;
+  v.intra_const = li.intra_const;
   return v;
 }
 
@@ -135,6 +137,7 @@ __device__ __forceinline__ float score_posed(const LigView &V, const GridView &G
   // ---- a share of the intra pairs (whole blocks of four) runs while its
   // ---- loads are in flight, then the lookup is interpolated ----------------
   Kahan acc;
+  if (lane == 0) acc.add(V.intra_const);
   PairWalker<L> W(V, slot, lane);
   const int na = V.n > lane ? (V.n - lane + L - 1) / L : 0;               // atoms lane + k L
   const int np_l = V.n_pairs > lane ? (V.n_pairs - lane + L - 1) / L : 0;  // pairs lane + m L

@@ -44,6 +44,41 @@ __device__ double pair_energy64(const dock_type_params *P, int ti, int tj, doubl
   return disp + elec + des;
 }
 
+// Sum of the pair terms of ligand l's pose-invariant pairs at its input
+// geometry, one warp per ligand; lane-strided partial sums combined by a
+// fixed shuffle tree.
+__global__ void intra_const_kernel(LigInfo *ligs, int n_ligands, const float4 *atoms_raw,
+                                   const uint8_t *types, const uint32_t *pair_idx,
+                                   const dock_type_params *params) {
+  const int l = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (l >= n_ligands) return;
+  const LigInfo li = ligs[l];
+  const float4 *at = atoms_raw + li.atom_off;
+  const uint8_t *ty = types + li.atom_off;
+  double e = 0.0;
+  for (int p = li.n_pairs + lane; p < li.n_pairs_all; p += 32) {
+    const uint32_t idx = pair_idx[li.pair_off + p];
+    const int i = idx & 255, j = (idx >> 8) & 255;
+    const double dx = (double)at[i].x - (double)at[j].x, dy = (double)at[i].y - (double)at[j].y,
+                 dz = (double)at[i].z - (double)at[j].z;
+    e += pair_energy64(params, ty[i], ty[j], (double)at[i].w, (double)at[j].w,
+                       sqrt(dx * dx + dy * dy + dz * dz));
+  }
+  for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+  if (lane == 0) ligs[l].intra_const = (float)e;
+}
+
+cudaError_t launch_intra_const(LigInfo *ligs, int n_ligands, const float4 *atoms_raw,
+                               const uint8_t *types, const uint32_t *pair_idx,
+                               const dock_type_params *params, cudaStream_t s) {
+  if (n_ligands == 0) return cudaSuccess;
+  const int per_block = 8;
+  intra_const_kernel<<<(n_ligands + per_block - 1) / per_block, 32 * per_block, 0, s>>>(
+      ligs, n_ligands, atoms_raw, types, pair_idx, params);
+  return cudaGetLastError();
+}
+
 struct GridView64 {
   const float4 *maps;
   int n;
@@ -119,7 +154,7 @@ __device__ double pose_score_fp64_warp(const float *geno, const LigInfo &li, con
     else
       e += (double)kEout;
   }
-  for (int p = lane; p < li.n_pairs; p += 32) {
+  for (int p = lane; p < li.n_pairs_all; p += 32) {
     const uint32_t idx = F.pair_idx[li.pair_off + p];
     const int i = idx & 255, j = (idx >> 8) & 255;
     const double dx = xyz[3 * i] - xyz[3 * j], dy = xyz[3 * i + 1] - xyz[3 * j + 1],

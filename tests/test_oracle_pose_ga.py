@@ -90,6 +90,37 @@ def test_pose_preserves_bonds_and_fragments(lig):
             np.testing.assert_allclose(d[np.ix_(c, c)], d0[np.ix_(c, c)], atol=1e-12)
 
 
+@pytest.mark.parametrize("lig", ligands(seed=33))
+def test_pose_invariant_pair_rule(lig):
+    """The GPU path sums the included pairs whose distance no pose changes
+    once per ligand: those where every torsion that moves one atom and not
+    the other has the other on its axis. Checked here on the oracle's poses:
+    such pairs keep their input distance, every other pair changes it."""
+    moves, pairs = o.topology(lig)
+    par = lig.a["parent"]
+    axes = [(int(par[b]), int(b)) for b in lig.a["tors_b"]]
+
+    def invariant(i, j):
+        for t, (a, b) in enumerate(axes):
+            if moves[t, i] != moves[t, j]:
+                still = j if moves[t, i] else i
+                if still not in (a, b):
+                    return False
+        return True
+
+    x0 = np.stack([lig.a["x"], lig.a["y"], lig.a["z"]], 1).astype(np.float64)
+    d0 = np.linalg.norm(x0[pairs[:, 0]] - x0[pairs[:, 1]], axis=1)
+    rng = np.random.default_rng(lig.n + 3)
+    dmax = np.zeros(len(pairs))
+    for _ in range(8):
+        xyz = o.pose(lig, random_geno(rng, lig.k), [0.0, 1.0, -2.0])
+        d = np.linalg.norm(xyz[pairs[:, 0]] - xyz[pairs[:, 1]], axis=1)
+        dmax = np.maximum(dmax, np.abs(d - d0))
+    inv = np.array([invariant(int(i), int(j)) for i, j in pairs], bool)
+    assert np.all(dmax[inv] < 1e-9)
+    assert np.all(dmax[~inv] > 1e-4)
+
+
 @pytest.mark.parametrize("lig", ligands())
 def test_pose_orders_agree(lig):
     """Rigid-first (Algorithm 1's order), torsion-first, and leaf-to-root
