@@ -128,9 +128,12 @@ int dock_load_ligands(const dock_pocket *pocket, const dock_ligand_batch *batch,
 void dock_ligands_destroy(dock_ligands *ligands);
 
 /* Sizes of a loaded ligand set, for work accounting: totals over its ligands
- * of atoms, included intra pairs, torsions and torsion-moved atoms (sum over
- * torsions of the atoms each one rotates), and the bytes dock_load_ligands
- * copied to the device. Any output may be NULL. */
+ * of atoms, intra pairs evaluated per pose (the included pairs whose distance
+ * a pose can change; the others, where every torsion separating the two atoms
+ * has one of them on its axis, are summed once per ligand at load time),
+ * torsions and torsion-moved atoms (sum over torsions of the atoms each one
+ * rotates), and the bytes dock_load_ligands copied to the device. Any output
+ * may be NULL. */
 int dock_ligands_info(const dock_ligands *ligands, int32_t *n_ligands, int64_t *n_atoms,
                       int64_t *n_pairs, int64_t *n_torsions, int64_t *n_moved,
                       int64_t *h2d_bytes);
