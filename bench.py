@@ -57,15 +57,16 @@ def env_rank():
 
 def src_hash():
     h = hashlib.sha256()
-    for f in ("search.cu", "device_common.cuh", "dock_internal.h"):
+    for f in ("search.cu", "pose.cuh", "device_common.cuh", "dock_internal.h"):
         with open(os.path.join(ROOT, "paper_2509_12232_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def read_traffic():
-    """DRAM bytes per launch of the search kernel from the committed ncu
-    summary, if it was taken on the current kernel source."""
+    """DRAM bytes per search generation (the search-kernel launches of one
+    generation, one per lanes-per-pose group) from the committed ncu summary,
+    if it was taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "search_kernel_c2.txt")
     if not os.path.exists(p):
         return None
@@ -77,7 +78,7 @@ def read_traffic():
     if kv.get("source_hash") != src_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv["dram_bytes_per_generation"])
     except (KeyError, ValueError):
         return None
 
@@ -320,6 +321,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--ligands", type=int, default=0,
                     help="dock only the first N ligands (profiling runs; not a bench line)")
+    ap.add_argument("--shape", default="",
+                    help="THREADSxATOMS_PER_LANE launch shape instead of dock_autotune's pick "
+                         "(profiling runs)")
     args = ap.parse_args()
     rank, world, local = env_rank()
     if args.impl == "reference":
@@ -351,8 +355,20 @@ def main():
     gl = dock.dock_load_ligands(pocket, *largs, stream=stream)
     info = dock.dock_ligands_info(gl)
     # launch shape of the search kernel: measured on this ligand set (set-up, not timed)
-    tune = dock.dock_autotune(pocket, gl, w.pop, 4, stream=stream)
-    shape = tune["table"][tune["best"]]
+    if args.shape:
+        t_, a_ = (int(v) for v in args.shape.lower().split("x"))
+        shape = {"threads": t_, "atoms_per_lane": a_}
+        os.environ["DOCK_THREADS"], os.environ["DOCK_ATOMS_PER_LANE"] = str(t_), str(a_)
+        picked_by = "--shape"
+    else:
+        tune = dock.dock_autotune(pocket, gl, w.pop, 4, stream=stream)
+        shape = tune["table"][tune["best"]]
+        picked_by = "dock_autotune"
+    # one search launch per lanes-per-pose group L (smallest L in 1, 2, 4, 8
+    # with L * atoms_per_lane >= atoms) and generation
+    apl = shape["atoms_per_lane"]
+    groups = sorted({next(L for L in (1, 2, 4, 8) if L * apl >= n or L == 8)
+                     for n in np.diff(ligs.atom_off)})
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
 
     def step():
@@ -426,16 +442,17 @@ def main():
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12           # TFLOP/s
     mufu_peak = n_sm * 16 * sm_mhz * 1e6 / 1e12                 # Tops/s
     flops_pose, mufu_pose = work_per_pose(info, w.n_ligands)
-    per_launch_s = ms_kernels / 1000.0 / max(n_launch, 1)
-    ach_fp32 = flops_pose * w.pop / per_launch_s / 1e12
-    ach_mufu = mufu_pose * w.pop / per_launch_s / 1e12
+    per_gen_s = ms_kernels / 1000.0 / max(n_launch, 1)
+    ach_fp32 = flops_pose * w.pop / per_gen_s / 1e12
+    ach_mufu = mufu_pose * w.pop / per_gen_s / 1e12
     roof = {"bound": "alu", "achieved": round(ach_fp32, 3), "peak": round(fp32_peak, 2),
             "unit": "TFLOP/s", "frac": round(ach_fp32 / fp32_peak, 4),
             "traffic": read_traffic(), "kernel": "search_kernel",
             "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
             "mufu": {"achieved": round(ach_mufu, 4), "peak": round(mufu_peak, 4), "unit": "Tops/s",
                      "frac": round(ach_mufu / mufu_peak, 4)},
-            "launch_ms": round(per_launch_s * 1000, 4), "launches_timed": n_launch}
+            "generation_ms": round(per_gen_s * 1000, 4), "generations_timed": n_launch,
+            "launches_per_generation": len(groups), "lanes_per_pose_groups": groups}
     line = {"metric": METRIC, "value": round(value, 2), "unit": "ligands/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -444,12 +461,12 @@ def main():
                        "ligands_per_gpu": w.n_ligands, "pop": w.pop, "generations": w.generations,
                        "launch_shape": {"threads": shape["threads"],
                                         "atoms_per_lane": shape["atoms_per_lane"],
-                                        "picked_by": "dock_autotune"}},
+                                        "picked_by": picked_by}},
             "poses_scored_per_s": round(poses_per_step / (ms_step / 1000.0), 1),
             "roofline": roof,
             "e2e": {"value": round(total_ligands / e2e_s, 2), "unit": "ligands/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": args.steps * (w.generations + 1),
+            "gpu_launches": args.steps * (w.generations * len(groups) + 1),
             "clocks": clk}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_baseline_seconds)

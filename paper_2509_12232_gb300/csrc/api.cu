@@ -239,6 +239,8 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
       H.moves.push_back((uint8_t)a);
       for (int ch : kids[a]) stack.push_back(ch);
     }
+    // ascending atom order: the L lanes then rotate mostly consecutive rows
+    std::sort(H.moves.begin() + T.move_off, H.moves.end());
     T.n_move = (int16_t)(H.moves.size() - T.move_off);
     T.a = (uint8_t)par[bb];
     T.b = (uint8_t)bb;
@@ -284,9 +286,51 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
   };
   std::vector<uint32_t> inv_idx;
   const dock_type_params *tp = P->params.data();
+  // Row order of the per-pose pairs: rows i ascending; within a row the j are
+  // permuted so that the pairs at list positions p of one aligned window of 4
+  // (2, 8) have distinct j mod 4 (2, 8) where the row allows it. A pose's L
+  // lanes read the atoms of pairs p .. p + L - 1 together, and distinct j
+  // mod L keep those 16-byte shared-memory rows on distinct bank groups.
+  std::vector<int> row, order;
+  auto window_cost = [&](int pos, int j) {
+    int c = 0;
+    static const int kW[3] = {4, 2, 8}, kWt[3] = {100, 10, 1};
+    for (int w = 0; w < 3; ++w)
+      for (int q = pos - pos % kW[w]; q < pos; ++q)
+        if ((order[2 * q] - j) % kW[w] == 0) c += kWt[w];
+    return c;
+  };
+  for (int i = 0; i < n; ++i) {
+    row.clear();
+    for (int j = i + 1; j < n; ++j)
+      if (dist[(size_t)i * n + j] > 3 && frag[i] != frag[j] && !pose_invariant(i, j)) row.push_back(j);
+    while (!row.empty()) {
+      const int pos = (int)(order.size() / 2);
+      size_t best = 0;
+      int best_c = window_cost(pos, row[0]);
+      for (size_t r = 1; r < row.size() && best_c > 0; ++r) {
+        const int c = window_cost(pos, row[r]);
+        if (c < best_c) {
+          best_c = c;
+          best = r;
+        }
+      }
+      order.push_back(row[best]);
+      order.push_back(i);  // kept in pairs: order[2 p] = j, order[2 p + 1] = i
+      row.erase(row.begin() + (long)best);
+    }
+  }
+  // the pose-invariant pairs (FP64 constant) in plain row order
   for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j) {
-      if (dist[(size_t)i * n + j] <= 3 || frag[i] == frag[j]) continue;
+    for (int j = i + 1; j < n; ++j)
+      if (dist[(size_t)i * n + j] > 3 && frag[i] != frag[j] && pose_invariant(i, j)) {
+        const bool hb = (tp[b->type[a0 + i]].hb_role == 1 && tp[b->type[a0 + j]].hb_role == 2) ||
+                        (tp[b->type[a0 + i]].hb_role == 2 && tp[b->type[a0 + j]].hb_role == 1);
+        inv_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
+      }
+  for (size_t p = 0; p < order.size() / 2; ++p) {
+    {
+      const int j = order[2 * p], i = order[2 * p + 1];
       const int ti = b->type[a0 + i], tj = b->type[a0 + j];
       const double qi = b->q[a0 + i], qj = b->q[a0 + j];
       const bool hb = (tp[ti].hb_role == 1 && tp[tj].hb_role == 2) ||
@@ -307,12 +351,7 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
       }
       const double si = (double)tp[ti].solpar + kHQasp * std::fabs(qi);
       const double sj = (double)tp[tj].solpar + kHQasp * std::fabs(qj);
-      const uint32_t idx = (uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16);
-      if (pose_invariant(i, j)) {
-        inv_idx.push_back(idx);
-        continue;
-      }
-      H.pair_idx.push_back(idx);
+      H.pair_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
       const uint32_t oi = 16u * (uint32_t)i, oj = 16u * (uint32_t)j;
       float oif, ojf;
       std::memcpy(&oif, &oi, 4);
@@ -322,6 +361,7 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
                             (float)(kHWSol * (si * tp[tj].vol + sj * tp[ti].vol)), oif, ojf};
       H.pair_rec.insert(H.pair_rec.end(), rec, rec + 8);
     }
+  }
   H.n_var = (int)H.pair_idx.size();
   H.pair_idx.insert(H.pair_idx.end(), inv_idx.begin(), inv_idx.end());
 }
