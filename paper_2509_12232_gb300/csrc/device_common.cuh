@@ -372,7 +372,8 @@ struct Lookup {
 __device__ __forceinline__ Lookup grid_issue(const GridView &G, int t, float q, float x, float y,
                                              float z) {
   Lookup L;
-  const float ux = (x - G.ox) * G.inv_h, uy = (y - G.oy) * G.inv_h, uz = (z - G.oz) * G.inv_h;
+  // grid coordinates u = x / h - origin / h (one rounding less than (x - o) / h)
+  const float ux = fmaf(x, G.inv_h, G.gx), uy = fmaf(y, G.inv_h, G.gy), uz = fmaf(z, G.inv_h, G.gz);
   const float nm1 = (float)(G.n - 1);
   L.inside = ux >= 0.0f && ux <= nm1 && uy >= 0.0f && uy <= nm1 && uz >= 0.0f && uz <= nm1;
   L.q = q;
@@ -383,8 +384,9 @@ __device__ __forceinline__ Lookup grid_issue(const GridView &G, int t, float q, 
     L.fz = uz - (float)iz;
     const int nc = G.n - 1;
     const int sg = q < 0.0f ? 1 : 0;
-    const int e = (int)((((int64_t)(2 * t + sg) * G.n + iz) * nc + iy) * nc + ix) * 2;
-    const int ez = e + nc * nc * 2;
+    // 32-bit element index: the texture holds at most 2^27 elements
+    const int e = ((((2 * t + sg) * G.n + iz) * nc + iy) * nc + ix) * 2;
+    const int ez = e + G.plane_elems;
     const float4 a0 = tex1Dfetch<float4>(G.xytex, e), a1 = tex1Dfetch<float4>(G.xytex, e + 1);
     const float4 b0 = tex1Dfetch<float4>(G.xytex, ez), b1 = tex1Dfetch<float4>(G.xytex, ez + 1);
     L.c0[0] = a0.x; L.c0[1] = a0.y; L.c0[2] = a0.z; L.c0[3] = a0.w;

@@ -60,6 +60,8 @@ struct GridView {
   int32_t n;            // nodes per axis
   float ox, oy, oz;     // origin
   float inv_h;
+  float gx, gy, gz;     // -origin / h: grid coordinate u = x inv_h + g
+  int32_t plane_elems;  // texture elements of one z plane of records, 2 (n-1)^2
   int32_t n_types;
 };
 

@@ -74,6 +74,10 @@ inline GridView grid_view(const dock_pocket *p) {
   g.oy = (float)p->oy;
   g.oz = (float)p->oz;
   g.inv_h = (float)(1.0 / p->h);
+  g.gx = (float)(-p->ox / p->h);
+  g.gy = (float)(-p->oy / p->h);
+  g.gz = (float)(-p->oz / p->h);
+  g.plane_elems = 2 * (p->n - 1) * (p->n - 1);
   g.n_types = p->n_types;
   return g;
 }
