@@ -323,7 +323,9 @@ int dock_surrogate_set_params(dock_surrogate *surrogate, const float *params, fl
                               float t_std, float t_clip, void *stream);
 int dock_surrogate_get_params(const dock_surrogate *surrogate, float *params, float *t_mean,
                               float *t_std, float *t_clip);
-/* Predicted scores (device FP32 [n]) of device BF16 features [n][128]. */
+/* Predicted scores (device FP32 [n]) of device BF16 features [n][128] (16-byte
+ * aligned), by the fused tensor-core forward pass. Returns once the scores are
+ * written; DOCK_EDEVICE if a device-side wait ran out (those rows are NaN). */
 int dock_surrogate_predict(dock_surrogate *surrogate, const uint16_t *features, int64_t n,
                            float *out, void *stream);
 /* Gradient (device FP32, packed like the parameters) of

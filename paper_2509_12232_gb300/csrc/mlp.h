@@ -48,5 +48,15 @@ cudaError_t adam(float *p, float *m, float *v, const float *g, int n, float lr, 
 cudaError_t cast_weights(const float *W, int in, int out, __nv_bfloat16 *w16, __nv_bfloat16 *wt16,
                          cudaStream_t s);
 
+// Fused forward pass on the tensor cores (mlp_tc.cu): y[r] for rows r < n of
+// X [n][128] (BF16, 16-byte aligned rows), weights wc in the tensor-core
+// layout (canon_weights, canon_weight_elems() BF16 values), biases and w4,
+// b4 from the packed FP32 parameters. A device-side wait that runs out sets
+// *err = 1 and leaves the rows of the skipped tiles untouched.
+cudaError_t canon_weights(const float *p, __nv_bfloat16 *wc, cudaStream_t s);
+int canon_weight_elems();
+cudaError_t fused_forward(const __nv_bfloat16 *X, int64_t n, const __nv_bfloat16 *wc,
+                          const float *params, float *y, int *err, cudaStream_t s);
+
 }  // namespace mlp
 }  // namespace dk

@@ -38,7 +38,6 @@ static int sfail(int st, const char *fmt, ...) {
   } while (0)
 
 namespace {
-constexpr int kPredictChunk = 65536;   // rows per inference chunk
 constexpr int kMaxTrainBatch = 65536;
 
 __global__ void gather_rows_kernel(const __nv_bfloat16 *X, const float *t, const int64_t *idx,
@@ -105,8 +104,15 @@ struct dock_surrogate {
   double *stats = nullptr;
   int step = 0;
   float t_mean = 0.0f, t_std = 1.0f, t_clip = 1e30f;
+  // weights of the fused tensor-core forward pass (refreshed lazily after the
+  // FP32 masters change) and its device error flag
+  __nv_bfloat16 *wc = nullptr;
+  bool wc_valid = false;
+  int *err = nullptr;
   ~dock_surrogate() {
     for (float *q : {p, m, v, g, y, t, part, outg}) if (q) cudaFree(q);
+    if (wc) cudaFree(wc);
+    if (err) cudaFree(err);
     for (int l = 0; l < 3; ++l) {
       if (w16[l]) cudaFree(w16[l]);
       if (wt16[l]) cudaFree(wt16[l]);
@@ -155,6 +161,7 @@ static int ensure_workspace(dock_surrogate *S, int rows) {
 static int refresh_bf16(dock_surrogate *S, cudaStream_t s) {
   for (int l = 0; l < 3; ++l)
     SCU(mlp::cast_weights(S->p + kOffW[l], kIn[l], HIDDEN, S->w16[l], S->wt16[l], s));
+  S->wc_valid = false;
   return DOCK_OK;
 }
 
@@ -215,6 +222,9 @@ extern "C" int dock_surrogate_create(uint64_t seed, void *stream, dock_surrogate
     SCU(cudaMalloc(&S->w16[l], sizeof(__nv_bfloat16) * kIn[l] * HIDDEN));
     SCU(cudaMalloc(&S->wt16[l], sizeof(__nv_bfloat16) * kIn[l] * HIDDEN));
   }
+  SCU(cudaMalloc(&S->wc, sizeof(__nv_bfloat16) * mlp::canon_weight_elems()));
+  SCU(cudaMalloc(&S->err, sizeof(int)));
+  SCU(cudaMemsetAsync(S->err, 0, sizeof(int), s));
   // He-normal weights, zero biases (host draw from the seed, one upload)
   std::vector<float> h(N_PARAMS, 0.0f);
   std::mt19937_64 rng(seed);
@@ -265,22 +275,17 @@ extern "C" int dock_surrogate_get_params(const dock_surrogate *S, float *params,
 
 int dk_surrogate_predict_raw(dock_surrogate *S, const uint16_t *features, int64_t n, float *out,
                              int destandardize, cudaStream_t s) {
+  if (n <= 0) return DOCK_OK;
   const __nv_bfloat16 *F = reinterpret_cast<const __nv_bfloat16 *>(features);
-  int st = ensure_workspace(S, kPredictChunk);
-  if (st != DOCK_OK) return st;
-  for (int64_t r0 = 0; r0 < n; r0 += kPredictChunk) {
-    const int rows_valid = (int)std::min<int64_t>(kPredictChunk, n - r0);
-    const int rows = (rows_valid + 127) / 128 * 128;
-    gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(F + r0 * FEATURES, nullptr, nullptr,
-                                                               n - r0, rows, rows_valid, S->X,
-                                                               nullptr, 0.f, 1.f, 0.f);
-    SCU(cudaGetLastError());
-    if ((st = forward(S, rows, false, s)) != DOCK_OK) return st;
-    if (destandardize)
-      destandardize_kernel<<<(rows_valid + 255) / 256, 256, 0, s>>>(S->y, rows_valid, S->t_mean,
-                                                                    S->t_std, out + r0);
-    else
-      SCU(cudaMemcpyAsync(out + r0, S->y, sizeof(float) * rows_valid, cudaMemcpyDeviceToDevice, s));
+  if (!S->wc_valid) {
+    SCU(mlp::canon_weights(S->p, S->wc, s));
+    S->wc_valid = true;
+  }
+  SCU(cudaMemsetAsync(out, 0xFF, sizeof(float) * n, s));  // NaN in rows a failed tile skips
+  SCU(mlp::fused_forward(F, n, S->wc, S->p, out, S->err, s));
+  if (destandardize) {
+    destandardize_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, (int)n, S->t_mean,
+                                                                      S->t_std, out);
     SCU(cudaGetLastError());
   }
   return DOCK_OK;
@@ -289,9 +294,21 @@ int dk_surrogate_predict_raw(dock_surrogate *S, const uint16_t *features, int64_
 extern "C" int dock_surrogate_predict(dock_surrogate *S, const uint16_t *features, int64_t n,
                                       float *out, void *stream) {
   if (!S || (n > 0 && (!features || !out))) return sfail(DOCK_EINVAL, "dock_surrogate_predict: NULL");
-  if (n < 0) return sfail(DOCK_EINVAL, "dock_surrogate_predict: n < 0");
+  if (n < 0 || n > INT32_MAX) return sfail(DOCK_EINVAL, "dock_surrogate_predict: n out of range");
+  if ((reinterpret_cast<uintptr_t>(features) & 15) != 0)
+    return sfail(DOCK_EINVAL, "dock_surrogate_predict: features not 16-byte aligned");
   SCU(cudaSetDevice(S->device));
-  return dk_surrogate_predict_raw(S, features, n, out, 1, (cudaStream_t)stream);
+  cudaStream_t s = (cudaStream_t)stream;
+  int st = dk_surrogate_predict_raw(S, features, n, out, 1, s);
+  if (st != DOCK_OK) return st;
+  int flag = 0;
+  SCU(cudaMemcpyAsync(&flag, S->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SCU(cudaStreamSynchronize(s));
+  if (flag) {
+    SCU(cudaMemsetAsync(S->err, 0, sizeof(int), s));
+    return sfail(DOCK_EDEVICE, "dock_surrogate_predict: a device wait ran out (rows left NaN)");
+  }
+  return DOCK_OK;
 }
 
 extern "C" int dock_surrogate_gradients(dock_surrogate *S, const uint16_t *features,

@@ -91,6 +91,44 @@ def test_pose_and_score_parity_c1(dock, c1):
     assert np.all(ok64 | (ref["margin"] < 2e-4))
 
 
+def test_exhaustive_lattice_tiny_ligands(dock, c1):
+    """Brute force on tiny inputs: a 6-atom ligand with one torsion (and an
+    intra pair) and a 3-atom rigid one, every pose of a lattice
+    (translation on a 0.5 A grid over [-2, 2]^3 x the 24 rotations of the
+    cube x torsion angles on a 30 degree grid), scored by the GPU and the
+    oracle; every pose must agree, and so must the lattice minimum."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.Generator(np.random.Philox(404))
+    ligs = synth.make_ligands(rng, np.array([6, 3]), np.array([1, 0]), id_base=900)
+    assert [ligs.n_tors(0), ligs.n_tors(1)] == [1, 0]
+    side = OracleSide(c1["pk"], ligs, grid=c1["ora"].grid)
+    assert len(o.topology(side.lig(0))[1]) > 0
+    gl = gpu_ligands(dock, c1["pocket"], ligs)
+    ax = np.arange(-2.0, 2.0001, 0.5)
+    T = np.stack(np.meshgrid(ax, ax, ax, indexing="ij"), -1).reshape(-1, 3)
+    q = Rotation.create_group("O").as_quat()[:, [3, 0, 1, 2]]      # (w, x, y, z)
+    assert q.shape == (24, 4)
+    for l, thetas in ((0, np.deg2rad(np.arange(-180, 180, 30))), (1, np.zeros(1))):
+        k = ligs.n_tors(l)
+        tt, qq, th = np.meshgrid(np.arange(len(T)), np.arange(24), np.arange(len(thetas)), indexing="ij")
+        n = tt.size
+        g = np.zeros((n, 23), np.float32)
+        g[:, :3] = T[tt.ravel()]
+        g[:, 3:7] = q[qq.ravel()]
+        if k:
+            g[:, 7] = thetas[th.ravel()]
+        pl = torch.full((n,), l, dtype=torch.int32, device="cuda")
+        sc = torch.zeros(n, dtype=torch.float32, device="cuda")
+        dock.dock_score(c1["pocket"], gl, pl, to_dev(torch, g), scores=sc)
+        torch.cuda.synchronize()
+        ref = side.score(l, g[:, :7 + k])
+        gpu = sc.cpu().numpy()
+        checked, near, worst, fails = compare_scores(gpu, ref["score"], ref["margin"])
+        assert len(fails) == 0, (l, fails[:5], gpu[fails[:5]], ref["score"][fails[:5]])
+        assert near <= n // 100
+        assert within(gpu.min(), ref["score"].min())
+
+
 def _replay(dock, side, gl, pocket, pop, gens, seed, lanes=0, use_graph=1, ligs_check=None,
             gens_check=None, poses_per_gen=None):
     """Run a traced search; replay the GA on the CPU from the GPU scores."""

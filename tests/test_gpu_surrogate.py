@@ -159,6 +159,35 @@ def test_mlp_predict_matches_oracle(dock, feature_rows):
     assert np.corrcoef(got, ref)[0, 1] > 0.999
 
 
+@pytest.mark.parametrize("n", [1, 127, 129, 50_001])
+def test_mlp_predict_tiles_and_ragged_tail(dock, n):
+    """The fused tensor-core forward pass over many 128-row tiles per CTA and
+    a ragged last tile: every sampled row equals the oracle's network within
+    the BF16 budget, no row is left unwritten, and the result does not depend
+    on how the rows are batched."""
+    S = dock.dock_surrogate_create(seed=11)
+    p32, _, _, _ = dock.dock_surrogate_get_params(S)
+    dock.dock_surrogate_set_params(S, p32, t_mean=1.5, t_std=2.0)
+    g = torch.Generator(device="cuda").manual_seed(n)
+    X = (torch.randn(n, 128, device="cuda", generator=g) * 0.7).to(torch.bfloat16).view(torch.int16)
+    out = torch.zeros(n, dtype=torch.float32, device="cuda")
+    dock.dock_surrogate_predict(S, X, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    rows = np.unique(np.concatenate([np.arange(min(n, 64)), np.arange(max(0, n - 64), n),
+                                     np.random.default_rng(n).integers(0, n, 256)]))
+    ref = o.mlp_forward(oracle_params(p32), bf16_to_f64(X[rows].cpu().numpy().view(np.uint16)))
+    ref = ref * 2.0 + 1.5
+    scale = np.sqrt(np.mean(ref ** 2)) + 1e-6
+    assert np.max(np.abs(got[rows] - ref)) <= 2e-2 * (np.abs(ref) + scale).max()
+    if n > 200:
+        part = torch.zeros(200, dtype=torch.float32, device="cuda")
+        dock.dock_surrogate_predict(S, X[n - 200:], part)
+        torch.cuda.synchronize()
+        assert np.array_equal(part.cpu().numpy(), got[n - 200:])
+
+
 def test_surrogate_search_replay(dock, env):
     """Pre-screened generations equal the oracle's GA children -> top-k of the
     GPU predictions -> merge with the GPU's exact scores, bit for bit."""
