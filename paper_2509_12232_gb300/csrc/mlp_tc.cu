@@ -1,7 +1,7 @@
 // Fused forward pass of the surrogate MLP (128 -> 256 -> 256 -> 256 -> 1,
 // erf-GELU after the hidden layers) on the 5th-generation tensor cores.
 //
-// One persistent CTA per SM (4 warps) takes tiles of 128 feature rows:
+// One persistent CTA per SM (8 warps) takes tiles of 128 feature rows:
 //   - the tile is stored in shared memory in the K-major "core matrix" layout
 //     the tensor core reads without swizzling (8 rows x 16 bytes per 128-byte
 //     block, blocks ordered by row group then by K);
@@ -11,10 +11,11 @@
 //   - one thread issues tcgen05.mma (M = 128, N = 256, K = 16 per instruction)
 //     into a 256-column FP32 accumulator in tensor memory and commits it to an
 //     mbarrier;
-//   - the four warps read their 32 accumulator lanes with tcgen05.ld, add the
-//     bias, apply GELU, round to BF16 and store the activations in the same
-//     layout as the next layer's A operand; after the third layer each thread
-//     (one row) forms the output as a dot product with the FP32 w4.
+//   - warps w and w + 4 read accumulator lanes 32 (w mod 4) .. + 31 (columns
+//     0-127 and 128-255) with tcgen05.ld, add the bias, apply GELU, round to
+//     BF16 and store the activations in the same layout as the next layer's A
+//     operand; after the third layer each thread forms half of its row's
+//     output (a dot product with the FP32 w4) and the halves are added.
 // Every mbarrier wait is bounded (one second of globaltimer); a timeout sets
 // *err, skips the rest of the CTA's tiles (the caller fills the output with
 // NaN beforehand) and releases the tensor memory after waiting, again
@@ -30,10 +31,12 @@ namespace mlp {
 namespace {
 
 constexpr int TM = 128;        // rows per tile (MMA M)
-constexpr int kThreads = 128;  // warp w reads accumulator lanes 32 w .. 32 w + 31
+constexpr int kThreads = 256;  // warps w and w + 4 read accumulator lanes 32 w .. 32 w + 31
+                               // (columns 0-127 and 128-255)
 constexpr int XH_BYTES = TM * HIDDEN * 2;       // feature tile (32 KB) or hidden tile (64 KB)
 constexpr int W_BYTES = HIDDEN * HIDDEN * 2;    // one layer's weights (at most 128 KB)
-constexpr int SMEM_BYTES = XH_BYTES + W_BYTES + 64;
+constexpr int SMEM_BYTES = XH_BYTES + W_BYTES + 64 + TM * 4 + 4 * HIDDEN * 4;
+// + output partial sums, biases b1..b3 and w4
 constexpr int WC_L2 = HIDDEN * FEATURES;        // element offsets of layers 2, 3 in the weights
 constexpr int WC_L3 = WC_L2 + HIDDEN * HIDDEN;
 constexpr int kCopyChunk = 16384;               // bytes per bulk copy
@@ -150,8 +153,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// GELU(z) = z Phi(z) = (z + |z| erf(|z| / sqrt 2)) / 2, with erf from
+// Abramowitz & Stegun, Handbook of Mathematical Functions, eq. 7.1.28:
+// erf(x) = 1 - (1 + a1 x + ... + a6 x^6)^-16 for x >= 0, |error| <= 3e-7 (one
+// reciprocal and four squarings; the result is rounded to BF16 anyway).
 __device__ __forceinline__ float gelu(float z) {
-  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
+  const float x = fabsf(z) * 0.70710678118654752f;
+  float p = fmaf(4.30638e-5f, x, 2.765672e-4f);
+  p = fmaf(p, x, 1.520143e-4f);
+  p = fmaf(p, x, 9.2705272e-3f);
+  p = fmaf(p, x, 4.22820123e-2f);
+  p = fmaf(p, x, 7.05230784e-2f);
+  p = fmaf(p, x, 1.0f);
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+  r *= r;
+  r *= r;
+  r *= r;
+  r *= r;  // p^-16
+  return 0.5f * fmaf(fabsf(z), 1.0f - r, z);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -166,7 +186,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   unsigned char *xh = sm;
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + XH_BYTES + W_BYTES);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+  float *ypart = reinterpret_cast<float *>(sm + XH_BYTES + W_BYTES + 64);
+  float *s_par = ypart + TM;  // b1, b2, b3, w4 (256 each)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;  // accumulator lanes 32 quad.., columns 128 half..
   const uint32_t bar_w = smem_u32(&bars[0]), bar_m = smem_u32(&bars[1]);
   const uint32_t s_xh = smem_u32(xh), s_w = smem_u32(sm + XH_BYTES);
   if (tid == 0) {
@@ -180,13 +203,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  for (int i = tid; i < 3 * HIDDEN; i += kThreads)
+    s_par[i] = params[(i >> 8) == 0 ? OFF_B1 + i : ((i >> 8) == 1 ? OFF_B2 + i - 256 : OFF_B3 + i - 512)];
+  for (int i = tid; i < HIDDEN; i += kThreads) s_par[3 * HIDDEN + i] = params[OFF_W4 + i];
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t t_lane = tmem + ((uint32_t)(32 * warp) << 16);
-  const float *B[3] = {params + OFF_B1, params + OFF_B2, params + OFF_B3};
-  const float *w4 = params + OFF_W4;
+  const uint32_t t_lane = tmem + ((uint32_t)(32 * quad) << 16);
   const float b4 = params[OFF_B4];
   const int64_t n_tiles = (n + TM - 1) / TM;
   uint32_t ph_w = 0, ph_m = 0;
@@ -209,8 +233,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---- feature tile -> K-major core-matrix layout (K = 128); a warp moves
     // ---- 8 rows x 4 chunks of 16 bytes per step (full 32-byte sectors) ----
 #pragma unroll 4
-    for (int i = 0; i < 16; ++i) {
-      const int v = warp + 4 * i;
+    for (int i = 0; i < 8; ++i) {
+      const int v = warp + 8 * i;
       const int row = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
       const int64_t gr = t * TM + row;
       uint4 val = make_uint4(0, 0, 0, 0);
@@ -219,8 +243,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     fence_proxy_async();
     __syncthreads();
-    const int64_t r_glob = t * TM + 32 * warp + lane;  // this thread's row (accumulator lane)
-    float yrow = b4;
+    const int row = 32 * quad + lane;                  // this thread's row (accumulator lane)
+    float yrow = half ? 0.0f : b4;
     for (int layer = 0; layer < 3 && ok; ++layer) {
       const int K = layer == 0 ? FEATURES : HIDDEN;
       // this layer's weights are in shared memory (the outcome of every wait
@@ -249,38 +273,41 @@ __global__ void __launch_bounds__(kThreads, 1)
       else if (t + gridDim.x < n_tiles)
         load_w(0);
       // ---- epilogue: bias + GELU -> BF16 (next A operand) or the output --
-      const float *bias = B[layer];
-      for (int cc = 0; cc < HIDDEN / 32; ++cc) {
+      const float *bias = s_par + HIDDEN * layer;
+      const float *w4 = s_par + 3 * HIDDEN;
+      for (int cc = 4 * half; cc < 4 * half + 4; ++cc) {
         float v[32];
         tmem_ld32(t_lane + 32u * cc, v);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
+          const float4 bl = *reinterpret_cast<const float4 *>(bias + 32 * cc + 8 * q);
+          const float4 bh = *reinterpret_cast<const float4 *>(bias + 32 * cc + 8 * q + 4);
+          const float bq[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
           uint32_t w[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int c = 32 * cc + 8 * q + 2 * e;
-            w[e] = pack_bf16(gelu(v[8 * q + 2 * e] + __ldg(bias + c)),
-                             gelu(v[8 * q + 2 * e + 1] + __ldg(bias + c + 1)));
-          }
+          for (int e = 0; e < 4; ++e)
+            w[e] = pack_bf16(gelu(v[8 * q + 2 * e] + bq[2 * e]),
+                             gelu(v[8 * q + 2 * e + 1] + bq[2 * e + 1]));
           if (layer < 2) {
-            *reinterpret_cast<uint4 *>(xh + canon_off(32 * warp + lane, 32 * cc + 8 * q, HIDDEN)) =
+            *reinterpret_cast<uint4 *>(xh + canon_off(row, 32 * cc + 8 * q, HIDDEN)) =
                 make_uint4(w[0], w[1], w[2], w[3]);
           } else {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int c = 32 * cc + 8 * q + 2 * e;
               const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[e]);
-              yrow = fmaf(__low2float(h), __ldg(w4 + c), yrow);
-              yrow = fmaf(__high2float(h), __ldg(w4 + c + 1), yrow);
+              yrow = fmaf(__low2float(h), w4[c], yrow);
+              yrow = fmaf(__high2float(h), w4[c + 1], yrow);
             }
           }
         }
       }
       if (layer < 2) fence_proxy_async();
+      else if (half) ypart[row] = yrow;
       fence_before_sync();
       __syncthreads();
     }
-    if (ok && r_glob < n) y[r_glob] = yrow;
+    if (ok && !half && t * TM + row < n) y[t * TM + row] = yrow + ypart[row];
   }
   // ---- teardown: let copies and products in flight finish, free TMEM ------
   if (w_pending) mbar_wait(bar_w, ph_w);
