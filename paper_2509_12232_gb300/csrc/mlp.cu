@@ -54,9 +54,7 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float gelu(float z) {
-  return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f));
-}
+__device__ __forceinline__ float gelu(float z) { return gelu_as(z); }
 __device__ __forceinline__ float gelu_d(float z) {
   return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
          z * 0.39894228040143268f * __expf(-0.5f * z * z);
@@ -108,6 +106,11 @@ __global__ void __launch_bounds__(NTHREADS) gemm_kernel(const __nv_bfloat16 *__r
                                                         int K, Epilogue ep) {
   __shared__ __align__(128) Tiles<AT, BT> T;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // split K: this CTA's K range starts at blockIdx.z * K
+  const int64_t kz = (int64_t)blockIdx.z * K;
+  A += AT ? kz * lda : kz;
+  B += BT ? kz * ldb : kz;
+  if (EPI == EPI_STORE_F32) ep.c32 += (int64_t)blockIdx.z * ep.split_stride;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wm = warp >> 2, wn = warp & 3;  // 2 x 4 warps, 64 x 32 each
   float acc[4][4][4];
@@ -225,13 +228,16 @@ __global__ void out_layer_bwd_kernel(const float *y, const float *t, int n, int 
   }
 }
 
-// out[c] = sum over rows of X[r][c] (+ partial-block sums), c < cols.
-__global__ void colsum_kernel(const __nv_bfloat16 *X, int rows, int cols, float *out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= cols) return;
-  float s = 0.0f;
-  for (int r = 0; r < rows; ++r) s += __bfloat162float(X[(int64_t)r * cols + c]);
-  out[c] = s;
+// part[b][c] = sum of X[r][c] over the rows of chunk b (chunk_rows rows each).
+__global__ void colsum_part_kernel(const __nv_bfloat16 *X, int rows, int cols, int chunk_rows,
+                                   float *part) {
+  const int b = blockIdx.x;
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+    float s = 0.0f;
+    const int r1 = min(rows, (b + 1) * chunk_rows);
+    for (int r = b * chunk_rows; r < r1; ++r) s += __bfloat162float(X[(int64_t)r * cols + c]);
+    part[(int64_t)b * cols + c] = s;
+  }
 }
 
 __global__ void reduce_parts_kernel(const float *part, int blocks, int width, float *out) {
@@ -270,10 +276,10 @@ __global__ void cast_weights_kernel(const float *W, int in, int out, __nv_bfloat
 
 template <bool AT, bool BT, int EPI>
 static cudaError_t gemm(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M,
-                        int N, int K, const Epilogue &ep, cudaStream_t s) {
-  if (M % BM || N % BN || K % BK) return cudaErrorInvalidValue;
-  dim3 grid(N / BN, M / BM);
-  gemm_kernel<AT, BT, EPI><<<grid, NTHREADS, 0, s>>>(A, lda, B, ldb, K, ep);
+                        int N, int K, const Epilogue &ep, cudaStream_t s, int splits = 1) {
+  if (M % BM || N % BN || K % (BK * splits)) return cudaErrorInvalidValue;
+  dim3 grid(N / BN, M / BM, splits);
+  gemm_kernel<AT, BT, EPI><<<grid, NTHREADS, 0, s>>>(A, lda, B, ldb, K / splits, ep);
   return cudaGetLastError();
 }
 
@@ -288,11 +294,26 @@ cudaError_t gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, in
 }
 
 cudaError_t gemm_tt_f32(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M,
-                        int N, int K, float *C, int ldc, cudaStream_t s) {
+                        int N, int K, float *C, float *scratch, int64_t scratch_elems,
+                        cudaStream_t s) {
   Epilogue ep{};
-  ep.c32 = C;
-  ep.ldc = ldc;
-  return gemm<true, true, EPI_STORE_F32>(A, lda, B, ldb, M, N, K, ep, s);
+  ep.ldc = N;
+  // enough K splits to fill the GPU (about 128 CTAs), each a multiple of BK
+  const int tiles = (M / BM) * (N / BN);
+  int splits = 1;
+  while (splits < 64 && tiles * splits < 128 && K % (BK * splits * 2) == 0 &&
+         (int64_t)splits * 2 * M * N <= scratch_elems)
+    splits *= 2;
+  if (splits == 1) {
+    ep.c32 = C;
+    return gemm<true, true, EPI_STORE_F32>(A, lda, B, ldb, M, N, K, ep, s);
+  }
+  ep.c32 = scratch;
+  ep.split_stride = (int64_t)M * N;
+  cudaError_t e = gemm<true, true, EPI_STORE_F32>(A, lda, B, ldb, M, N, K, ep, s, splits);
+  if (e != cudaSuccess) return e;
+  reduce_parts_kernel<<<(M * N + 255) / 256, 256, 0, s>>>(scratch, splits, M * N, C);
+  return cudaGetLastError();
 }
 
 cudaError_t out_layer(const __nv_bfloat16 *H, const float *w, const float *b, int rows, float *y,
@@ -310,8 +331,13 @@ cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const
   return cudaGetLastError();
 }
 
-cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, cudaStream_t s) {
-  colsum_kernel<<<(cols + 127) / 128, 128, 0, s>>>(X, rows, cols, out);
+cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, float *scratch,
+                   cudaStream_t s) {
+  if (rows <= 0) return cudaMemsetAsync(out, 0, sizeof(float) * cols, s);
+  const int chunks = rows < 64 ? rows : 64;
+  const int chunk_rows = (rows + chunks - 1) / chunks;
+  colsum_part_kernel<<<chunks, 256, 0, s>>>(X, rows, cols, chunk_rows, scratch);
+  reduce_parts_kernel<<<(cols + 255) / 256, 256, 0, s>>>(scratch, chunks, cols, out);
   return cudaGetLastError();
 }
 

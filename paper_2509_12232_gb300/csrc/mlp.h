@@ -23,26 +23,53 @@ constexpr int N_PARAMS = OFF_B4 + 1;
 
 enum { EPI_STORE_F32 = 0, EPI_BIAS_GELU = 1, EPI_GELU_BWD = 2 };
 
+// GELU(z) = z Phi(z) = (z + |z| erf(|z| / sqrt 2)) / 2 with erf from Abramowitz &
+// Stegun, Handbook of Mathematical Functions, eq. 7.1.28: erf(x) = 1 - (1 + a1 x
+// + ... + a6 x^6)^-16 for x >= 0, |error| <= 3e-7 (one reciprocal, four squarings).
+__device__ __forceinline__ float gelu_as(float z) {
+  const float x = fabsf(z) * 0.70710678118654752f;
+  float p = fmaf(4.30638e-5f, x, 2.765672e-4f);
+  p = fmaf(p, x, 1.520143e-4f);
+  p = fmaf(p, x, 9.2705272e-3f);
+  p = fmaf(p, x, 4.22820123e-2f);
+  p = fmaf(p, x, 7.05230784e-2f);
+  p = fmaf(p, x, 1.0f);
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
+  r *= r;
+  r *= r;
+  r *= r;
+  r *= r;  // p^-16
+  return 0.5f * fmaf(fabsf(z), 1.0f - r, z);
+}
+
 struct Epilogue {
   float *c32;               // FP32 output (STORE) or pre-activation cache (BIAS_GELU), or null
   __nv_bfloat16 *c16;       // BF16 output (BIAS_GELU: activation; GELU_BWD: dZ)
   const float *bias;        // BIAS_GELU
   const float *zin;         // GELU_BWD: pre-activations
   int ldc;
+  int64_t split_stride;     // STORE with split K: elements between the splits' partial outputs
 };
 
 // C = A Bt^T: A [M][K] row-major, Bt [N][K] row-major.
 cudaError_t gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb, int M, int N,
                     int K, int epi, const Epilogue &ep, cudaStream_t s);
-// C (FP32) = A^T B: A stored [K][M], B stored [K][N] (weight gradients).
+// C (FP32, ldc = N) = A^T B: A stored [K][M], B stored [K][N] (weight
+// gradients). K is split over CTAs when scratch (scratch_elems floats) holds
+// the partial products; the partials are summed in a fixed order.
 cudaError_t gemm_tt_f32(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M,
-                        int N, int K, float *C, int ldc, cudaStream_t s);
+                        int N, int K, float *C, float *scratch, int64_t scratch_elems,
+                        cudaStream_t s);
 cudaError_t out_layer(const __nv_bfloat16 *H, const float *w, const float *b, int rows, float *y,
                       cudaStream_t s);
 cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const __nv_bfloat16 *H3,
                           const float *Z3, const float *w4, __nv_bfloat16 *dZ3, float *part,
                           int blocks, float *out, cudaStream_t s);
-cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, cudaStream_t s);
+// out[c] = sum over rows of X[r][c]: row chunks in parallel, then a fixed-order sum
+// (scratch: at least 64 * cols floats).
+cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, float *scratch,
+                   cudaStream_t s);
 cudaError_t adam(float *p, float *m, float *v, const float *g, int n, float lr, int step,
                  cudaStream_t s);
 cudaError_t cast_weights(const float *W, int in, int out, __nv_bfloat16 *w16, __nv_bfloat16 *wt16,

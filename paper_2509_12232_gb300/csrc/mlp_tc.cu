@@ -153,26 +153,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// GELU(z) = z Phi(z) = (z + |z| erf(|z| / sqrt 2)) / 2, with erf from
-// Abramowitz & Stegun, Handbook of Mathematical Functions, eq. 7.1.28:
-// erf(x) = 1 - (1 + a1 x + ... + a6 x^6)^-16 for x >= 0, |error| <= 3e-7 (one
-// reciprocal and four squarings; the result is rounded to BF16 anyway).
-__device__ __forceinline__ float gelu(float z) {
-  const float x = fabsf(z) * 0.70710678118654752f;
-  float p = fmaf(4.30638e-5f, x, 2.765672e-4f);
-  p = fmaf(p, x, 1.520143e-4f);
-  p = fmaf(p, x, 9.2705272e-3f);
-  p = fmaf(p, x, 4.22820123e-2f);
-  p = fmaf(p, x, 7.05230784e-2f);
-  p = fmaf(p, x, 1.0f);
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(p));
-  r *= r;
-  r *= r;
-  r *= r;
-  r *= r;  // p^-16
-  return 0.5f * fmaf(fabsf(z), 1.0f - r, z);
-}
+__device__ __forceinline__ float gelu(float z) { return gelu_as(z); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);

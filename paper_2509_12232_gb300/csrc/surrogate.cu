@@ -109,10 +109,12 @@ struct dock_surrogate {
   __nv_bfloat16 *wc = nullptr;
   bool wc_valid = false;
   int *err = nullptr;
+  float *wpart = nullptr;  // split-K partial weight gradients, column-sum partials
   ~dock_surrogate() {
     for (float *q : {p, m, v, g, y, t, part, outg}) if (q) cudaFree(q);
     if (wc) cudaFree(wc);
     if (err) cudaFree(err);
+    if (wpart) cudaFree(wpart);
     for (int l = 0; l < 3; ++l) {
       if (w16[l]) cudaFree(w16[l]);
       if (wt16[l]) cudaFree(wt16[l]);
@@ -130,6 +132,7 @@ static const int kIn[3] = {FEATURES, HIDDEN, HIDDEN};
 static const int kOffW[3] = {mlp::OFF_W1, mlp::OFF_W2, mlp::OFF_W3};
 static const int kOffB[3] = {mlp::OFF_B1, mlp::OFF_B2, mlp::OFF_B3};
 static const int kBwdBlocks = 128;
+static const int64_t kWpartElems = 32 * HIDDEN * HIDDEN;  // 32 K splits of a 256 x 256 gradient
 
 static int ensure_workspace(dock_surrogate *S, int rows) {
   if (rows <= S->cap) return DOCK_OK;
@@ -193,8 +196,8 @@ static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
     const __nv_bfloat16 *act_in = l ? S->H[l - 1] : S->X;
     // dW_l = act_in^T dZ_l ; db_l = column sums of dZ_l
     SCU(mlp::gemm_tt_f32(act_in, kIn[l], S->dZ[l], HIDDEN, kIn[l], HIDDEN, rows, S->g + kOffW[l],
-                         HIDDEN, s));
-    SCU(mlp::colsum(S->dZ[l], rows, HIDDEN, S->g + kOffB[l], s));
+                         S->wpart, kWpartElems, s));
+    SCU(mlp::colsum(S->dZ[l], rows, HIDDEN, S->g + kOffB[l], S->wpart, s));
     if (l) {
       // dZ_{l-1} = (dZ_l W_l^T) * gelu'(Z_{l-1})
       mlp::Epilogue ep{};
@@ -223,6 +226,7 @@ extern "C" int dock_surrogate_create(uint64_t seed, void *stream, dock_surrogate
     SCU(cudaMalloc(&S->wt16[l], sizeof(__nv_bfloat16) * kIn[l] * HIDDEN));
   }
   SCU(cudaMalloc(&S->wc, sizeof(__nv_bfloat16) * mlp::canon_weight_elems()));
+  SCU(cudaMalloc(&S->wpart, sizeof(float) * kWpartElems));
   SCU(cudaMalloc(&S->err, sizeof(int)));
   SCU(cudaMemsetAsync(S->err, 0, sizeof(int), s));
   // He-normal weights, zero biases (host draw from the seed, one upload)
