@@ -307,14 +307,74 @@ def run_surrogate(args, rank, world):
     return 0
 
 
+def run_mlp(args, rank, world):
+    """The surrogate network alone: the fused tensor-core forward pass over one
+    pre-screened generation's candidates (1,000 ligands x 4,096 = 4,194,304
+    feature rows), against the measured BF16 peak; and the training step
+    (forward, backward, Adam) over 2,097,152 rows in batches of 4,096."""
+    import torch
+    from paper_2509_12232_gb300 import build, dock
+    torch.cuda.set_device(env_rank()[2])
+    build.build()
+    stream = torch.cuda.current_stream()
+    S = dock.dock_surrogate_create(seed=2)
+    rows = args.ligands * 4096 if args.ligands else 4 << 20
+    g = torch.Generator(device="cuda").manual_seed(7)
+    X = (torch.randn(rows, 128, device="cuda", generator=g) * 0.5).to(torch.bfloat16).view(torch.int16)
+    out = torch.empty(rows, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        dock.dock_surrogate_predict(S, X, out)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        dock.dock_surrogate_predict(S, X, out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    flops_row = 2 * (128 * 256 + 2 * 256 * 256 + 256)
+    peaks, peak_kind = measured_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 1900.0))
+    ach = flops_row * rows / (ms / 1000.0) / 1e12
+    n_tr = 2 << 20
+    Y = torch.randn(n_tr, device="cuda", generator=g)
+    dock.dock_surrogate_train(S, X[:n_tr], Y, epochs=1, batch=4096)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dock.dock_surrogate_train(S, X[:n_tr], Y, epochs=2, batch=4096)
+    torch.cuda.synchronize()
+    tr_s = (time.perf_counter() - t0) / 2
+    line = {"metric": "surrogate candidates predicted per s (fused tensor-core forward pass, "
+                      "128-256-256-256-1 BF16 MLP)",
+            "value": round(rows / (ms / 1000.0), 1), "unit": "rows/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "%d BF16 feature rows (one pre-screened generation of %d "
+                                   "ligands x 4,096 candidates)" % (rows, rows // 4096),
+                       "l2": "flushed between steps (256 MiB write)"},
+            "roofline": {"bound": "tensor", "achieved": round(ach, 2), "peak": bf16,
+                         "unit": "TFLOP/s", "frac": round(ach / bf16, 4), "traffic": None,
+                         "kernel": "fused_forward_kernel",
+                         "peak_source": "bf16_tflops (%s)" % peak_kind},
+            "training": {"rows_per_epoch": n_tr, "batch": 4096, "s_per_epoch": round(tr_s, 4),
+                         "tflops": round(3 * flops_row * n_tr / tr_s / 1e12, 2)}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="plain", choices=["plain", "surrogate"],
-                    help="surrogate: pre-screened vs plain comparison (its own JSON line)")
+    ap.add_argument("--mode", default="plain", choices=["plain", "surrogate", "mlp"],
+                    help="surrogate: pre-screened vs plain comparison; mlp: the surrogate "
+                         "network's forward pass and training step alone (each its own JSON line)")
     ap.add_argument("--ref-ligands-per-core", type=int, default=1)
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -330,6 +390,8 @@ def main():
         return run_reference(args, rank, world)
     if args.mode == "surrogate":
         return run_surrogate(args, rank, world)
+    if args.mode == "mlp":
+        return run_mlp(args, rank, world)
 
     import torch
     import torch.distributed as dist
