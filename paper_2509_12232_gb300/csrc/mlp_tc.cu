@@ -135,9 +135,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
       : "memory");
 }
 
-// 32 consecutive accumulator columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
+// Issue a read of 32 consecutive accumulator columns of this thread's lane;
+// the registers are valid after tmem_wait on them.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
       "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
@@ -148,12 +148,44 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float gelu(float z) { return gelu_as(z); }
+// Wait for this thread's accumulator reads; ties r to the wait so that no use
+// of it is scheduled before.
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
+// gelu_as (mlp.h) on two activations with packed two-wide FP32 arithmetic (the same
+// operations in the same order, one instruction for both lanes of a pair).
+__device__ __forceinline__ float2 gelu2(float2 z) {
+  const float2 az = make_float2(fabsf(z.x), fabsf(z.y));
+  const float2 x = __fmul2_rn(az, make_float2(0.70710678118654752f, 0.70710678118654752f));
+  float2 p = __ffma2_rn(make_float2(4.30638e-5f, 4.30638e-5f), x,
+                        make_float2(2.765672e-4f, 2.765672e-4f));
+  p = __ffma2_rn(p, x, make_float2(1.520143e-4f, 1.520143e-4f));
+  p = __ffma2_rn(p, x, make_float2(9.2705272e-3f, 9.2705272e-3f));
+  p = __ffma2_rn(p, x, make_float2(4.22820123e-2f, 4.22820123e-2f));
+  p = __ffma2_rn(p, x, make_float2(7.05230784e-2f, 7.05230784e-2f));
+  p = __ffma2_rn(p, x, make_float2(1.0f, 1.0f));
+  float2 r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(p.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(p.y));
+  r = __fmul2_rn(r, r);
+  r = __fmul2_rn(r, r);
+  r = __fmul2_rn(r, r);
+  r = __fmul2_rn(r, r);  // p^-16
+  const float2 t = __ffma2_rn(r, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+  return __fmul2_rn(make_float2(0.5f, 0.5f), __ffma2_rn(az, t, z));
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -209,18 +241,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     w_pending = true;
   };
 
-  if (blockIdx.x < n_tiles) load_w(0);
-  for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-    // ---- feature tile -> K-major core-matrix layout (K = 128); a warp moves
-    // ---- 8 rows x 4 chunks of 16 bytes per step (full 32-byte sectors) ----
-#pragma unroll 4
+  // feature tile t: a warp moves 8 rows x 4 chunks of 16 bytes per step (full
+  // 32-byte sectors) into registers, stored later in the K-major core-matrix
+  // layout (K = 128); the next tile's rows are read during the last epilogue
+  uint4 xr[8];
+  auto load_x = [&](int64_t t) {
+#pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int v = warp + 8 * i;
       const int row = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
       const int64_t gr = t * TM + row;
-      uint4 val = make_uint4(0, 0, 0, 0);
-      if (gr < n) val = __ldg(reinterpret_cast<const uint4 *>(X + gr * FEATURES) + chunk);
-      *reinterpret_cast<uint4 *>(xh + canon_off(row, 8 * chunk, FEATURES)) = val;
+      xr[i] = gr < n ? __ldg(reinterpret_cast<const uint4 *>(X + gr * FEATURES) + chunk)
+                     : make_uint4(0, 0, 0, 0);
+    }
+  };
+  if (blockIdx.x < n_tiles) {
+    load_w(0);
+    load_x(blockIdx.x);
+  }
+  for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int v = warp + 8 * i;
+      const int row = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
+      *reinterpret_cast<uint4 *>(xh + canon_off(row, 8 * chunk, FEATURES)) = xr[i];
     }
     fence_proxy_async();
     __syncthreads();
@@ -248,17 +292,21 @@ __global__ void __launch_bounds__(kThreads, 1)
       m_pending = false;
       ph_m ^= 1u;
       fence_after_sync();
-      // the next weights stream in during this epilogue
-      if (layer < 2)
+      // the next weights (and after the last layer the next tile's features)
+      // stream in during this epilogue
+      if (layer < 2) {
         load_w(layer + 1);
-      else if (t + gridDim.x < n_tiles)
+      } else if (t + gridDim.x < n_tiles) {
         load_w(0);
+        load_x(t + gridDim.x);
+      }
       // ---- epilogue: bias + GELU -> BF16 (next A operand) or the output --
       const float *bias = s_par + HIDDEN * layer;
       const float *w4 = s_par + 3 * HIDDEN;
-      for (int cc = 4 * half; cc < 4 * half + 4; ++cc) {
-        float v[32];
-        tmem_ld32(t_lane + 32u * cc, v);
+      // four chunks of 32 columns; the read of chunk j + 1 is in flight while
+      // chunk j is processed
+      uint32_t ra[32], rb[32];
+      auto chunk = [&](int cc, const uint32_t (&r)[32]) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const float4 bl = *reinterpret_cast<const float4 *>(bias + 32 * cc + 8 * q);
@@ -266,9 +314,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           const float bq[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
           uint32_t w[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            w[e] = pack_bf16(gelu(v[8 * q + 2 * e] + bq[2 * e]),
-                             gelu(v[8 * q + 2 * e + 1] + bq[2 * e + 1]));
+          for (int e = 0; e < 4; ++e) {
+            const float2 a = gelu2(__fadd2_rn(make_float2(__uint_as_float(r[8 * q + 2 * e]),
+                                                          __uint_as_float(r[8 * q + 2 * e + 1])),
+                                              make_float2(bq[2 * e], bq[2 * e + 1])));
+            w[e] = pack_bf16(a.x, a.y);
+          }
           if (layer < 2) {
             *reinterpret_cast<uint4 *>(xh + canon_off(row, 32 * cc + 8 * q, HIDDEN)) =
                 make_uint4(w[0], w[1], w[2], w[3]);
@@ -282,7 +333,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
         }
-      }
+      };
+      const int c0 = 4 * half;
+      tmem_ld32(t_lane + 32u * c0, ra);
+      tmem_wait(ra);
+      tmem_ld32(t_lane + 32u * (c0 + 1), rb);
+      chunk(c0, ra);
+      tmem_wait(rb);
+      tmem_ld32(t_lane + 32u * (c0 + 2), ra);
+      chunk(c0 + 1, rb);
+      tmem_wait(ra);
+      tmem_ld32(t_lane + 32u * (c0 + 3), rb);
+      chunk(c0 + 2, ra);
+      tmem_wait(rb);
+      chunk(c0 + 3, rb);
       if (layer < 2) fence_proxy_async();
       else if (half) ypart[row] = yrow;
       fence_before_sync();
