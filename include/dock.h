@@ -234,6 +234,17 @@ int dock_score(dock_pocket *pocket, dock_ligands *ligands, const int32_t *pose_l
                const float *genotypes, int64_t n_poses, float *scores, double *scores64,
                float *coords, int32_t fp64, void *stream);
 
+/* Scores (device FP32 [n_poses]) of caller-given poses with the pairwise
+ * inter-energy: for every ligand atom, every protein atom within the 8 A
+ * cutoff through the same pair terms as the intra pairs (the sum the grid maps
+ * approximate; Algorithm 2's inter loop over nearby protein atoms, Section V),
+ * plus the intra-energy. There is no grid box and no outside penalty, so the
+ * score is invariant under a rigid motion of protein and ligand together.
+ * FP32 with compensated sums; pose_ligand and genotypes as for dock_score;
+ * pose_ligand entries outside [0, n_ligands) score NaN. Asynchronous on stream. */
+int dock_score_pairwise(dock_pocket *pocket, dock_ligands *ligands, const int32_t *pose_ligand,
+                        const float *genotypes, int64_t n_poses, float *scores, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Search without device allocation                                          */
 /* ------------------------------------------------------------------------ */

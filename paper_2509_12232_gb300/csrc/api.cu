@@ -60,6 +60,30 @@ extern "C" const char *dock_version(void) {
 static const double kHWVdw = 0.1662, kHWHb = 0.1209, kHWElec = 0.1406, kHWSol = 0.1322;
 static const double kHCoulomb = 332.06363, kHQasp = 0.01097, kHEmax = 1.0e5;
 
+// Dispersion coefficients of a type pair with the weight folded in: a
+// donor-acceptor pair takes the 12-10 H-bond form with R and eps of the
+// acceptor (c6 = 0), any other the 12-6 form with the combined R and eps
+// (c10 = 0); w is the term's weight (the raw value is capped at EMAX before it).
+static void pair_coeffs(const dock_type_params *tp, int ti, int tj, double &c12, double &c6,
+                        double &c10, double &w) {
+  const bool hb = (tp[ti].hb_role == 1 && tp[tj].hb_role == 2) ||
+                  (tp[ti].hb_role == 2 && tp[tj].hb_role == 1);
+  c6 = c10 = 0.0;
+  if (hb) {
+    const int acc = tp[ti].hb_role == 2 ? ti : tj;
+    const double R = tp[acc].hb_R, e = tp[acc].hb_eps;
+    w = kHWHb;
+    c12 = w * 5.0 * e * std::pow(R, 12);
+    c10 = w * 6.0 * e * std::pow(R, 10);
+  } else {
+    const double R = 0.5 * ((double)tp[ti].Rii + (double)tp[tj].Rii);
+    const double e = std::sqrt((double)tp[ti].eps * (double)tp[tj].eps);
+    w = kHWVdw;
+    c12 = w * e * std::pow(R, 12);
+    c6 = w * 2.0 * e * std::pow(R, 6);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // pocket
 // ---------------------------------------------------------------------------
@@ -137,6 +161,72 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
     td.readMode = cudaReadModeElementType;
     CU(cudaCreateTextureObject(&P->xytex, &rd, &td, nullptr));
   }
+  // ---- pairwise scorer: protein atoms by 8 A cell, type tables -------------
+  std::vector<float4> cprot((size_t)d->n_atoms), cext((size_t)d->n_atoms);
+  std::vector<int32_t> cell_start;
+  {
+    const double cs = 8.0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int m = 0; m < 3; ++m) {
+      const float *c = m == 0 ? d->x : (m == 1 ? d->y : d->z);
+      lo[m] = d->n_atoms ? c[0] : 0.0;
+      hi[m] = lo[m];
+      for (int i = 1; i < d->n_atoms; ++i) {
+        lo[m] = std::min(lo[m], (double)c[i]);
+        hi[m] = std::max(hi[m], (double)c[i]);
+      }
+      P->cell_lo[m] = (float)(lo[m] - 0.5);
+      const double dm = std::floor((hi[m] - (double)P->cell_lo[m]) / cs) + 1.0;
+      if (dm > 4096) return fail(DOCK_EINVAL, "dock_create_pocket: protein extent too large");
+      P->cell_dims[m] = (int)dm;
+    }
+    const int64_t ncell = (int64_t)P->cell_dims[0] * P->cell_dims[1] * P->cell_dims[2];
+    if (ncell > (1 << 26)) return fail(DOCK_EINVAL, "dock_create_pocket: too many cells");
+    std::vector<int32_t> cell_of((size_t)d->n_atoms);
+    cell_start.assign((size_t)ncell + 1, 0);
+    for (int i = 0; i < d->n_atoms; ++i) {
+      int ci[3];
+      const float c3[3] = {d->x[i], d->y[i], d->z[i]};
+      for (int m = 0; m < 3; ++m)
+        ci[m] = std::min(P->cell_dims[m] - 1,
+                         std::max(0, (int)std::floor(((double)c3[m] - P->cell_lo[m]) / cs)));
+      cell_of[i] = (ci[2] * P->cell_dims[1] + ci[1]) * P->cell_dims[0] + ci[0];
+      ++cell_start[(size_t)cell_of[i] + 1];
+    }
+    for (int64_t c = 0; c < ncell; ++c) cell_start[(size_t)c + 1] += cell_start[(size_t)c];
+    std::vector<int32_t> fill(cell_start.begin(), cell_start.end() - 1);
+    for (int i = 0; i < d->n_atoms; ++i) {
+      const int dst = fill[(size_t)cell_of[i]]++;
+      const dock_type_params &tq = P->params[d->type[i]];
+      cprot[dst] = make_float4(d->x[i], d->y[i], d->z[i], d->q[i]);
+      cext[dst] = make_float4((float)((double)tq.solpar + kHQasp * std::fabs((double)d->q[i])),
+                              tq.vol, (float)d->type[i], 0.0f);
+    }
+  }
+  std::vector<float4> tpair((size_t)P->n_types * P->n_types);
+  std::vector<float2> tsv((size_t)P->n_types);
+  for (int ti = 0; ti < P->n_types; ++ti) {
+    tsv[ti] = make_float2(P->params[ti].solpar, P->params[ti].vol);
+    for (int tj = 0; tj < P->n_types; ++tj) {
+      double c12, c6, c10, w;
+      pair_coeffs(P->params.data(), ti, tj, c12, c6, c10, w);
+      tpair[(size_t)ti * P->n_types + tj] =
+          make_float4((float)c12, (float)c6, (float)c10, (float)(w * kHEmax));
+    }
+  }
+  CU(dalloc(&P->d_cprot, std::max<size_t>(1, cprot.size())));
+  CU(dalloc(&P->d_cext, std::max<size_t>(1, cext.size())));
+  CU(dalloc(&P->d_cell_start, cell_start.size()));
+  CU(dalloc(&P->d_tpair, tpair.size()));
+  CU(dalloc(&P->d_tsv, tsv.size()));
+  if (d->n_atoms) {
+    CU(cudaMemcpyAsync(P->d_cprot, cprot.data(), sizeof(float4) * cprot.size(), cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(P->d_cext, cext.data(), sizeof(float4) * cext.size(), cudaMemcpyHostToDevice, s));
+  }
+  CU(cudaMemcpyAsync(P->d_cell_start, cell_start.data(), sizeof(int32_t) * cell_start.size(),
+                     cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(P->d_tpair, tpair.data(), sizeof(float4) * tpair.size(), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(P->d_tsv, tsv.data(), sizeof(float2) * tsv.size(), cudaMemcpyHostToDevice, s));
   CU(cudaStreamSynchronize(s));
   *out = guard.release();
   return DOCK_OK;
@@ -335,20 +425,8 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
       const double qi = b->q[a0 + i], qj = b->q[a0 + j];
       const bool hb = (tp[ti].hb_role == 1 && tp[tj].hb_role == 2) ||
                       (tp[ti].hb_role == 2 && tp[tj].hb_role == 1);
-      double c12, c6 = 0.0, c10 = 0.0, w;
-      if (hb) {
-        const int acc = tp[ti].hb_role == 2 ? ti : tj;
-        const double R = tp[acc].hb_R, e = tp[acc].hb_eps;
-        w = kHWHb;
-        c12 = w * 5.0 * e * std::pow(R, 12);
-        c10 = w * 6.0 * e * std::pow(R, 10);
-      } else {
-        const double R = 0.5 * ((double)tp[ti].Rii + (double)tp[tj].Rii);
-        const double e = std::sqrt((double)tp[ti].eps * (double)tp[tj].eps);
-        w = kHWVdw;
-        c12 = w * e * std::pow(R, 12);
-        c6 = w * 2.0 * e * std::pow(R, 6);
-      }
+      double c12, c6, c10, w;
+      pair_coeffs(tp, ti, tj, c12, c6, c10, w);
       const double si = (double)tp[ti].solpar + kHQasp * std::fabs(qi);
       const double sj = (double)tp[tj].solpar + kHQasp * std::fabs(qj);
       H.pair_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
@@ -1016,6 +1094,46 @@ extern "C" int dock_score(dock_pocket *P, dock_ligands *L, const int32_t *pose_l
   A.lanes = 8;
   A.atoms_per_lane = DOCK_MAX_ATOMS / 8;
   CU(launch_score(A, s));
+  return DOCK_OK;
+}
+
+extern "C" int dock_score_pairwise(dock_pocket *P, dock_ligands *L, const int32_t *pose_ligand,
+                                   const float *genos, int64_t n_poses, float *scores, void *stream) {
+  if (!P || !L) return fail(DOCK_EINVAL, "dock_score_pairwise: NULL pocket or ligands");
+  if (n_poses < 0) return fail(DOCK_EINVAL, "dock_score_pairwise: n_poses < 0");
+  if (n_poses == 0) return DOCK_OK;
+  if (!pose_ligand || !genos || !scores)
+    return fail(DOCK_EINVAL, "dock_score_pairwise: NULL device buffer");
+  CU(cudaSetDevice(L->device));
+  PairwiseArgs A;
+  A.ligs = L->d_info;
+  A.atoms = L->d_atoms;
+  A.types = L->d_types;
+  A.pair_rec = L->d_pair_rec;
+  A.tors = L->d_tors;
+  A.moves = L->d_moves;
+  A.cx = P->center[0];
+  A.cy = P->center[1];
+  A.cz = P->center[2];
+  A.pose_ligand = pose_ligand;
+  A.n_ligands = L->n_ligands;
+  A.genos = genos;
+  A.n_poses = n_poses;
+  A.scores = scores;
+  A.cprot = P->d_cprot;
+  A.cext = P->d_cext;
+  A.cell_start = P->d_cell_start;
+  A.lox = P->cell_lo[0];
+  A.loy = P->cell_lo[1];
+  A.loz = P->cell_lo[2];
+  A.inv_cs = 1.0f / 8.0f;
+  A.dx = P->cell_dims[0];
+  A.dy = P->cell_dims[1];
+  A.dz = P->cell_dims[2];
+  A.tpair = P->d_tpair;
+  A.tsv = P->d_tsv;
+  A.n_types = P->n_types;
+  CU(launch_score_pairwise(A, (cudaStream_t)stream));
   return DOCK_OK;
 }
 

@@ -119,6 +119,34 @@ struct ScoreArgs {
   int32_t atoms_per_lane;
 };
 
+// Pairwise scoring of caller-given poses (pairwise.cu): the ScoreArgs inputs
+// plus the protein cell list and the type tables.
+struct PairwiseArgs {
+  const LigInfo *ligs;
+  const float4 *atoms;
+  const uint8_t *types;
+  const float *pair_rec;
+  const TorInfo *tors;
+  const uint8_t *moves;
+  float cx, cy, cz;
+  const int32_t *pose_ligand;
+  int32_t n_ligands;        // pose_ligand entries outside [0, n_ligands) score NaN
+  const float *genos;       // [n_poses][DOCK_MAX_GENES]
+  int64_t n_poses;
+  float *scores;
+  // protein atoms sorted by 8 A cell (x fastest): cprot {x, y, z, q}, cext
+  // {S_j = solpar + 0.01097 |q|, V_j, type, 0}; the atoms of cell c are
+  // [cell_start[c], cell_start[c + 1])
+  const float4 *cprot, *cext;
+  const int32_t *cell_start;
+  float lox, loy, loz, inv_cs;
+  int32_t dx, dy, dz;
+  const float4 *tpair;      // [T][T] {c12, c6, c10, cap} weights folded in
+  const float2 *tsv;        // [T] {solpar, vol}
+  int32_t n_types;
+};
+cudaError_t launch_score_pairwise(const PairwiseArgs &a, cudaStream_t s);
+
 // FP64 rescoring / scoring inputs (type table in FP32 as given).
 struct Fp64Args {
   const LigInfo *ligs;

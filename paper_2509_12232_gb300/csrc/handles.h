@@ -53,8 +53,19 @@ struct dock_pocket {
   double ox = 0, oy = 0, oz = 0, h = 0;
   float center[3] = {0, 0, 0};
   float radius = 0;
+  // protein cell list and type tables of the pairwise scorer
+  float4 *d_cprot = nullptr, *d_cext = nullptr, *d_tpair = nullptr;
+  float2 *d_tsv = nullptr;
+  int32_t *d_cell_start = nullptr;
+  float cell_lo[3] = {0, 0, 0};
+  int cell_dims[3] = {1, 1, 1};
   ~dock_pocket() {
     if (xytex) cudaDestroyTextureObject(xytex);
+    dfree(d_cprot);
+    dfree(d_cext);
+    dfree(d_tpair);
+    dfree(d_tsv);
+    dfree(d_cell_start);
     dfree(d_params);
     dfree(d_prot);
     dfree(d_ptype);

@@ -120,6 +120,7 @@ def lib():
         L.dock_job_destroy.argtypes = [vp]
         L.dock_job_destroy.restype = None
         L.dock_score.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp, vp, C.c_int32, vp]
+        L.dock_score_pairwise.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp]
         P_i64 = C.POINTER(C.c_int64)
         L.dock_ligands_info.argtypes = [vp, P_i32, P_i64, P_i64, P_i64, P_i64, P_i64]
         L.dock_batch_noalloc.argtypes = [vp, vp, C.POINTER(dock_search_params), vp, vp]
@@ -139,6 +140,7 @@ def lib():
                                            vp]
         for name in ("dock_create_pocket", "dock_pocket_grid", "dock_load_ligands", "dock_batch",
                      "dock_results", "dock_job_population", "dock_job_kernel_time", "dock_score",
+                     "dock_score_pairwise",
                      "dock_ligands_info", "dock_batch_noalloc", "dock_features",
                      "dock_features_population", "dock_surrogate_create",
                      "dock_surrogate_set_params", "dock_surrogate_get_params",
@@ -352,6 +354,16 @@ def dock_score(pocket: Pocket, ligands: Ligands, pose_ligand, genotypes, scores=
     check(lib().dock_score(pocket.handle, ligands.handle, _dptr(pose_ligand), _dptr(genotypes), n,
                            _dptr(scores), _dptr(scores64), _dptr(coords), 1 if fp64 else 0,
                            _stream(stream)))
+
+
+def dock_score_pairwise(pocket: Pocket, ligands: Ligands, pose_ligand, genotypes, scores,
+                        stream=None):
+    """Scores with the pairwise inter-energy (no grid) plus intra-energy of
+    genotypes ([n, 23] float32) posed for ligands pose_ligand ([n] int32), all
+    device tensors or pointers; asynchronous on stream."""
+    n = int(pose_ligand.shape[0]) if hasattr(pose_ligand, "shape") else int(genotypes.shape[0])
+    check(lib().dock_score_pairwise(pocket.handle, ligands.handle, _dptr(pose_ligand),
+                                    _dptr(genotypes), n, _dptr(scores), _stream(stream)))
 
 
 def version() -> str:
