@@ -103,13 +103,11 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
     if (p.hb_role < 0 || p.hb_role > 2 || !(p.Rii > 0) || !(p.eps >= 0))
       return fail(DOCK_EINVAL, "dock_create_pocket: bad parameters for type %d", t);
   }
-  std::vector<float4> prot((size_t)d->n_atoms);
   for (int i = 0; i < d->n_atoms; ++i) {
     if (d->type[i] >= d->n_types) return fail(DOCK_EINVAL, "protein atom %d: type out of range", i);
     if (!std::isfinite(d->x[i]) || !std::isfinite(d->y[i]) || !std::isfinite(d->z[i]) ||
         !std::isfinite(d->q[i]))
       return fail(DOCK_EINVAL, "protein atom %d: non-finite value", i);
-    prot[i] = make_float4(d->x[i], d->y[i], d->z[i], d->q[i]);
   }
   const double n_f = std::floor(2.0 * (double)d->radius / (double)d->spacing + 1e-9) + 1.0;
   if (n_f < 2 || n_f > 1024) return fail(DOCK_EINVAL, "grid of %g nodes per axis", n_f);
@@ -130,38 +128,10 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
   cudaStream_t s = (cudaStream_t)stream;
   const size_t nodes = (size_t)P->n * P->n * P->n;
   CU(dalloc(&P->d_params, P->n_types));
-  CU(dalloc(&P->d_prot, prot.size()));
-  CU(dalloc(&P->d_ptype, (size_t)d->n_atoms));
-  CU(dalloc(&P->d_maps, nodes * P->n_types));
   CU(cudaMemcpyAsync(P->d_params, P->params.data(), sizeof(dock_type_params) * P->n_types,
                      cudaMemcpyHostToDevice, s));
-  if (d->n_atoms) {
-    CU(cudaMemcpyAsync(P->d_prot, prot.data(), sizeof(float4) * prot.size(), cudaMemcpyHostToDevice, s));
-    CU(cudaMemcpyAsync(P->d_ptype, d->type, d->n_atoms, cudaMemcpyHostToDevice, s));
-  }
-  CU(dalloc(&P->d_xycell, (size_t)P->n_types * 2 * P->n * (P->n - 1) * (P->n - 1) * 8));
-  CU(dalloc(&P->d_fpm, nodes));
-  CU(launch_grid_build_impl(P->d_prot, P->d_ptype, P->n_prot, P->d_params, P->n_types, P->n,
-                            P->ox, P->oy, P->oz, P->h, P->d_maps, P->d_fpm, s));
-  CU(launch_xycell_maps(P->d_maps, P->d_fpm, P->n_types, P->n, P->d_xycell, s));
-  {
-    const size_t n4 = (size_t)P->n_types * 2 * P->n * (P->n - 1) * (P->n - 1) * 2;
-    int max_w = 0;
-    CU(cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture1DLinearWidth, P->device));
-    if (n4 > (size_t)max_w || n4 > (size_t)INT32_MAX)
-      return fail(DOCK_EINVAL, "dock_create_pocket: %zu grid records exceed the texture limit", n4 / 2);
-    cudaResourceDesc rd;
-    memset(&rd, 0, sizeof rd);
-    rd.resType = cudaResourceTypeLinear;
-    rd.res.linear.devPtr = P->d_xycell;
-    rd.res.linear.desc = cudaCreateChannelDesc<float4>();
-    rd.res.linear.sizeInBytes = n4 * sizeof(float4);
-    cudaTextureDesc td;
-    memset(&td, 0, sizeof td);
-    td.readMode = cudaReadModeElementType;
-    CU(cudaCreateTextureObject(&P->xytex, &rd, &td, nullptr));
-  }
-  // ---- pairwise scorer: protein atoms by 8 A cell, type tables -------------
+  // ---- protein atoms by 8 A cell and the type-pair tables (grid build and
+  // ---- pairwise scorer) -------------------------------------------------------
   std::vector<float4> cprot((size_t)d->n_atoms), cext((size_t)d->n_atoms);
   std::vector<int32_t> cell_start;
   {
@@ -204,14 +174,18 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
     }
   }
   std::vector<float4> tpair((size_t)P->n_types * P->n_types);
+  std::vector<double4> gcoef((size_t)P->n_types * P->n_types);
   std::vector<float2> tsv((size_t)P->n_types);
+  std::vector<double2> gtsv((size_t)P->n_types);
   for (int ti = 0; ti < P->n_types; ++ti) {
     tsv[ti] = make_float2(P->params[ti].solpar, P->params[ti].vol);
+    gtsv[ti] = make_double2(P->params[ti].solpar, P->params[ti].vol);
     for (int tj = 0; tj < P->n_types; ++tj) {
       double c12, c6, c10, w;
       pair_coeffs(P->params.data(), ti, tj, c12, c6, c10, w);
       tpair[(size_t)ti * P->n_types + tj] =
           make_float4((float)c12, (float)c6, (float)c10, (float)(w * kHEmax));
+      gcoef[(size_t)ti * P->n_types + tj] = make_double4(c12, c6, c10, w * kHEmax);
     }
   }
   CU(dalloc(&P->d_cprot, std::max<size_t>(1, cprot.size())));
@@ -227,6 +201,61 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
                      cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(P->d_tpair, tpair.data(), sizeof(float4) * tpair.size(), cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(P->d_tsv, tsv.data(), sizeof(float2) * tsv.size(), cudaMemcpyHostToDevice, s));
+  double4 *d_gcoef = nullptr;
+  double2 *d_gtsv = nullptr;
+  CU(dalloc(&d_gcoef, gcoef.size()));
+  CU(dalloc(&d_gtsv, gtsv.size()));
+  std::unique_ptr<double4, void (*)(double4 *)> gcoef_guard(d_gcoef, [](double4 *q) { dfree(q); });
+  std::unique_ptr<double2, void (*)(double2 *)> gtsv_guard(d_gtsv, [](double2 *q) { dfree(q); });
+  CU(cudaMemcpyAsync(d_gcoef, gcoef.data(), sizeof(double4) * gcoef.size(), cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(d_gtsv, gtsv.data(), sizeof(double2) * gtsv.size(), cudaMemcpyHostToDevice, s));
+  // ---- grid maps ---------------------------------------------------------------
+  CU(dalloc(&P->d_maps, nodes * P->n_types));
+  CU(dalloc(&P->d_xycell, (size_t)P->n_types * 2 * P->n * (P->n - 1) * (P->n - 1) * 8));
+  CU(dalloc(&P->d_fpm, nodes));
+  {
+    GridBuildArgs G;
+    G.cprot = P->d_cprot;
+    G.cext = P->d_cext;
+    G.cell_start = P->d_cell_start;
+    G.lox = P->cell_lo[0];
+    G.loy = P->cell_lo[1];
+    G.loz = P->cell_lo[2];
+    G.inv_cs = 1.0f / 8.0f;
+    G.dx = P->cell_dims[0];
+    G.dy = P->cell_dims[1];
+    G.dz = P->cell_dims[2];
+    G.coef = d_gcoef;
+    G.tsv = d_gtsv;
+    G.n_types = P->n_types;
+    G.n = P->n;
+    G.ox = P->ox;
+    G.oy = P->oy;
+    G.oz = P->oz;
+    G.h = P->h;
+    G.maps = P->d_maps;
+    G.fpm = P->d_fpm;
+    CU(launch_grid_build_impl(G, s));
+  }
+  CU(launch_xycell_maps(P->d_maps, P->d_fpm, P->n_types, P->n, P->d_xycell, s));
+  {
+    const size_t n4 = (size_t)P->n_types * 2 * P->n * (P->n - 1) * (P->n - 1) * 2;
+    int max_w = 0;
+    CU(cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture1DLinearWidth, P->device));
+    if (n4 > (size_t)max_w || n4 > (size_t)INT32_MAX)
+      return fail(DOCK_EINVAL, "dock_create_pocket: %zu grid records exceed the texture limit", n4 / 2);
+    cudaResourceDesc rd;
+    memset(&rd, 0, sizeof rd);
+    rd.resType = cudaResourceTypeLinear;
+    rd.res.linear.devPtr = P->d_xycell;
+    rd.res.linear.desc = cudaCreateChannelDesc<float4>();
+    rd.res.linear.sizeInBytes = n4 * sizeof(float4);
+    cudaTextureDesc td;
+    memset(&td, 0, sizeof td);
+    td.readMode = cudaReadModeElementType;
+    CU(cudaCreateTextureObject(&P->xytex, &rd, &td, nullptr));
+  }
+  // the tables above are freed on return: wait for the kernels that read them
   CU(cudaStreamSynchronize(s));
   *out = guard.release();
   return DOCK_OK;

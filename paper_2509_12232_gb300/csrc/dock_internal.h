@@ -162,10 +162,20 @@ struct Fp64Args {
 };
 
 // Launchers (defined in the .cu files).
-cudaError_t launch_grid_build_impl(const float4 *prot, const uint8_t *ptype, int n_prot,
-                                   const dock_type_params *params_dev, int n_types, int n,
-                                   double ox, double oy, double oz, double h, float4 *maps,
-                                   float2 *fpm, cudaStream_t s);
+// Grid maps from the protein cell list (grid.cu).
+struct GridBuildArgs {
+  const float4 *cprot, *cext;  // cell-sorted protein atoms, as in PairwiseArgs
+  const int32_t *cell_start;
+  float lox, loy, loz, inv_cs;
+  int32_t dx, dy, dz;
+  const double4 *coef;         // [T][T] {c12, c6, c10, w EMAX}, weights folded in
+  const double2 *tsv;          // [T] {solpar, vol}
+  int32_t n_types, n;
+  double ox, oy, oz, h;
+  float4 *maps;
+  float2 *fpm;                 // per node {E + D, E - D}, rounded once from FP64
+};
+cudaError_t launch_grid_build_impl(const GridBuildArgs &A, cudaStream_t s);
 // Energy of each ligand's pose-invariant pairs (FP64 sum, stored rounded to
 // FP32 in ligs[l].intra_const); one warp per ligand.
 cudaError_t launch_intra_const(LigInfo *ligs, int n_ligands, const float4 *atoms_raw,

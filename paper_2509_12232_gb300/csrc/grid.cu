@@ -1,49 +1,42 @@
 // Grid-map construction (Section V: the inter-energy is memoised in 3-D maps
 // around the fixed protein, one per ligand atom type, as AutoGrid does).
 //
-// One thread per node. Protein atoms stream through shared memory in tiles;
-// a float32 distance test prefilters, the kept pairs are evaluated and summed
+// One thread per node, nodes tiled 8 x 8 x 4 per block so a block's nodes
+// share their neighbour cells of the protein cell list (8 A cells; the three
+// x-neighbours of a cell are one contiguous atom range, nine ranges per node).
+// A float32 distance test prefilters, the kept pairs are evaluated and summed
 // in FP64 and the node values are rounded to FP32 once:
-//   M_t = sum_j w min(disp_raw(t, t_j, r), EMAX) + W_sol (solpar_t V_j + S_j V_t) g(r)
+//   M_t = sum_j min(c12 r^-12 - c6 r^-6 - c10 r^-10, w EMAX) + W_sol (solpar_t V_j + S_j V_t) g(r)
 //   E   = sum_j W_elec 332.06363 q_j / (eps(r) r)
 //   D   = sum_j W_sol 0.01097 V_j g(r),          g(r) = exp(-r^2 / (2 sigma^2))
-// with r floored at 0.5 A and pairs at r >= 8 A skipped; M_t capped at EMAX.
+// with the type-pair coefficients c12, c6, c10 (weight w folded in; 12-10 form
+// for donor-acceptor pairs) from an FP64 table, r floored at 0.5 A, pairs at
+// r >= 8 A skipped and M_t capped at EMAX.
 // Layout: float4 {M_t, E, D, 0} in [t][z][y][x] order.
 #include "device_common.cuh"
 
 namespace dk {
 
 namespace {
-constexpr int kTile = 256;
 
-__device__ __forceinline__ double ipow64(double x, int n) {
-  double r = 1.0;
-  for (int i = 0; i < n; ++i) r *= x;
-  return r;
+__device__ __forceinline__ void cell_span(float u, int d, int &lo, int &hi) {
+  const float c = floorf(fminf(fmaxf(u, -4.0f), (float)d + 4.0f));
+  lo = max((int)c - 1, 0);
+  hi = min((int)c + 1, d - 1);
 }
 
-struct GridBuildArgs {
-  const float4 *prot;
-  const uint8_t *ptype;
-  int n_prot;
-  const dock_type_params *params;
-  int n_types;
-  int n;
-  double ox, oy, oz, h;
-  float4 *maps;
-  float2 *fpm;   // per node {E + D, E - D}, rounded once from FP64
-};
-
 __global__ void __launch_bounds__(256) grid_build_kernel(const GridBuildArgs A) {
-  __shared__ float4 s_atom[kTile];
-  __shared__ uint8_t s_type[kTile];
-  __shared__ dock_type_params s_par[DOCK_MAX_TYPES];
+  __shared__ double4 s_coef[DOCK_MAX_TYPES * DOCK_MAX_TYPES];  // {c12, c6, c10, w EMAX}
+  __shared__ double2 s_sv[DOCK_MAX_TYPES];                      // {solpar, vol}
   const int T = A.n_types;
-  if (threadIdx.x < T) s_par[threadIdx.x] = A.params[threadIdx.x];
-  const int64_t nn = (int64_t)A.n * A.n * A.n;
-  const int64_t node = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = node < nn;
-  const int ix = (int)(node % A.n), iy = (int)((node / A.n) % A.n), iz = (int)(node / ((int64_t)A.n * A.n));
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  for (int i = tid; i < T * T; i += 256) s_coef[i] = A.coef[i];
+  for (int i = tid; i < T; i += 256) s_sv[i] = A.tsv[i];
+  __syncthreads();
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+  const int iz = blockIdx.z * blockDim.z + threadIdx.z;
+  if (ix >= A.n || iy >= A.n || iz >= A.n) return;
   const double px = A.ox + ix * A.h, py = A.oy + iy * A.h, pz = A.oz + iz * A.h;
   const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
   double m[DOCK_MAX_TYPES];
@@ -51,54 +44,47 @@ __global__ void __launch_bounds__(256) grid_build_kernel(const GridBuildArgs A) 
   for (int t = 0; t < DOCK_MAX_TYPES; ++t) m[t] = 0.0;
   double E = 0.0, D = 0.0;
   const double inv2s2 = 1.0 / (2.0 * kSigma * kSigma);
-  for (int base = 0; base < A.n_prot; base += kTile) {
-    __syncthreads();
-    const int cnt = min(kTile, A.n_prot - base);
-    if (threadIdx.x < cnt) {
-      s_atom[threadIdx.x] = A.prot[base + threadIdx.x];
-      s_type[threadIdx.x] = A.ptype[base + threadIdx.x];
-    }
-    __syncthreads();
-    if (!active) continue;
-    for (int a = 0; a < cnt; ++a) {
-      const float4 p = s_atom[a];
-      const float dxf = pxf - p.x, dyf = pyf - p.y, dzf = pzf - p.z;
-      if (dxf * dxf + dyf * dyf + dzf * dzf > 64.5f) continue;
-      const double dx = px - (double)p.x, dy = py - (double)p.y, dz = pz - (double)p.z;
-      double r = sqrt(dx * dx + dy * dy + dz * dz);
-      if (!(r < 8.0)) continue;
-      if (r < 0.5) r = 0.5;
-      const int tj = s_type[a];
-      const double qj = p.w;
-      const double g = exp(-r * r * inv2s2);
-      const double sj = (double)s_par[tj].solpar + kQasp * fabs(qj);
-      const double vj = s_par[tj].vol;
-      const int rj = s_par[tj].hb_role;
+  const double kE = (double)kWElec * kCoulomb, kD = (double)kWSol * kQasp;
+  int x0, x1, y0, y1, z0, z1;
+  cell_span((pxf - A.lox) * A.inv_cs, A.dx, x0, x1);
+  cell_span((pyf - A.loy) * A.inv_cs, A.dy, y0, y1);
+  cell_span((pzf - A.loz) * A.inv_cs, A.dz, z0, z1);
+  for (int cz = z0; cz <= z1; ++cz)
+    for (int cy = y0; cy <= y1; ++cy) {
+      if (x0 > x1) break;
+      const int row = (cz * A.dy + cy) * A.dx;
+      const int j1 = __ldg(A.cell_start + row + x1 + 1);
+      for (int j = __ldg(A.cell_start + row + x0); j < j1; ++j) {
+        const float4 p = __ldg(A.cprot + j);
+        const float dxf = pxf - p.x, dyf = pyf - p.y, dzf = pzf - p.z;
+        if (dxf * dxf + dyf * dyf + dzf * dzf > 64.5f) continue;
+        const double dx = px - (double)p.x, dy = py - (double)p.y, dz = pz - (double)p.z;
+        const double r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < 64.0)) continue;
+        const double r2c = r2 < 0.25 ? 0.25 : r2;  // r floored at 0.5 A
+        const double r = sqrt(r2c);
+        const double ir2 = 1.0 / r2c, ir4 = ir2 * ir2, ir6 = ir4 * ir2;
+        const double ir10 = ir6 * ir4, ir12 = ir6 * ir6;
+        const float4 ex = __ldg(A.cext + j);  // {S_j, V_j, type, 0}
+        const int tj = (int)ex.z;
+        const double qj = p.w, vj = ex.y;
+        const double g = exp(-r2c * inv2s2);
+        const double aj = (double)kWSol * vj * g, bj = (double)kWSol * (double)ex.x * g;
 #pragma unroll
-      for (int t = 0; t < DOCK_MAX_TYPES; ++t) {
-        if (t < T) {
-          const int rt = s_par[t].hb_role;
-          double disp;
-          if ((rt == 1 && rj == 2) || (rt == 2 && rj == 1)) {
-            const int acc = rt == 2 ? t : tj;
-            const double R = s_par[acc].hb_R, e = s_par[acc].hb_eps, s = R / r;
-            disp = 5.0 * e * ipow64(s, 12) - 6.0 * e * ipow64(s, 10);
-            disp = (disp > kEmax ? kEmax : disp) * (double)kWHb;
-          } else {
-            const double R = 0.5 * ((double)s_par[t].Rii + (double)s_par[tj].Rii);
-            const double e = sqrt((double)s_par[t].eps * (double)s_par[tj].eps), s = R / r;
-            disp = e * ipow64(s, 12) - 2.0 * e * ipow64(s, 6);
-            disp = (disp > kEmax ? kEmax : disp) * (double)kWVdw;
+        for (int t = 0; t < DOCK_MAX_TYPES; ++t) {
+          if (t < T) {
+            const double4 c = s_coef[t * T + tj];
+            const double raw = c.x * ir12 - c.y * ir6 - c.z * ir10;
+            m[t] += (raw > c.w ? c.w : raw) + s_sv[t].x * aj + s_sv[t].y * bj;
           }
-          m[t] += disp + (double)kWSol * ((double)s_par[t].solpar * vj + sj * (double)s_par[t].vol) * g;
         }
+        const double diel = kDielA + kDielB / (1.0 + kDielK * exp(-kDielLambda * kDielB * r));
+        E += kE * qj / (diel * r);
+        D += kD * vj * g;
       }
-      const double diel = kDielA + kDielB / (1.0 + kDielK * exp(-kDielLambda * kDielB * r));
-      E += (double)kWElec * kCoulomb * qj / (diel * r);
-      D += (double)kWSol * kQasp * vj * g;
     }
-  }
-  if (!active) return;
+  const int64_t nn = (int64_t)A.n * A.n * A.n;
+  const int64_t node = ((int64_t)iz * A.n + iy) * A.n + ix;
   A.fpm[node] = make_float2((float)(E + D), (float)(E - D));
 #pragma unroll
   for (int t = 0; t < DOCK_MAX_TYPES; ++t) {
@@ -110,23 +96,10 @@ __global__ void __launch_bounds__(256) grid_build_kernel(const GridBuildArgs A) 
 }
 }  // namespace
 
-cudaError_t launch_grid_build_impl(const float4 *prot, const uint8_t *ptype, int n_prot,
-                                   const dock_type_params *params_dev, int n_types, int n,
-                                   double ox, double oy, double oz, double h, float4 *maps,
-                                   float2 *fpm, cudaStream_t s) {
-  GridBuildArgs A;
-  A.prot = prot;
-  A.ptype = ptype;
-  A.n_prot = n_prot;
-  A.params = params_dev;
-  A.n_types = n_types;
-  A.n = n;
-  A.ox = ox; A.oy = oy; A.oz = oz; A.h = h;
-  A.maps = maps;
-  A.fpm = fpm;
-  const int64_t nn = (int64_t)n * n * n;
-  const int threads = 256;
-  grid_build_kernel<<<(unsigned)((nn + threads - 1) / threads), threads, 0, s>>>(A);
+cudaError_t launch_grid_build_impl(const GridBuildArgs &A, cudaStream_t s) {
+  const dim3 blk(8, 8, 4);
+  const dim3 grd((A.n + 7) / 8, (A.n + 7) / 8, (A.n + 3) / 4);
+  grid_build_kernel<<<grd, blk, 0, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -42,8 +42,6 @@ struct dock_pocket {
   int n_types = 0;
   std::vector<dock_type_params> params;
   dock_type_params *d_params = nullptr;
-  float4 *d_prot = nullptr;
-  uint8_t *d_ptype = nullptr;
   int n_prot = 0;
   float4 *d_maps = nullptr;
   float *d_xycell = nullptr;  // (x, y)-cell records of the FP32 scorer
@@ -67,8 +65,6 @@ struct dock_pocket {
     dfree(d_tsv);
     dfree(d_cell_start);
     dfree(d_params);
-    dfree(d_prot);
-    dfree(d_ptype);
     dfree(d_maps);
     dfree(d_xycell);
     dfree(d_fpm);
