@@ -366,13 +366,52 @@ def run_mlp(args, rank, world):
     return 0
 
 
+def run_grid(args, rank, world):
+    """The per-pocket grid-map build (the AutoGrid step, timed apart from the
+    search): dock_create_pocket end to end (host cell list and tables, device
+    allocations, the map kernel, the scorer's record layout) for the c2 pocket
+    (4,000 atoms, 86^3 nodes x 7 types) and the c5 pocket (10,000 atoms,
+    107^3 nodes)."""
+    import torch
+    from paper_2509_12232_gb300 import build, dock, synth
+    torch.cuda.set_device(env_rank()[2])
+    build.build()
+    out = {}
+    for name in ("c2", "c5"):
+        w = synth.WORKLOADS[name]
+        pk = synth.make_pocket(w.pocket_atoms, w.radius, seed=0)
+        make = lambda: dock.dock_create_pocket(pk.x, pk.y, pk.z, pk.q, pk.type, pk.center,  # noqa
+                                               pk.radius, pk.spacing, synth.TYPE_PARAMS)
+        for _ in range(args.warmup):
+            make().close()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            make().close()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / args.steps * 1e3
+        n = int(round(2 * w.radius / pk.spacing)) + 1
+        out[name] = {"atoms": w.pocket_atoms, "nodes": n ** 3, "types": synth.N_TYPES,
+                     "ms_per_pocket": round(ms, 3),
+                     "node_types_per_s": round(n ** 3 * synth.N_TYPES / (ms / 1000.0), 1)}
+    line = {"metric": "pocket grid builds per s (dock_create_pocket, c2 pocket)",
+            "value": round(1000.0 / out["c2"]["ms_per_pocket"], 3), "unit": "pockets/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["c2"]["ms_per_pocket"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "grid maps of the c2 and c5 pockets", "pockets": out},
+            "roofline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="plain", choices=["plain", "surrogate", "mlp"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "surrogate", "mlp", "grid"],
                     help="surrogate: pre-screened vs plain comparison; mlp: the surrogate "
                          "network's forward pass and training step alone (each its own JSON line)")
     ap.add_argument("--ref-ligands-per-core", type=int, default=1)
@@ -392,6 +431,8 @@ def main():
         return run_surrogate(args, rank, world)
     if args.mode == "mlp":
         return run_mlp(args, rank, world)
+    if args.mode == "grid":
+        return run_grid(args, rank, world)
 
     import torch
     import torch.distributed as dist

@@ -293,7 +293,23 @@ struct LigHost {
 };
 
 // Topology and pair coefficients of ligand l (see dock_load_ligands in dock.h).
-void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, LigHost &H) {
+// Weighted dispersion coefficients {c12, c6, c10, w} of every type pair (one
+// table per dock_load_ligands call).
+struct TypePairTable {
+  int T = 0;
+  std::vector<double> c;  // [T][T][4]
+  explicit TypePairTable(const dock_pocket *P) : T(P->n_types), c((size_t)T * T * 4) {
+    for (int ti = 0; ti < T; ++ti)
+      for (int tj = 0; tj < T; ++tj) {
+        double *q = &c[((size_t)ti * T + tj) * 4];
+        pair_coeffs(P->params.data(), ti, tj, q[0], q[1], q[2], q[3]);
+      }
+  }
+  const double *at(int ti, int tj) const { return &c[((size_t)ti * T + tj) * 4]; }
+};
+
+void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, const TypePairTable &TP, int l,
+                    LigHost &H) {
   const int a0 = b->atom_off[l], n = b->atom_off[l + 1] - a0;
   const int t0 = b->tors_off[l], k = b->tors_off[l + 1] - t0;
   char msg[160];
@@ -409,44 +425,53 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
   // permuted so that the pairs at list positions p of one aligned window of 4
   // (2, 8) have distinct j mod 4 (2, 8) where the row allows it. A pose's L
   // lanes read the atoms of pairs p .. p + L - 1 together, and distinct j
-  // mod L keep those 16-byte shared-memory rows on distinct bank groups.
+  // mod L keep those 16-byte shared-memory rows on distinct bank groups. The
+  // residues taken in the current windows are kept as bitmasks; the first j
+  // with the lowest clash cost (L = 4 first, then 2, then 8) is placed next.
+  // The pose-invariant pairs (the FP64 constant's) keep plain row order.
   std::vector<int> row, order;
-  auto window_cost = [&](int pos, int j) {
-    int c = 0;
-    static const int kW[3] = {4, 2, 8}, kWt[3] = {100, 10, 1};
-    for (int w = 0; w < 3; ++w)
-      for (int q = pos - pos % kW[w]; q < pos; ++q)
-        if ((order[2 * q] - j) % kW[w] == 0) c += kWt[w];
-    return c;
+  uint32_t used4 = 0, used2 = 0, used8 = 0;
+  auto cost = [&](int j) {
+    return 100 * (int)((used4 >> (j & 3)) & 1u) + 10 * (int)((used2 >> (j & 1)) & 1u) +
+           (int)((used8 >> (j & 7)) & 1u);
   };
   for (int i = 0; i < n; ++i) {
     row.clear();
-    for (int j = i + 1; j < n; ++j)
-      if (dist[(size_t)i * n + j] > 3 && frag[i] != frag[j] && !pose_invariant(i, j)) row.push_back(j);
+    for (int j = i + 1; j < n; ++j) {
+      if (dist[(size_t)i * n + j] <= 3 || frag[i] == frag[j]) continue;
+      if (!pose_invariant(i, j)) {
+        row.push_back(j);
+        continue;
+      }
+      const bool hb = (tp[b->type[a0 + i]].hb_role == 1 && tp[b->type[a0 + j]].hb_role == 2) ||
+                      (tp[b->type[a0 + i]].hb_role == 2 && tp[b->type[a0 + j]].hb_role == 1);
+      inv_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
+    }
     while (!row.empty()) {
       const int pos = (int)(order.size() / 2);
+      if (pos % 4 == 0) used4 = 0;
+      if (pos % 2 == 0) used2 = 0;
+      if (pos % 8 == 0) used8 = 0;
       size_t best = 0;
-      int best_c = window_cost(pos, row[0]);
+      int best_c = cost(row[0]);
       for (size_t r = 1; r < row.size() && best_c > 0; ++r) {
-        const int c = window_cost(pos, row[r]);
+        const int c = cost(row[r]);
         if (c < best_c) {
           best_c = c;
           best = r;
         }
       }
-      order.push_back(row[best]);
+      const int j = row[best];
+      used4 |= 1u << (j & 3);
+      used2 |= 1u << (j & 1);
+      used8 |= 1u << (j & 7);
+      order.push_back(j);
       order.push_back(i);  // kept in pairs: order[2 p] = j, order[2 p + 1] = i
       row.erase(row.begin() + (long)best);
     }
   }
-  // the pose-invariant pairs (FP64 constant) in plain row order
-  for (int i = 0; i < n; ++i)
-    for (int j = i + 1; j < n; ++j)
-      if (dist[(size_t)i * n + j] > 3 && frag[i] != frag[j] && pose_invariant(i, j)) {
-        const bool hb = (tp[b->type[a0 + i]].hb_role == 1 && tp[b->type[a0 + j]].hb_role == 2) ||
-                        (tp[b->type[a0 + i]].hb_role == 2 && tp[b->type[a0 + j]].hb_role == 1);
-        inv_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
-      }
+  H.pair_rec.reserve(order.size() * 4);
+  H.pair_idx.reserve(order.size() / 2 + inv_idx.size());
   for (size_t p = 0; p < order.size() / 2; ++p) {
     {
       const int j = order[2 * p], i = order[2 * p + 1];
@@ -454,8 +479,8 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, int l, Lig
       const double qi = b->q[a0 + i], qj = b->q[a0 + j];
       const bool hb = (tp[ti].hb_role == 1 && tp[tj].hb_role == 2) ||
                       (tp[ti].hb_role == 2 && tp[tj].hb_role == 1);
-      double c12, c6, c10, w;
-      pair_coeffs(tp, ti, tj, c12, c6, c10, w);
+      const double *cw = TP.at(ti, tj);
+      const double c12 = cw[0], c6 = cw[1], c10 = cw[2], w = cw[3];
       const double si = (double)tp[ti].solpar + kHQasp * std::fabs(qi);
       const double sj = (double)tp[tj].solpar + kHQasp * std::fabs(qj);
       H.pair_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
@@ -480,9 +505,9 @@ void parallel_for(int n, F f) {
   std::atomic<int> next(0);
   auto work = [&]() {
     for (;;) {
-      const int i = next.fetch_add(64);
+      const int i = next.fetch_add(4);
       if (i >= n) break;
-      for (int j = i; j < std::min(n, i + 64); ++j) f(j);
+      for (int j = i; j < std::min(n, i + 4); ++j) f(j);
     }
   };
   std::vector<std::thread> th;
@@ -507,7 +532,8 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
     if (b->atom_off[l + 1] < b->atom_off[l] || b->tors_off[l + 1] < b->tors_off[l])
       return fail(DOCK_EINVAL, "dock_load_ligands: offsets decrease at ligand %d", l);
   std::vector<LigHost> H((size_t)nl);
-  parallel_for(nl, [&](int l) { prepare_ligand(b, P, l, H[l]); });
+  const TypePairTable TP(P);
+  parallel_for(nl, [&](int l) { prepare_ligand(b, P, TP, l, H[l]); });
   for (int l = 0; l < nl; ++l)
     if (!H[l].err.empty()) return fail(DOCK_EINVAL, "dock_load_ligands: %s", H[l].err.c_str());
   dock_ligands *L = new dock_ligands();
@@ -540,7 +566,9 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   std::vector<float4> atoms((size_t)n_atoms), raw((size_t)n_atoms);
   std::vector<double> cent((size_t)nl * 3);
   std::vector<uint32_t> pidx((size_t)np);
-  std::vector<float> prec((size_t)np * 8);
+  // records of the per-pose pairs at their pair offsets; the slots of the
+  // pose-invariant pairs are zeroed per ligand below (no serial fill)
+  std::unique_ptr<float[]> prec(new float[(size_t)np * 8]);
   std::vector<TorInfo> tors((size_t)nt);
   std::vector<uint8_t> moves((size_t)nm);
   parallel_for(nl, [&](int l) {
@@ -553,7 +581,9 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
     }
     for (int m = 0; m < 3; ++m) cent[(size_t)l * 3 + m] = H[l].cent[m];
     std::copy(H[l].pair_idx.begin(), H[l].pair_idx.end(), pidx.begin() + I.pair_off);
-    std::copy(H[l].pair_rec.begin(), H[l].pair_rec.end(), prec.begin() + (size_t)I.pair_off * 8);
+    std::copy(H[l].pair_rec.begin(), H[l].pair_rec.end(), prec.get() + (size_t)I.pair_off * 8);
+    std::fill(prec.get() + ((size_t)I.pair_off + I.n_pairs) * 8,
+              prec.get() + ((size_t)I.pair_off + I.n_pairs_all) * 8, 0.0f);
     std::copy(H[l].tors.begin(), H[l].tors.end(), tors.begin() + I.tors_off);
     if (!H[l].tors.empty())
       std::copy(H[l].moves.begin(), H[l].moves.end(), moves.begin() + H[l].tors[0].move_off);
@@ -577,7 +607,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   CU(up(L->d_centroid, cent.data(), sizeof(double) * cent.size()));
   CU(up(L->d_types, b->type, (size_t)n_atoms));
   CU(up(L->d_pair_idx, pidx.data(), sizeof(uint32_t) * np));
-  CU(up(L->d_pair_rec, prec.data(), sizeof(float) * 8 * np));
+  CU(up(L->d_pair_rec, prec.get(), sizeof(float) * 8 * np));
   CU(up(L->d_tors, tors.data(), sizeof(TorInfo) * nt));
   CU(up(L->d_moves, moves.data(), (size_t)nm));
   CU(launch_intra_const(L->d_info, nl, L->d_atoms_raw, L->d_types, L->d_pair_idx, P->d_params, s));
