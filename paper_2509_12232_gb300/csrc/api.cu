@@ -470,7 +470,7 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, const Type
       row.erase(row.begin() + (long)best);
     }
   }
-  H.pair_rec.reserve(order.size() * 4);
+  H.pair_rec.reserve(order.size() * 2);
   H.pair_idx.reserve(order.size() / 2 + inv_idx.size());
   for (size_t p = 0; p < order.size() / 2; ++p) {
     {
@@ -484,14 +484,13 @@ void prepare_ligand(const dock_ligand_batch *b, const dock_pocket *P, const Type
       const double si = (double)tp[ti].solpar + kHQasp * std::fabs(qi);
       const double sj = (double)tp[tj].solpar + kHQasp * std::fabs(qj);
       H.pair_idx.push_back((uint32_t)i | ((uint32_t)j << 8) | ((uint32_t)(hb ? 1 : 0) << 16));
-      const uint32_t oi = 16u * (uint32_t)i, oj = 16u * (uint32_t)j;
-      float oif, ojf;
-      std::memcpy(&oif, &oi, 4);
-      std::memcpy(&ojf, &oj, 4);
-      const float rec[8] = {(float)c12, (float)c6, (float)c10, (float)(w * kHEmax),
-                            (float)(kHWElec * kHCoulomb * qi * qj),
-                            (float)(kHWSol * (si * tp[tj].vol + sj * tp[ti].vol)), oif, ojf};
-      H.pair_rec.insert(H.pair_rec.end(), rec, rec + 8);
+      (void)w;
+      const uint32_t oij = (16u * (uint32_t)i) | ((16u * (uint32_t)j) << 16);
+      float oijf;
+      std::memcpy(&oijf, &oij, 4);
+      const float rec[4] = {oijf, (float)c12, hb ? (float)-c10 : (float)c6,
+                            (float)(kHWSol * (si * tp[tj].vol + sj * tp[ti].vol))};
+      H.pair_rec.insert(H.pair_rec.end(), rec, rec + 4);
     }
   }
   H.n_var = (int)H.pair_idx.size();
@@ -568,7 +567,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   std::vector<uint32_t> pidx((size_t)np);
   // records of the per-pose pairs at their pair offsets; the slots of the
   // pose-invariant pairs are zeroed per ligand below (no serial fill)
-  std::unique_ptr<float[]> prec(new float[(size_t)np * 8]);
+  std::unique_ptr<float[]> prec(new float[(size_t)np * 4]);
   std::vector<TorInfo> tors((size_t)nt);
   std::vector<uint8_t> moves((size_t)nm);
   parallel_for(nl, [&](int l) {
@@ -581,9 +580,9 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
     }
     for (int m = 0; m < 3; ++m) cent[(size_t)l * 3 + m] = H[l].cent[m];
     std::copy(H[l].pair_idx.begin(), H[l].pair_idx.end(), pidx.begin() + I.pair_off);
-    std::copy(H[l].pair_rec.begin(), H[l].pair_rec.end(), prec.get() + (size_t)I.pair_off * 8);
-    std::fill(prec.get() + ((size_t)I.pair_off + I.n_pairs) * 8,
-              prec.get() + ((size_t)I.pair_off + I.n_pairs_all) * 8, 0.0f);
+    std::copy(H[l].pair_rec.begin(), H[l].pair_rec.end(), prec.get() + (size_t)I.pair_off * 4);
+    std::fill(prec.get() + ((size_t)I.pair_off + I.n_pairs) * 4,
+              prec.get() + ((size_t)I.pair_off + I.n_pairs_all) * 4, 0.0f);
     std::copy(H[l].tors.begin(), H[l].tors.end(), tors.begin() + I.tors_off);
     if (!H[l].tors.empty())
       std::copy(H[l].moves.begin(), H[l].moves.end(), moves.begin() + H[l].tors[0].move_off);
@@ -595,7 +594,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   CU(dalloc(&L->d_centroid, (size_t)nl * 3));
   CU(dalloc(&L->d_types, (size_t)n_atoms));
   CU(dalloc(&L->d_pair_idx, (size_t)np));
-  CU(dalloc(&L->d_pair_rec, (size_t)np * 8));
+  CU(dalloc(&L->d_pair_rec, (size_t)np * 4));
   CU(dalloc(&L->d_tors, (size_t)nt));
   CU(dalloc(&L->d_moves, (size_t)nm));
   auto up = [&](void *dst, const void *src, size_t bytes) -> cudaError_t {
@@ -607,7 +606,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   CU(up(L->d_centroid, cent.data(), sizeof(double) * cent.size()));
   CU(up(L->d_types, b->type, (size_t)n_atoms));
   CU(up(L->d_pair_idx, pidx.data(), sizeof(uint32_t) * np));
-  CU(up(L->d_pair_rec, prec.get(), sizeof(float) * 8 * np));
+  CU(up(L->d_pair_rec, prec.get(), sizeof(float) * 4 * np));
   CU(up(L->d_tors, tors.data(), sizeof(TorInfo) * nt));
   CU(up(L->d_moves, moves.data(), (size_t)nm));
   CU(launch_intra_const(L->d_info, nl, L->d_atoms_raw, L->d_types, L->d_pair_idx, P->d_params, s));
@@ -616,7 +615,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   L->total_tors = nt;
   L->total_moved = nm;
   L->h2d_bytes = (int64_t)(sizeof(LigInfo) * nl + 2 * sizeof(float4) * n_atoms + sizeof(double) * 3 * nl +
-                           n_atoms + (sizeof(uint32_t) + 8 * sizeof(float)) * np + sizeof(TorInfo) * nt + nm);
+                           n_atoms + (sizeof(uint32_t) + 4 * sizeof(float)) * np + sizeof(TorInfo) * nt + nm);
   *out = guard.release();
   return DOCK_OK;
 }

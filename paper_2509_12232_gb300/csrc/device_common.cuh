@@ -304,6 +304,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
   e = __fadd_rn(__fsub_rn(a, aa), __fsub_rn(b, bb));
 }
 
+// One 128-bit read-only load.
+__device__ __forceinline__ float4 ld4(const float *p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
 // One 256-bit read-only load (8 floats, 32-byte aligned address).
 __device__ __forceinline__ void ld8(const float *p, float (&v)[8]) {
   asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -355,6 +364,31 @@ __device__ __forceinline__ float pair_energy(float r2, const float (&rec)[8]) {
   return r2 < kCutoff2 ? e : 0.0f;
 }
 
+
+// The same pair energy from a 16-byte record {offsets, c12, cb, ds}: cb = c6
+// for a 12-6 pair and -c10 for a 12-10 (H-bond) pair, whose sign also picks
+// the cap w EMAX; qq = W_elec 332.06363 q_i q_j is the product of the two
+// atoms' scaled charges.
+__device__ __forceinline__ float pair_energy16(float r2, float c12, float cb, float ds, float qq) {
+  const float kLb = (float)(-kDielLambda * kDielB * 1.4426950408889634);  // ex2 argument per A
+  const float kS = (float)(-1.4426950408889634 / (2.0 * kSigma * kSigma));
+  const float dA = (float)kDielA, dB = (float)kDielB, dK = (float)kDielK;
+  const float kCapVdw = (float)((double)kWVdw * kEmax), kCapHb = (float)((double)kWHb * kEmax);
+  const float r2c = fmaxf(r2, kRmin2);
+  const float ir = rsqrt_ftz(r2c);
+  const float ir2 = ir * ir;
+  const float r = r2c * ir;
+  const float ir4 = ir2 * ir2;
+  const float ir6 = ir4 * ir2;
+  const bool hb = cb < 0.0f;
+  // r^-6 (c12 r^-6 - c6) or r^-6 (c12 r^-6 - c10 r^-4)
+  const float disp = fminf(ir6 * fmaf(c12, ir6, -fabsf(cb) * (hb ? ir4 : 1.0f)), hb ? kCapHb : kCapVdw);
+  const float onek = 1.0f + dK * ex2_ftz(kLb * r);
+  const float elec = qq * onek * rcp_ftz((dA * onek + dB) * r);
+  const float des = ds * ex2_ftz(kS * r2c);
+  const float e = disp + elec + des;
+  return r2 < kCutoff2 ? e : 0.0f;
+}
 
 // Grid lookup of M_t + q E + |q| D split in two halves so other work can run
 // while the loads are in flight: grid_issue computes the cell and fetches the

@@ -44,11 +44,12 @@ struct Item {
 };
 
 // pair_idx (u32, FP64 path): bits 0-7 atom i, 8-15 atom j, 16 H-bond flag.
-// pair_rec (FP32 path): 8 floats per pair, 32-byte aligned, weights folded in:
-// {c12, c6, c10, cap, qq, ds, bits(16 i), bits(16 j)} (the atoms' byte offsets
-// in a pose's coordinate slot) for
-// E = min(c12 r^-12 - c6 r^-6 - c10 r^-10, cap) + qq / (eps(r) r) + ds exp(-r^2 / 2 sigma^2),
-// c6 = 0 for an H-bond (12-10) pair and c10 = 0 otherwise; cap = w * EMAX.
+// pair_rec (FP32 path): 4 floats per pair, 16-byte aligned:
+// {bits(16 i | 16 j << 16), c12, cb, ds} (atoms' byte offsets in a pose's
+// coordinate slot; weights folded in; cb = c6 for a 12-6 pair and -c10 for a
+// 12-10 H-bond pair) for
+// E = min(c12 r^-12 - c6 r^-6 - c10 r^-10, w EMAX) + qq / (eps(r) r) + ds exp(-r^2 / 2 sigma^2);
+// qq comes from the scaled charges the pose slots carry.
 
 struct GridView {
   const float4 *maps;   // [n_types][n][n][n] {M_t, E, D, 0}

@@ -23,7 +23,7 @@ __host__ __device__ constexpr int slots_bytes(int threads, int L, int apl) {
 struct LigView {
   const float4 *atoms;      // this ligand's atoms (centred) + charge
   const uint8_t *types;
-  const float *pair_rec;    // 8 floats per pair
+  const float *pair_rec;    // 4 floats per pair
   const TorInfo *tors;
   int n, k, n_pairs;
   float intra_const;  // energy of the pose-invariant pairs
@@ -35,7 +35,7 @@ __device__ __forceinline__ LigView lig_view(const LigInfo &li, const float4 *ato
   LigView v;
   v.atoms = atoms + li.atom_off;
   v.types = types + li.atom_off;
-  v.pair_rec = pair_rec + (int64_t)li.pair_off * 8;
+  v.pair_rec = pair_rec + (int64_t)li.pair_off * 4;
   v.tors = tors + li.tors_off;
   v.n = li.n;
   v.k = li.k;
@@ -48,9 +48,10 @@ __device__ __forceinline__ float4 slot_row(const float4 *slot, uint32_t byte_off
   return *reinterpret_cast<const float4 *>(reinterpret_cast<const char *>(slot) + byte_off);
 }
 
-// Pair terms of one lane, pairs lane, lane + L, ... of the row-major list:
-// consecutive pairs of a lane mostly share atom i, whose coordinates stay in
-// registers. The record carries the byte offsets of both atoms in the slot.
+// Pair terms of one lane, pairs lane, lane + L, ... of the row-ordered list:
+// consecutive pairs of a lane mostly share atom i, whose coordinates (and
+// scaled charge, in w) stay in registers. The 16-byte record carries the byte
+// offsets of both atoms in the slot.
 template <int L>
 struct PairWalker {
   const float *rec;  // this lane's first record
@@ -58,19 +59,19 @@ struct PairWalker {
   uint32_t last_i = 0xffffffffu;
   float4 ci;
   __device__ __forceinline__ PairWalker(const LigView &v, const float4 *s, int lane)
-      : rec(v.pair_rec + lane * 8), slot(s) {}
+      : rec(v.pair_rec + lane * 4), slot(s) {}
   // m: the lane's pair counter (pair lane + m L)
   __device__ __forceinline__ float term(int m) {
-    float r[8];
-    ld8(rec + m * (8 * L), r);
-    const uint32_t oi = __float_as_uint(r[6]);
+    const float4 r = ld4(rec + m * (4 * L));
+    const uint32_t oij = __float_as_uint(r.x);
+    const uint32_t oi = oij & 0xffffu;
     if (oi != last_i) {
       ci = slot_row(slot, oi);
       last_i = oi;
     }
-    const float4 b = slot_row(slot, __float_as_uint(r[7]));
+    const float4 b = slot_row(slot, oij >> 16);
     const float dx = ci.x - b.x, dy = ci.y - b.y, dz = ci.z - b.z;
-    return pair_energy(dx * dx + dy * dy + dz * dz, r);
+    return pair_energy16(dx * dx + dy * dy + dz * dz, r.y, r.z, r.w, ci.w * b.w);
   }
 };
 
@@ -91,11 +92,14 @@ __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], con
   const float r20 = 2.f * (qx * qz - qw * qy), r21 = 2.f * (qy * qz + qw * qx),
               r22 = 1.f - 2.f * (qx * qx + qy * qy);
   const float tx = cx + g[0], ty = cy + g[1], tz = cz + g[2];
+  // w of a row: the atom's charge scaled by sqrt(W_elec 332.06363), so that a
+  // pair's qq is the product of its two rows' w
+  const float kq = (float)sqrt((double)kWElec * kCoulomb);
   for (int a = lane; a < V.n; a += L) {
     const float4 p = __ldg(V.atoms + a);
     slot[a] = make_float4(r00 * p.x + r01 * p.y + r02 * p.z + tx,
                           r10 * p.x + r11 * p.y + r12 * p.z + ty,
-                          r20 * p.x + r21 * p.y + r22 * p.z + tz, 0.0f);
+                          r20 * p.x + r21 * p.y + r22 * p.z + tz, kq * p.w);
   }
   __syncwarp(gmask);
   // ---- torsions root to leaf, each about the current bond axis ------------
@@ -120,7 +124,7 @@ __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], con
         const float vx = p.x - pa.x, vy = p.y - pa.y, vz = p.z - pa.z;
         slot[at] = make_float4(pa.x + m00 * vx + m01 * vy + m02 * vz,
                                pa.y + m10 * vx + m11 * vy + m12 * vz,
-                               pa.z + m20 * vx + m21 * vy + m22 * vz, 0.0f);
+                               pa.z + m20 * vx + m21 * vy + m22 * vz, p.w);
       }
       __syncwarp(gmask);
     }
@@ -153,10 +157,16 @@ __device__ __forceinline__ float score_posed(const LigView &V, const GridView &G
       coords_out[3 * a + 2] = pa.z;
     }
     const int m_end = min(np_l, m + ppa);
-    for (; m + 3 < m_end; m += 4) {
+    for (; m + 7 < m_end; m += 8) {
+      const float e0 = W.term(m), e1 = W.term(m + 1), e2 = W.term(m + 2), e3 = W.term(m + 3);
+      const float e4 = W.term(m + 4), e5 = W.term(m + 5), e6 = W.term(m + 6), e7 = W.term(m + 7);
+      acc.add(((e0 + e1) + (e2 + e3)) + ((e4 + e5) + (e6 + e7)));
+    }
+    if (m + 3 < m_end) {
       const float e0 = W.term(m), e1 = W.term(m + 1);
       const float e2 = W.term(m + 2), e3 = W.term(m + 3);
       acc.add((e0 + e1) + (e2 + e3));
+      m += 4;
     }
     acc.add(grid_finish(lk));
   }
