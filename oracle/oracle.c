@@ -13,6 +13,8 @@
  *     (per ligand atom pair) with electrostatic, van der Waals, hydrogen-bond
  *     and desolvation terms.
  *   Section V: a genetic algorithm without local search proposes the poses.
+ *   Optionally, the Lamarckian variant of AutoDock's search that the paper
+ *   leaves out: Solis-Wets local search on a share of each generation.
  * The paper prints no formulas or constants. The energy terms follow the
  * AutoDock4 free-energy function the paper names as its equivalent
  * (Section V, citing AutoDock4): 12-6 dispersion/repulsion, 12-10 hydrogen
@@ -647,6 +649,118 @@ void orc_ga_children(int k, int P, int n, float p_cross, float p_mut, uint64_t s
 }
 
 /* ======================================================================= */
+/* Solis-Wets local search: the Lamarckian variant of the GA. The paper's   */
+/* search has none (Section V); AutoDock's Lamarckian GA (Morris et al.      */
+/* 1998, in the paper's references) refines a share of each generation with  */
+/* the random search with bias of Solis & Wets (1981, Math. Oper. Res. 6).   */
+/* Readings, one step per iteration t of one individual x with score f:      */
+/*   step_e = (rho * sigma_e) * N(0,1), sigma = the mutation scales (1 A,    */
+/*     0.1 per quaternion component, 0.5 rad per torsion);                   */
+/*   xi = b + step; probe x + xi; if its score is lower, accept it and set   */
+/*     b = 0.2 b + 0.4 xi; otherwise probe x - xi; if that is lower, accept   */
+/*     it and set b = b - 0.4 xi; otherwise b = 0.5 b;                       */
+/*   an accepted probe counts a success (failures reset), else a failure     */
+/*     (successes reset); max_succ successes in a row double rho, max_fail    */
+/*     failures in a row halve it (counter reset);                           */
+/*   stop after max_its iterations or when rho < rho_lb.                     */
+/* A probe wraps torsions as the mutation does and renormalises the         */
+/* quaternion. NaN scores count as +inf. Genotype arithmetic is correctly    */
+/* rounded FP32 as in the GA. Random numbers: the GA's Philox counters with  */
+/* the generation word OR 2^31; the normal of gene e at iteration t uses     */
+/* slots 64 t + 2 e and 64 t + 2 e + 1; whether an individual is refined in  */
+/* a generation is decided by word 0 of slot 63 against the rate.            */
+/* ======================================================================= */
+typedef struct {
+  float rate;                    /* probability an individual is refined      */
+  int32_t max_its, max_succ, max_fail;
+  float rho, rho_lb;
+} orc_ls_params;
+
+/* objective of a probe: it = iteration, which = 0 forward / 1 backward */
+typedef float (*orc_objective)(const float *g, int32_t it, int32_t which, void *ctx);
+
+#define LS_GEN_BIT 0x80000000u
+
+int orc_ls_selected(float rate, uint64_t seed, uint64_t lig, uint32_t gen, uint32_t ind) {
+  uint32_t w[8];
+  orc_rng_words(seed, lig, gen | LS_GEN_BIT, ind, 63, w);
+  return (uint64_t)w[0] < prob_threshold(rate);
+}
+
+static float gene_sigma(int e) { return e < 3 ? 1.0f : (e < 7 ? 0.1f : 0.5f); }
+
+static float nan_to_inf(float v) { return v != v ? INFINITY : v; }
+
+/* y = x + xi (dir > 0) or x - xi (dir < 0), torsions wrapped, quaternion
+ * renormalised */
+static void ls_probe(int G, const float *x, const float *xi, int dir, float *y) {
+  for (int e = 0; e < G; ++e) {
+    y[e] = dir > 0 ? x[e] + xi[e] : x[e] - xi[e];
+    if (e >= 7) {
+      if (y[e] > PI_F) y[e] = y[e] - TWO_PI_F;
+      else if (y[e] < -PI_F) y[e] = y[e] + TWO_PI_F;
+    }
+  }
+  quat_normalize(y + 3);
+}
+
+/* Refines x (in/out, 7 + k genes) with score *f (in/out); returns the number
+ * of objective evaluations, the iterations run in *its. */
+int orc_solis_wets(int k, const orc_ls_params *p, uint64_t seed, uint64_t lig, uint32_t gen,
+                   uint32_t ind, float *x, float *f, orc_objective obj, void *ctx, int32_t *its) {
+  int G = 7 + k, evals = 0, succ = 0, fail = 0, t;
+  float b[32], xi[32], y[32];
+  float rho = p->rho, fx = nan_to_inf(*f);
+  for (int e = 0; e < G; ++e) b[e] = 0.0f;
+  for (t = 0; t < p->max_its && !(rho < p->rho_lb); ++t) {
+    for (int e = 0; e < G; ++e) {
+      float z = orc_normal(seed, lig, gen | LS_GEN_BIT, ind, 64u * (uint32_t)t + 2u * (uint32_t)e);
+      float step = (rho * gene_sigma(e)) * z;
+      xi[e] = b[e] + step;
+    }
+    int ok = 0;
+    ls_probe(G, x, xi, +1, y);
+    float f1 = nan_to_inf(obj(y, t, 0, ctx));
+    ++evals;
+    if (f1 < fx) {
+      memcpy(x, y, sizeof(float) * G);
+      fx = f1;
+      ok = 1;
+      for (int e = 0; e < G; ++e) b[e] = 0.2f * b[e] + 0.4f * xi[e];
+    } else {
+      ls_probe(G, x, xi, -1, y);
+      float f2 = nan_to_inf(obj(y, t, 1, ctx));
+      ++evals;
+      if (f2 < fx) {
+        memcpy(x, y, sizeof(float) * G);
+        fx = f2;
+        ok = 1;
+        for (int e = 0; e < G; ++e) b[e] = b[e] - 0.4f * xi[e];
+      } else {
+        for (int e = 0; e < G; ++e) b[e] = 0.5f * b[e];
+      }
+    }
+    if (ok) {
+      ++succ;
+      fail = 0;
+    } else {
+      ++fail;
+      succ = 0;
+    }
+    if (succ >= p->max_succ) {
+      rho = 2.0f * rho;
+      succ = 0;
+    } else if (fail >= p->max_fail) {
+      rho = 0.5f * rho;
+      fail = 0;
+    }
+  }
+  *f = fx;
+  if (its) *its = t;
+  return evals;
+}
+
+/* ======================================================================= */
 /* Whole search for a set of ligands (free-run: the oracle's own scores,     */
 /* rounded to float, drive selection), pthreads with a shared ligand index   */
 /* as in the paper's node-level work stealing (Section IV, Section VII).     */
@@ -655,6 +769,7 @@ typedef struct {
   int32_t pop, generations;
   float p_cross, p_mut;
   uint64_t seed;
+  orc_ls_params ls;  /* rate 0: GA only (the paper's search) */
 } orc_search;
 
 typedef struct {
@@ -679,6 +794,28 @@ typedef struct {
   volatile int next;
   pthread_mutex_t mu;
 } dock_ctx;
+
+/* objective of the oracle's own search: the FP64 score rounded to float */
+typedef struct {
+  const orc_ligand *L;
+  const orc_params *p;
+  const orc_grid *G;
+  const orc_pocket *P;
+  const uint8_t *moves;
+  const int32_t *pairs;
+  int np;
+  double *xyz;
+  double last;
+} ls_ctx;
+
+static float ls_objective(const float *g, int32_t it, int32_t which, void *ctx) {
+  ls_ctx *X = (ls_ctx *)ctx;
+  (void)it;
+  (void)which;
+  orc_pose(X->L, X->moves, g, X->P->center, 0, X->xyz);
+  X->last = orc_inter_grid(X->L, X->G, X->xyz, NULL) + orc_intra(X->L, X->p, X->pairs, X->np, X->xyz, NULL);
+  return (float)X->last;
+}
 
 static void dock_one(dock_ctx *C, int l) {
   const orc_batch *b = C->b;
@@ -706,6 +843,17 @@ static void dock_one(dock_ctx *C, int l) {
       orc_pose(&L, moves, ga + (size_t)i * G, C->P->center, 0, xyz);
       s64[i] = orc_inter_grid(&L, C->G, xyz, NULL) + orc_intra(&L, C->p, pairs, np, xyz, NULL);
       sc[i] = (float)s64[i];
+    }
+    if (C->s->ls.rate > 0.0f) {
+      /* Lamarckian step: the selected individuals are refined in place */
+      ls_ctx X = {&L, C->p, C->G, C->P, moves, pairs, np, xyz, 0.0};
+      for (int i = 0; i < P; ++i) {
+        if (!orc_ls_selected(C->s->ls.rate, C->s->seed, lig, (uint32_t)gen, (uint32_t)i)) continue;
+        orc_solis_wets(L.k, &C->s->ls, C->s->seed, lig, (uint32_t)gen, (uint32_t)i,
+                       ga + (size_t)i * G, sc + i, ls_objective, &X, NULL);
+        orc_pose(&L, moves, ga + (size_t)i * G, C->P->center, 0, xyz);
+        s64[i] = orc_inter_grid(&L, C->G, xyz, NULL) + orc_intra(&L, C->p, pairs, np, xyz, NULL);
+      }
     }
   }
   for (int i = 0; i < P; ++i) {

@@ -81,9 +81,18 @@ class OrcGrid(C.Structure):
                 ("maps", P_d)]
 
 
+class OrcLsParams(C.Structure):
+    _fields_ = [("rate", C.c_float), ("max_its", C.c_int32), ("max_succ", C.c_int32),
+                ("max_fail", C.c_int32), ("rho", C.c_float), ("rho_lb", C.c_float)]
+
+
 class OrcSearch(C.Structure):
     _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("p_cross", C.c_float),
-                ("p_mut", C.c_float), ("seed", C.c_uint64)]
+                ("p_mut", C.c_float), ("seed", C.c_uint64), ("ls", OrcLsParams)]
+
+
+# objective of a Solis-Wets probe: (genotype, iteration, 0 forward / 1 backward, ctx) -> score
+LS_OBJECTIVE = C.CFUNCTYPE(C.c_float, C.POINTER(C.c_float), C.c_int32, C.c_int32, C.c_void_p)
 
 
 class OrcBatch(C.Structure):
@@ -138,6 +147,12 @@ def _declare(L):
     L.orc_ga_children.restype = None
     L.orc_ga_children.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64,
                                   C.c_uint64, C.c_uint32, P_f, P_f, P_f]
+    L.orc_ls_selected.restype = C.c_int
+    L.orc_ls_selected.argtypes = [C.c_float, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32]
+    L.orc_solis_wets.restype = C.c_int
+    L.orc_solis_wets.argtypes = [C.c_int, C.POINTER(OrcLsParams), C.c_uint64, C.c_uint64,
+                                 C.c_uint32, C.c_uint32, P_f, P_f, LS_OBJECTIVE, C.c_void_p,
+                                 P_i32]
     L.orc_dock_batch.restype = None
     L.orc_dock_batch.argtypes = [C.POINTER(OrcBatch), C.POINTER(OrcParams), C.POINTER(OrcPocket),
                                  C.POINTER(OrcGrid), C.POINTER(OrcSearch), C.c_int, P_f, P_f, P_d,
@@ -399,6 +414,45 @@ def ga_children(k: int, pop: int, n: int, p_cross: float, p_mut: float, seed: in
     return out.reshape(n, 7 + k)
 
 
+class LsParams:
+    """Solis-Wets settings; the defaults are AutoDock's published ones (Morris et
+    al. 1998): 6% of the individuals per generation, at most 300 iterations,
+    rho doubled after 4 successes and halved after 4 failures in a row, from
+    1.0 down to 0.01."""
+
+    def __init__(self, rate=0.06, max_its=300, max_succ=4, max_fail=4, rho=1.0, rho_lb=0.01):
+        self.s = OrcLsParams(rate, max_its, max_succ, max_fail, rho, rho_lb)
+
+
+def ls_selected(rate: float, seed: int, lig_id: int, gen: int, ind: int) -> bool:
+    """Whether individual `ind` of generation `gen` is refined (Solis-Wets)."""
+    return bool(lib().orc_ls_selected(rate, seed, lig_id, gen, ind))
+
+
+def solis_wets(k: int, ls: LsParams, seed: int, lig_id: int, gen: int, ind: int, x0, f0,
+               objective):
+    """Solis-Wets local search of one individual (oracle.c states the steps).
+    objective(genotype float32[7 + k], iteration, which) -> score, which = 0
+    for the probe x + xi and 1 for x - xi. Returns (x, f, iterations, evals)."""
+    x = np.array(x0, np.float32).reshape(7 + k).copy()
+    f = np.array([f0], np.float32)
+    err = []
+
+    def cb(g, it, which, _ctx):
+        try:
+            return float(objective(np.ctypeslib.as_array(g, (7 + k,)).copy(), it, which))
+        except Exception as e:  # noqa: BLE001 - reported after the C call returns
+            err.append(e)
+            return float("nan")
+    fn = LS_OBJECTIVE(cb)
+    its = C.c_int32(0)
+    ev = lib().orc_solis_wets(k, C.byref(ls.s), seed, lig_id, gen, ind, _p(x, P_f), _p(f, P_f),
+                              fn, None, C.byref(its))
+    if err:
+        raise err[0]
+    return x, float(f[0]), int(its.value), int(ev)
+
+
 def _order_key(scores):
     """Sort key of FP32 scores: NaN counts as +inf (the GA's comparison)."""
     s = np.asarray(scores, np.float32).astype(np.float64)
@@ -422,8 +476,11 @@ def merge(pop_scores, kept_scores, pop: int):
 
 
 def dock_batch(ligs, params: Params, pocket: PocketS, grid: Grid, pop: int, generations: int,
-               p_cross: float = 0.8, p_mut: float = 0.02, seed: int = 0, n_threads: int = 0):
-    """Free-run search over a CSR ligand set (synth.LigandSet fields)."""
+               p_cross: float = 0.8, p_mut: float = 0.02, seed: int = 0, n_threads: int = 0,
+               ls: LsParams | None = None):
+    """Free-run search over a CSR ligand set (synth.LigandSet fields); with
+    `ls`, the Lamarckian variant (Solis-Wets on the selected individuals of
+    every generation, the oracle's own FP32-rounded scores as objective)."""
     a = dict(atom_off=_c(ligs.atom_off, np.int32), tors_off=_c(ligs.tors_off, np.int32),
              x=_c(ligs.x, np.float32), y=_c(ligs.y, np.float32), z=_c(ligs.z, np.float32),
              q=_c(ligs.q, np.float32), type=_c(ligs.type, np.uint8),
@@ -433,7 +490,8 @@ def dock_batch(ligs, params: Params, pocket: PocketS, grid: Grid, pop: int, gene
     b = OrcBatch(nl, _p(a["atom_off"], P_i32), _p(a["tors_off"], P_i32), _p(a["x"], P_f),
                  _p(a["y"], P_f), _p(a["z"], P_f), _p(a["q"], P_f), _p(a["type"], P_u8),
                  _p(a["parent"], P_i16), _p(a["tors_b"], P_i16), _p(a["ligand_id"], P_u64))
-    s = OrcSearch(pop, generations, p_cross, p_mut, seed)
+    s = OrcSearch(pop, generations, p_cross, p_mut, seed,
+                  ls.s if ls is not None else OrcLsParams(0.0, 0, 1, 1, 1.0, 0.0))
     geno = np.zeros((nl, pop, 23), np.float32)
     score = np.zeros((nl, pop), np.float32)
     best64 = np.zeros((nl, 8), np.float64)
