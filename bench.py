@@ -13,6 +13,10 @@ its host-side preparation, the search, and the D2H copy of the results).
 Under torchrun each rank docks its own shard of the same size (weak scaling,
 no collective on the data path).
 
+--mode lga runs the same workload as the Lamarckian variant (Solis-Wets
+refinement of 6% of each generation, at most 300 iterations: AutoDock's
+settings) and prints its own line.
+
 --impl reference times the CPU oracle (plain FP64 C, all host cores) on a
 bounded sample of the same workload; it is the only other user of oracle/.
 """
@@ -37,8 +41,12 @@ WORKLOAD = "c2"
 METRIC = "ligands/s (plain exact GA docking: 1,024 poses x 50 generations per ligand)"
 DESCR = ("1,000 synthetic ligands (10-60 heavy atoms, 0-12 torsions) vs a 4,000-atom pocket "
          "(16 A cavity, 86^3 x 7 grid maps), 1,024 poses x 50 generations, FP64 best-8 rescoring")
+METRIC_LGA = ("ligands/s (Lamarckian GA docking: 1,024 poses x 50 generations per ligand, "
+              "Solis-Wets on 6% of each generation, up to 300 iterations)")
+LS_DEFAULTS = dict(rate=0.06, max_its=300, max_succ=4, max_fail=4, rho=1.0, rho_lb=0.01)
 
-# Algorithmic work per pose (FMA = 2 flops); see DESIGN.md "Roofline".
+# Algorithmic work per pose (FMA = 2 flops), counted from the operations of
+# Algorithms 1 and 2.
 FLOP_RIGID_PER_ATOM = 18        # 3x3 rotation + translation
 FLOP_POSE_FIXED = 40            # quaternion -> matrix
 FLOP_TORSION = 40               # axis, sin/cos, rotation matrix
@@ -189,9 +197,9 @@ def run_reference(args, rank, world):
     return 0
 
 
-def cpu_baseline(budget_s):
+def cpu_baseline(budget_s, lga=False):
     """The oracle as it stands, on all host cores, on a bounded sample of the
-    workload (about budget_s seconds)."""
+    workload (about budget_s seconds); lga: the Lamarckian variant."""
     from oracle import oracle as o
     from paper_2509_12232_gb300 import synth
     pk, ligs, w = synth.make_workload(WORKLOAD)
@@ -199,10 +207,11 @@ def cpu_baseline(budget_s):
     pks = o.pocket_from(pk)
     grid = o.grid_build(pks, P)
     cores = os.cpu_count() or 1
+    ls = o.LsParams(**LS_DEFAULTS) if lga else None
     # calibrate on one ligand x 2 generations
     sub = ligs.subset([0])
     t0 = time.perf_counter()
-    o.dock_batch(sub, P, pks, grid, pop=w.pop, generations=2, seed=0, n_threads=1)
+    o.dock_batch(sub, P, pks, grid, pop=w.pop, generations=2, seed=0, n_threads=1, ls=ls)
     per_lig = (time.perf_counter() - t0) / 2 * w.generations
     per_lig *= float(np.diff(ligs.atom_off).mean() ** 2) / float(ligs.n_atoms(0) ** 2)
     n = int(max(cores, min(ligs.n_ligands, round(budget_s * cores / max(per_lig, 1e-3)))))
@@ -210,7 +219,8 @@ def cpu_baseline(budget_s):
     idx = list(range(n))
     sub = ligs.subset(idx)
     t0 = time.perf_counter()
-    o.dock_batch(sub, P, pks, grid, pop=w.pop, generations=w.generations, seed=0, n_threads=cores)
+    o.dock_batch(sub, P, pks, grid, pop=w.pop, generations=w.generations, seed=0, n_threads=cores,
+                 ls=ls)
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "ligands/s", "cores": cores, "kind": "oracle",
             "sample": "first %d ligands of the %s set, full %d poses x %d generations each, %.1f s" % (
@@ -411,9 +421,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="plain", choices=["plain", "surrogate", "mlp", "grid"],
-                    help="surrogate: pre-screened vs plain comparison; mlp: the surrogate "
-                         "network's forward pass and training step alone (each its own JSON line)")
+    ap.add_argument("--mode", default="plain", choices=["plain", "lga", "surrogate", "mlp", "grid"],
+                    help="lga: the Lamarckian search (Solis-Wets); surrogate: pre-screened vs "
+                         "plain comparison; mlp: the surrogate network's forward pass and training "
+                         "step alone; grid: the pocket grid build (each its own JSON line)")
     ap.add_argument("--ref-ligands-per-core", type=int, default=1)
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -473,9 +484,12 @@ def main():
     groups = sorted({next(L for L in (1, 2, 4, 8) if L * apl >= n or L == 8)
                      for n in np.diff(ligs.atom_off)})
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    lga = args.mode == "lga"
+    ls = dock.ls_params(**LS_DEFAULTS) if lga else None
 
     def step():
-        job = dock.dock_batch(pocket, gl, w.pop, w.generations, seed=0, use_graph=1, stream=stream)
+        job = dock.dock_batch(pocket, gl, w.pop, w.generations, seed=0, use_graph=1, stream=stream,
+                              ls=ls)
         return job
 
     # warm-up
@@ -483,10 +497,12 @@ def main():
         j = step()
         torch.cuda.synchronize()
         j.close()
-    # per-launch kernel times for the roofline (separate profiled pass)
+    # per-launch kernel times for the roofline (separate profiled pass); in
+    # the Lamarckian search also the scorings per ligand (GA + local search)
     os.environ["DOCK_PROFILE_LAUNCHES"] = "1"
     j = step()
     ms_kernels, n_launch = dock.dock_job_kernel_time(j)
+    evals_total = int(dock.dock_results(j)["exact_evals"].sum())
     j.close()
     del os.environ["DOCK_PROFILE_LAUNCHES"]
     # timed region
@@ -525,7 +541,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         g2 = dock.dock_load_ligands(pocket, *largs, stream=stream)
-        j = dock.dock_batch(pocket, g2, w.pop, w.generations, seed=0, use_graph=1, stream=stream)
+        j = dock.dock_batch(pocket, g2, w.pop, w.generations, seed=0, use_graph=1, stream=stream,
+                            ls=ls)
         dock.dock_results(j)
         j.close()
         g2.close()
@@ -546,17 +563,22 @@ def main():
     mufu_peak = n_sm * 16 * sm_mhz * 1e6 / 1e12                 # Tops/s
     flops_pose, mufu_pose = work_per_pose(info, w.n_ligands)
     per_gen_s = ms_kernels / 1000.0 / max(n_launch, 1)
-    ach_fp32 = flops_pose * w.pop / per_gen_s / 1e12
-    ach_mufu = mufu_pose * w.pop / per_gen_s / 1e12
+    # poses scored per generation per ligand: pop (GA), plus in the Lamarckian
+    # search the local-search probes (the mean per-pose work of the set)
+    poses_gen = w.pop if not lga else evals_total / w.n_ligands / w.generations
+    ach_fp32 = flops_pose * poses_gen / per_gen_s / 1e12
+    ach_mufu = mufu_pose * poses_gen / per_gen_s / 1e12
     roof = {"bound": "alu", "achieved": round(ach_fp32, 3), "peak": round(fp32_peak, 2),
             "unit": "TFLOP/s", "frac": round(ach_fp32 / fp32_peak, 4),
-            "traffic": read_traffic(), "kernel": "search_kernel",
+            "traffic": None if lga else read_traffic(),
+            "kernel": "search_kernel + ls_kernel" if lga else "search_kernel",
             "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
             "mufu": {"achieved": round(ach_mufu, 4), "peak": round(mufu_peak, 4), "unit": "Tops/s",
                      "frac": round(ach_mufu / mufu_peak, 4)},
             "generation_ms": round(per_gen_s * 1000, 4), "generations_timed": n_launch,
             "launches_per_generation": len(groups), "lanes_per_pose_groups": groups}
-    line = {"metric": METRIC, "value": round(value, 2), "unit": "ligands/s", "n_gpus": world,
+    line = {"metric": METRIC_LGA if lga else METRIC, "value": round(value, 2), "unit": "ligands/s",
+            "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
@@ -565,14 +587,18 @@ def main():
                        "launch_shape": {"threads": shape["threads"],
                                         "atoms_per_lane": shape["atoms_per_lane"],
                                         "picked_by": picked_by}},
-            "poses_scored_per_s": round(poses_per_step / (ms_step / 1000.0), 1),
+            "poses_scored_per_s": round((evals_total * world if lga else poses_per_step) /
+                                        (ms_step / 1000.0), 1),
             "roofline": roof,
             "e2e": {"value": round(total_ligands / e2e_s, 2), "unit": "ligands/s",
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": args.steps * (w.generations * len(groups) + 1),
+            "gpu_launches": args.steps * (w.generations * len(groups) * (2 if lga else 1) + 1),
             "clocks": clk}
+    if lga:
+        line["config"]["local_search"] = dict(LS_DEFAULTS, method="Solis-Wets, Lamarckian")
+        line["scorings_per_step"] = evals_total * world
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_baseline_seconds)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_baseline_seconds, lga=lga)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -149,6 +149,35 @@ int dock_ligands_info(const dock_ligands *ligands, int32_t *n_ligands, int64_t *
 /* ------------------------------------------------------------------------ */
 typedef struct dock_surrogate dock_surrogate;
 
+/* Solis-Wets local search: the Lamarckian variant of AutoDock's GA (Morris
+ * et al. 1998, in the paper's references; the random search with bias of
+ * Solis & Wets 1981). The paper's own search has none (Section V). One
+ * iteration on genotype x with score f: step_e = (rho sigma_e) N(0,1) with
+ * the mutation scales sigma (1 A, 0.1, 0.5 rad); xi = b + step; probe x + xi,
+ * accepted if its score is lower (b = 0.2 b + 0.4 xi), else probe x - xi,
+ * accepted if lower (b = b - 0.4 xi), else b = 0.5 b; max_succ successes in a
+ * row double rho, max_fail failures in a row halve it; the search ends after
+ * max_its iterations or once rho < rho_lb. Probes wrap torsions as the
+ * mutation does and renormalise the quaternion; NaN scores count as +inf;
+ * genotype arithmetic is correctly rounded FP32 (bit-exact with the CPU
+ * oracle given the same scores). Random numbers: the GA's Philox counters
+ * with the generation word OR 2^31 (normals of iteration t, gene e from slots
+ * 64 t + 2 e, +1; the selection draw is word 0 of slot 63). */
+typedef struct {
+  float rate;                    /* dock_batch: probability that an individual
+                                    is refined after scoring, every generation
+                                    (0 = the paper's GA without local search;
+                                    AutoDock: 0.06); ignored by
+                                    dock_local_search (every pose is refined)  */
+  int32_t max_its;               /* iterations per refinement, 1..DOCK_LS_MAX_ITS
+                                    (AutoDock: 300)                            */
+  int32_t max_succ, max_fail;    /* >= 1 (AutoDock: 4 and 4)                   */
+  float rho, rho_lb;             /* initial step scale and the stop threshold,
+                                    finite, rho > 0 (AutoDock: 1.0, 0.01)       */
+} dock_ls_params;
+
+#define DOCK_LS_MAX_ITS 10000
+
 typedef struct {
   int32_t pop;                   /* individuals per ligand, 2..DOCK_MAX_POP     */
   int32_t generations;           /* scoring passes, >= 1 (generation 0 = init)  */
@@ -172,6 +201,20 @@ typedef struct {
                                     (1..candidates), merged (mu + lambda) with the
                                     population by exact score                   */
   dock_surrogate *surrogate;     /* surrogate: the trained network                */
+  dock_ls_params ls;             /* plain mode only: ls.rate > 0 makes the search
+                                    Lamarckian (Solis-Wets on the selected
+                                    individuals of every generation, generation 0
+                                    included; the refined genotype and score
+                                    replace the individual before the next
+                                    generation's selection); rate 0 = no local
+                                    search                                      */
+  float *trace_ls;               /* optional device [generations][n_ligands*pop]
+                                    [2 + 2 ls.max_its]: for each refined
+                                    individual its score before refinement, the
+                                    iterations run, then per iteration the
+                                    scores of the probes x + xi and x - xi (NaN
+                                    when not evaluated); rows of individuals not
+                                    refined are not written                     */
 } dock_search_params;
 
 #define DOCK_MODE_PLAIN 0
@@ -205,7 +248,8 @@ typedef struct {
   double best_fp64[DOCK_N_BEST]; /* the same poses rescored in FP64               */
   int32_t best_index[DOCK_N_BEST];/* their index in the final population          */
   float genotype[DOCK_N_BEST][DOCK_MAX_GENES];
-  uint64_t exact_evals;          /* exact FP32 scorings done for this ligand      */
+  uint64_t exact_evals;          /* exact FP32 scorings done for this ligand
+                                    (local-search probes included)              */
   uint64_t surrogate_evals;      /* surrogate evaluations (0 in plain mode)       */
 } dock_result;
 
@@ -244,6 +288,22 @@ int dock_score(dock_pocket *pocket, dock_ligands *ligands, const int32_t *pose_l
  * pose_ligand entries outside [0, n_ligands) score NaN. Asynchronous on stream. */
 int dock_score_pairwise(dock_pocket *pocket, dock_ligands *ligands, const int32_t *pose_ligand,
                         const float *genotypes, int64_t n_poses, float *scores, void *stream);
+
+/* Solis-Wets refinement (see dock_ls_params) of caller-given poses: pose i
+ * (ligand pose_ligand[i], genotype genotypes[i], layout as for dock_score) is
+ * scored, then refined with the random-number counters of individual i of
+ * generation `generation` of a search with `seed`; the refined genotype
+ * replaces genotypes[i] (genes beyond G_l untouched) and its FP32 score is
+ * written to scores[i]. Eight lanes per pose. trace: optional device
+ * [n_poses][2 + 2 ls->max_its] as for dock_search_params.trace_ls. evals:
+ * optional device [n_poses] uint32 probes scored. A pose whose pose_ligand
+ * entry is outside [0, n_ligands) keeps its genotype and scores NaN.
+ * Asynchronous on stream.
+ * Errors: DOCK_EINVAL, DOCK_ECUDA. */
+int dock_local_search(dock_pocket *pocket, dock_ligands *ligands, const dock_ls_params *ls,
+                      uint64_t seed, uint32_t generation, const int32_t *pose_ligand,
+                      int64_t n_poses, float *genotypes, float *scores, float *trace,
+                      uint32_t *evals, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Search without device allocation                                          */

@@ -40,6 +40,15 @@ static int fail(int st, const char *fmt, ...) {
   return st;
 }
 
+// Solis-Wets settings other than the rate (dock_ls_params).
+static int check_ls_params(const dock_ls_params *ls, const char *who) {
+  if (ls->max_its < 1 || ls->max_its > DOCK_LS_MAX_ITS || ls->max_succ < 1 || ls->max_fail < 1 ||
+      !(ls->rho > 0.0f) || !std::isfinite(ls->rho) || !std::isfinite(ls->rho_lb))
+    return fail(DOCK_EINVAL, "%s: local search needs 1 <= max_its <= %d, max_succ, max_fail >= 1, "
+                             "finite rho > 0 and finite rho_lb", who, DOCK_LS_MAX_ITS);
+  return DOCK_OK;
+}
+
 #define CU(call)                                                                     \
   do {                                                                               \
     cudaError_t e_ = (call);                                                         \
@@ -659,17 +668,38 @@ struct dock_job {
 // take over SMs as the previous group's queue drains.
 struct LaunchGroup {
   int32_t L, begin, count, blocks;
+  int32_t ls_begin, ls_count, ls_blocks;  // local-search units of the group
+  int32_t ls_L, ls_apl;                   // lanes per chain, shared-memory atoms per lane
 };
 
+// With ls (Lamarckian search), each group's search launch is followed on the
+// same stream by its Solis-Wets launch over the same items (queue counter
+// 4 + group).
 static cudaError_t enqueue_search(Workspace &W, const SearchArgs &a, const std::vector<LaunchGroup> &groups,
-                                  int threads, cudaStream_t q) {
+                                  int threads, cudaStream_t q, const LsArgs *ls = nullptr) {
   cudaError_t e = cudaSuccess;
   auto one = [&](size_t i, cudaStream_t st) {
     SearchArgs b = a;
     b.items = a.items + groups[i].begin;
     b.n_items = groups[i].count;
     b.counter = a.counter + i;
-    return launch_search(b, groups[i].blocks, threads, groups[i].L, st);
+    cudaError_t r = launch_search(b, groups[i].blocks, threads, groups[i].L, st);
+    if (r != cudaSuccess || ls == nullptr) return r;
+    if (groups[i].ls_count == 0) return r;
+    LsArgs c = *ls;
+    const int64_t gl = (int64_t)a.gen * c.n_ligands;
+    c.units = ls->units + groups[i].ls_begin;
+    c.n_units = groups[i].ls_count;
+    c.counter = a.counter + 4 + i;
+    c.gen = (uint32_t)a.gen;
+    c.sel_bits = ls->sel_bits + gl * c.sel_words;
+    c.sel_count = ls->sel_count + gl;
+    c.chain_ctr = ls->chain_ctr + gl;
+    c.atoms_per_lane = groups[i].ls_apl;
+    c.geno = a.geno_next;
+    c.score = a.score_next;
+    c.best = a.best_next;
+    return launch_ls(c, groups[i].ls_blocks, threads, groups[i].ls_L, st);
   };
   if (groups.empty()) return cudaSuccess;
   if (groups.size() == 1) return one(0, q);
@@ -711,6 +741,14 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   const int forced = sp->lanes_per_pose;
   if (forced != 0 && forced != 1 && forced != 2 && forced != 4 && forced != 8)
     return fail(DOCK_EINVAL, "dock_batch: lanes_per_pose %d", forced);
+  if (!(sp->ls.rate >= 0.0f && sp->ls.rate <= 1.0f))
+    return fail(DOCK_EINVAL, "dock_batch: ls.rate out of [0, 1]");
+  const bool lamarck = sp->ls.rate > 0.0f;
+  if (lamarck && sur) return fail(DOCK_EINVAL, "dock_batch: local search needs the plain mode");
+  if (lamarck) {
+    const int st = check_ls_params(&sp->ls, "dock_batch");
+    if (st != DOCK_OK) return st;
+  }
   CU(cudaSetDevice(L->device));
   cudaStream_t s = (cudaStream_t)stream;
   const int nl = L->n_ligands, pop = sp->pop, gens = sp->generations;
@@ -764,6 +802,33 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
       groups.push_back(LaunchGroup{host_items[i].lanes, (int32_t)i, 0, 0});
     ++groups.back().count;
   }
+  // local-search units: each ligand of a group R times (R warps share its
+  // chains, about three chains per lane group), largest ligands first
+  std::vector<int32_t> host_units;
+  int ls_lanes = 0;  // lanes per chain: 0 = the search group's
+  if (const char *e = getenv("DOCK_LS_LANES")) ls_lanes = atoi(e);
+  if (ls_lanes != 0 && ls_lanes != 1 && ls_lanes != 2 && ls_lanes != 4 && ls_lanes != 8)
+    return fail(DOCK_EINVAL, "dock_batch: DOCK_LS_LANES %d", ls_lanes);
+  if (lamarck) {
+    for (LaunchGroup &gr : groups) {
+      gr.ls_L = std::max(gr.L, ls_lanes);
+      gr.ls_apl = (gr.L * cfg.atoms_per_lane + gr.ls_L - 1) / gr.ls_L;
+      const int gpw = 32 / gr.ls_L;
+      const double expect = (double)sp->ls.rate * pop;
+      const int R = std::max(1, (int)std::ceil(expect / (3.0 * gpw)));
+      gr.ls_begin = (int32_t)host_units.size();
+      int last = -1;
+      for (int i = gr.begin; i < gr.begin + gr.count; ++i) {
+        const int l = host_items[i].lig;
+        if (l == last) continue;  // items of a ligand are adjacent (same cost)
+        last = l;
+        for (int r = 0; r < R; ++r) host_units.push_back(l);
+      }
+      gr.ls_count = (int32_t)host_units.size() - gr.ls_begin;
+    }
+  } else {
+    for (LaunchGroup &gr : groups) gr.ls_begin = gr.ls_count = gr.ls_L = gr.ls_apl = 0;
+  }
   const size_t n_scores = (size_t)nl * pop;
   // workspace: grown on demand and reused by later batches on this ligand set
   if ((size_t)total_genes > W.geno_cap || !W.geno[0]) {
@@ -788,11 +853,11 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     CU(dalloc(&W.best, (size_t)gens * nl));
     W.best_cap = (size_t)gens * nl;
   }
-  if ((size_t)gens * 4 > W.gen_cap || !W.counters) {
+  if ((size_t)gens * 8 > W.gen_cap || !W.counters) {
     dfree(W.counters);
     W.gen_cap = 0;
-    CU(dalloc(&W.counters, (size_t)gens * 4));
-    W.gen_cap = (size_t)gens * 4;
+    CU(dalloc(&W.counters, (size_t)gens * 8));
+    W.gen_cap = (size_t)gens * 8;
   }
   if (groups.size() > 1 && !W.fork) {
     for (int i = 0; i < 3; ++i) {
@@ -812,13 +877,42 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     dfree(W.lig_status);
     dfree(W.results);
     W.lig_cap = 0;
+    dfree(W.ls_evals);
     CU(dalloc(&W.geno_off, (size_t)nl));
     CU(dalloc(&W.lig_status, (size_t)nl));
     CU(dalloc(&W.results, (size_t)nl));
+    CU(dalloc(&W.ls_evals, (size_t)nl));
     W.lig_cap = (size_t)nl;
   }
   if (!W.status) CU(dalloc(&W.status, 1));
   if (!W.deadline) CU(dalloc(&W.deadline, 1));
+  const int sel_words = (pop + 31) / 32;
+  if (lamarck) {
+    const size_t nb = (size_t)gens * nl * sel_words, nc = (size_t)gens * nl;
+    if (nb > W.ls_bits_cap || !W.ls_bits) {
+      dfree(W.ls_bits);
+      W.ls_bits_cap = 0;
+      CU(dalloc(&W.ls_bits, nb));
+      W.ls_bits_cap = nb;
+    }
+    if (nc > W.ls_count_cap || !W.ls_count) {
+      dfree(W.ls_count);
+      dfree(W.ls_chain);
+      W.ls_count_cap = 0;
+      CU(dalloc(&W.ls_count, nc));
+      CU(dalloc(&W.ls_chain, nc));
+      W.ls_count_cap = nc;
+    }
+    if (host_units.size() > W.ls_units_cap || !W.ls_units) {
+      dfree(W.ls_units);
+      W.ls_units_cap = 0;
+      CU(dalloc(&W.ls_units, host_units.size()));
+      W.ls_units_cap = host_units.size();
+    }
+    if (!host_units.empty())
+      CU(cudaMemcpyAsync(W.ls_units, host_units.data(), sizeof(int32_t) * host_units.size(),
+                         cudaMemcpyHostToDevice, s));
+  }
   CU(cudaMemcpyAsync(W.geno_off, goff.data(), sizeof(int64_t) * nl, cudaMemcpyHostToDevice, s));
   CU(cudaMemcpyAsync(W.items, host_items.data(), sizeof(Item) * host_items.size(),
                      cudaMemcpyHostToDevice, s));
@@ -829,6 +923,14 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     CU(search_occupancy(cfg.threads, gr.L, cfg.atoms_per_lane, &per_sm));
     if (per_sm < 1) return fail(DOCK_EINVAL, "dock_batch: launch shape does not fit an SM");
     gr.blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, gr.count));
+    gr.ls_blocks = 0;
+    if (lamarck && gr.ls_count > 0) {
+      // one warp per unit
+      CU(ls_occupancy(cfg.threads, gr.ls_L, gr.ls_apl, &per_sm));
+      if (per_sm < 1) return fail(DOCK_EINVAL, "dock_batch: launch shape does not fit an SM");
+      const int64_t need = (gr.ls_count + cfg.threads / 32 - 1) / (cfg.threads / 32);
+      gr.ls_blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, need));
+    }
   }
 
   dock_job *J = new dock_job();
@@ -865,6 +967,38 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   A.status = W.status;
   A.lig_status = W.lig_status;
   A.deadline = sp->timeout_ns ? W.deadline : nullptr;
+
+  LsArgs LA{};
+  if (lamarck) {
+    LA.ligs = L->d_info;
+    LA.atoms = L->d_atoms;
+    LA.types = L->d_types;
+    LA.pair_rec = L->d_pair_rec;
+    LA.tors = L->d_tors;
+    LA.moves = L->d_moves;
+    LA.grid = grid_view(P);
+    LA.cx = P->center[0];
+    LA.cy = P->center[1];
+    LA.cz = P->center[2];
+    LA.atoms_per_lane = cfg.atoms_per_lane;
+    LA.max_its = sp->ls.max_its;
+    LA.max_succ = sp->ls.max_succ;
+    LA.max_fail = sp->ls.max_fail;
+    LA.rho = sp->ls.rho;
+    LA.rho_lb = sp->ls.rho_lb;
+    LA.seed = sp->seed;
+    LA.units = W.ls_units;
+    LA.sel_bits = W.ls_bits;
+    LA.sel_count = W.ls_count;
+    LA.chain_ctr = W.ls_chain;
+    LA.sel_words = sel_words;
+    LA.n_ligands = nl;
+    LA.geno_off = W.geno_off;
+    LA.pop = pop;
+    LA.evals = W.ls_evals;
+    LA.status = W.status;
+    LA.deadline = A.deadline;
+  }
 
   Fp64Args F;
   F.ligs = L->d_info;
@@ -964,7 +1098,14 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   };
 
   auto enqueue = [&](cudaStream_t q) -> int {
-    CU(cudaMemsetAsync(W.counters, 0, sizeof(uint32_t) * gens * 4, q));
+    CU(cudaMemsetAsync(W.counters, 0, sizeof(uint32_t) * gens * 8, q));
+    if (lamarck) {
+      CU(cudaMemsetAsync(W.ls_evals, 0, sizeof(unsigned long long) * (size_t)nl, q));
+      CU(cudaMemsetAsync(W.ls_chain, 0, sizeof(uint32_t) * (size_t)gens * nl, q));
+      // which individuals each generation refines (drawn up front: no data dependence)
+      CU(launch_ls_select(L->d_info, nl, pop, gens, sp->seed, prob_threshold(sp->ls.rate), W.ls_bits,
+                          W.ls_count, q));
+    }
     CU(cudaMemsetAsync(W.best, 0xFF, sizeof(unsigned long long) * (size_t)gens * nl, q));
     CU(cudaMemsetAsync(W.status, 0, sizeof(int32_t), q));
     CU(cudaMemsetAsync(W.lig_status, 0, sizeof(int32_t) * (size_t)nl, q));
@@ -972,7 +1113,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     for (int g = 0; g < gens; ++g) {
       SearchArgs a = A;
       a.gen = g;
-      a.counter = W.counters + (size_t)g * 4;
+      a.counter = W.counters + (size_t)g * 8;  // 4 search + 4 local-search queues
       a.geno_prev = W.geno[(g + 1) & 1];
       a.geno_next = W.geno[g & 1];
       a.score_prev = W.score[(g + 1) & 1];
@@ -982,17 +1123,22 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
       if (sur && g > 0) {
         const int st2 = surrogate_generation(g, q);
         if (st2 != DOCK_OK) return st2;
-      } else if (profile) {
-        cudaEvent_t e0, e1;
-        CU(cudaEventCreate(&e0));
-        CU(cudaEventCreate(&e1));
-        J->ev.push_back(e0);
-        J->ev.push_back(e1);
-        CU(cudaEventRecord(e0, q));
-        CU(enqueue_search(W, a, groups, cfg.threads, q));
-        CU(cudaEventRecord(e1, q));
       } else {
-        CU(enqueue_search(W, a, groups, cfg.threads, q));
+        LsArgs la = LA;
+        if (lamarck && sp->trace_ls)
+          la.trace = sp->trace_ls + (size_t)g * n_scores * (size_t)(2 + 2 * sp->ls.max_its);
+        if (profile) {
+          cudaEvent_t e0, e1;
+          CU(cudaEventCreate(&e0));
+          CU(cudaEventCreate(&e1));
+          J->ev.push_back(e0);
+          J->ev.push_back(e1);
+          CU(cudaEventRecord(e0, q));
+          CU(enqueue_search(W, a, groups, cfg.threads, q, lamarck ? &la : nullptr));
+          CU(cudaEventRecord(e1, q));
+        } else {
+          CU(enqueue_search(W, a, groups, cfg.threads, q, lamarck ? &la : nullptr));
+        }
       }
       if (sp->trace_genotypes && total_genes)
         CU(cudaMemcpyAsync(sp->trace_genotypes + (size_t)g * total_genes, W.geno[g & 1],
@@ -1004,7 +1150,8 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     CU(launch_finalize_impl(F, L->d_centroid, nl, pop, W.geno_off, W.geno[(gens - 1) & 1],
                             W.score[(gens - 1) & 1], W.lig_status, W.status,
                             sur ? (uint64_t)pop + (uint64_t)(gens - 1) * K : (uint64_t)pop * gens,
-                            sur ? (uint64_t)(gens - 1) * C : 0, P->ox, P->oy, P->oz, W.results, q));
+                            sur ? (uint64_t)(gens - 1) * C : 0, lamarck ? W.ls_evals : nullptr,
+                            P->ox, P->oy, P->oz, W.results, q));
     return DOCK_OK;
   };
 
@@ -1022,7 +1169,10 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     put(&cfg, sizeof cfg);
     put(&sp->trace_genotypes, sizeof(void *));
     put(&sp->trace_scores, sizeof(void *));
-    const void *bufs[6] = {W.geno[0], W.geno[1], W.score[0], W.score[1], W.best, W.results};
+    put(&sp->ls, sizeof sp->ls);
+    put(&sp->trace_ls, sizeof(void *));
+    const void *bufs[11] = {W.geno[0], W.geno[1], W.score[0], W.score[1], W.best, W.results,
+                            W.ls_evals, W.ls_bits, W.ls_count, W.ls_chain, W.ls_units};
     put(bufs, sizeof bufs);
     if (!W.graph || key != W.graph_key) {
       if (W.graph) {
@@ -1152,6 +1302,58 @@ extern "C" int dock_score(dock_pocket *P, dock_ligands *L, const int32_t *pose_l
   A.lanes = 8;
   A.atoms_per_lane = DOCK_MAX_ATOMS / 8;
   CU(launch_score(A, s));
+  return DOCK_OK;
+}
+
+extern "C" int dock_local_search(dock_pocket *P, dock_ligands *L, const dock_ls_params *ls,
+                                 uint64_t seed, uint32_t generation, const int32_t *pose_ligand,
+                                 int64_t n_poses, float *genos, float *scores, float *trace,
+                                 uint32_t *evals, void *stream) {
+  if (!P || !L || !ls) return fail(DOCK_EINVAL, "dock_local_search: NULL argument");
+  if (n_poses < 0) return fail(DOCK_EINVAL, "dock_local_search: n_poses < 0");
+  const int st = check_ls_params(ls, "dock_local_search");
+  if (st != DOCK_OK) return st;
+  if (n_poses > 0xffffffffll) return fail(DOCK_EINVAL, "dock_local_search: n_poses >= 2^32");
+  if (n_poses == 0) return DOCK_OK;
+  if (!pose_ligand || !genos || !scores)
+    return fail(DOCK_EINVAL, "dock_local_search: NULL device buffer");
+  CU(cudaSetDevice(L->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  LsArgs A{};
+  A.ligs = L->d_info;
+  A.atoms = L->d_atoms;
+  A.types = L->d_types;
+  A.pair_rec = L->d_pair_rec;
+  A.tors = L->d_tors;
+  A.moves = L->d_moves;
+  A.grid = grid_view(P);
+  A.cx = P->center[0];
+  A.cy = P->center[1];
+  A.cz = P->center[2];
+  A.atoms_per_lane = DOCK_MAX_ATOMS / 8;
+  A.max_its = ls->max_its;
+  A.max_succ = ls->max_succ;
+  A.max_fail = ls->max_fail;
+  A.rho = ls->rho;
+  A.rho_lb = ls->rho_lb;
+  A.seed = seed;
+  A.gen = generation;
+  A.units = nullptr;
+  A.pose_ligand = pose_ligand;
+  A.n_ligands = L->n_ligands;
+  A.n_poses = n_poses;
+  A.genos = genos;
+  A.scores = scores;
+  A.pose_evals = evals;
+  A.trace = trace;
+  const int threads = 128, lanes = 8;
+  int per_sm = 0, n_sm = 0;
+  CU(ls_occupancy(threads, lanes, A.atoms_per_lane, &per_sm));
+  CU(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, L->device));
+  if (per_sm < 1) return fail(DOCK_EINVAL, "dock_local_search: launch shape does not fit an SM");
+  const int64_t need = (n_poses + threads / lanes - 1) / (threads / lanes);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, need));
+  CU(launch_ls(A, blocks, threads, lanes, s));
   return DOCK_OK;
 }
 
@@ -1297,6 +1499,8 @@ extern "C" int dock_autotune(dock_pocket *P, dock_ligands *L, const dock_search_
   q.trace_genotypes = nullptr;
   q.trace_scores = nullptr;
   q.timeout_ns = 0;
+  q.ls.rate = 0.0f;  // the launch shape of the search kernel alone
+  q.trace_ls = nullptr;
   for (int ti = 0; ti < 2; ++ti)
     for (int ai = 0; ai < 5; ++ai) {
       const int apl = kApl[ai], thr = kThreads[ti];

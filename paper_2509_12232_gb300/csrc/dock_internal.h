@@ -101,6 +101,64 @@ struct SearchArgs {
   const uint64_t *deadline;  // device globaltimer deadline, NULL = none
 };
 
+// Solis-Wets refinement (local_search.cu). Batch mode (units != nullptr):
+// after a generation's search launch; the individuals drawn for refinement
+// are the set bits of sel_bits (one bit mask of pop bits per ligand, built
+// for every generation by launch_ls_select), their number sel_count. A unit
+// is a ligand: the warp that takes it runs that ligand's chains, its lane
+// groups pulling them one by one from the ligand's chain counter (several
+// units per ligand share it). Standalone mode: pose p of genos / scores,
+// ligand pose_ligand[p], scored first.
+struct LsArgs {
+  const LigInfo *ligs;
+  const float4 *atoms;
+  const uint8_t *types;
+  const float *pair_rec;
+  const TorInfo *tors;
+  const uint8_t *moves;
+  GridView grid;
+  float cx, cy, cz;
+  int32_t atoms_per_lane;
+  int32_t max_its, max_succ, max_fail;
+  float rho, rho_lb;
+  uint64_t seed;
+  uint32_t gen;
+  // batch mode
+  const int32_t *units;           // ligand of each warp unit
+  int32_t n_units;
+  uint32_t *counter;              // unit queue counter (starts at 0)
+  const uint32_t *sel_bits;       // [n_ligands][pop / 32 rounded up] of this generation
+  const uint32_t *sel_count;      // [n_ligands]
+  uint32_t *chain_ctr;            // [n_ligands] chains taken (starts at 0)
+  int32_t sel_words;
+  const int64_t *geno_off;
+  float *geno;                    // the generation's population (CSR)
+  float *score;                   // [n_ligands][pop]
+  int32_t pop;
+  unsigned long long *best;       // [n_ligands] best key of the generation
+  unsigned long long *evals;      // [n_ligands] probes scored
+  int32_t *status;
+  const uint64_t *deadline;
+  // standalone mode
+  const int32_t *pose_ligand;
+  int32_t n_ligands;
+  int64_t n_poses;
+  float *genos;                   // [n_poses][DOCK_MAX_GENES]
+  float *scores;
+  uint32_t *pose_evals;           // optional [n_poses]
+  // optional trace rows of 2 + 2 max_its floats: batch [n_ligands * pop],
+  // standalone [n_poses]
+  float *trace;
+};
+// Selection bits and counts of generations [0, gens) (counts zeroed first):
+// bit i of ligand l, generation g is set when individual i is refined.
+cudaError_t launch_ls_select(const LigInfo *ligs, int n_ligands, int pop, int gens, uint64_t seed,
+                             uint64_t thr_ls, uint32_t *sel_bits, uint32_t *sel_count,
+                             cudaStream_t s);
+cudaError_t ls_occupancy(int threads, int L, int atoms_per_lane, int *blocks_per_sm);
+int ls_smem_bytes(int threads, int L, int atoms_per_lane);
+cudaError_t launch_ls(const LsArgs &a, int blocks, int threads, int L, cudaStream_t s);
+
 struct ScoreArgs {
   const LigInfo *ligs;
   const float4 *atoms;
@@ -190,8 +248,9 @@ cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int n_ligands, int pop,
                                  const int64_t *geno_off, const float *genos, const float *scores,
                                  const int32_t *lig_status, const int32_t *status,
-                                 uint64_t exact_evals, uint64_t surrogate_evals, double ox,
-                                 double oy, double oz, dock_result *out, cudaStream_t s);
+                                 uint64_t exact_evals, uint64_t surrogate_evals,
+                                 const unsigned long long *extra_evals, double ox, double oy,
+                                 double oz, dock_result *out, cudaStream_t s);
 cudaError_t launch_score_fp64_impl(const Fp64Args &f, const double *centroids, double ox, double oy,
                                    double oz, const int32_t *pose_ligand, int n_ligands,
                                    const float *genos, int64_t n_poses, double *out, cudaStream_t s);

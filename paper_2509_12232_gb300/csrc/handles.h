@@ -101,6 +101,12 @@ struct Workspace {
   uint64_t *deadline = nullptr;
   int32_t *lig_status = nullptr;
   dock_result *results = nullptr;
+  unsigned long long *ls_evals = nullptr;  // [n_ligands] local-search probes
+  // Lamarckian search: selection bits [gens][n_ligands][pop/32], counts and
+  // chain counters [gens][n_ligands], warp units (ligand per unit)
+  size_t ls_bits_cap = 0, ls_count_cap = 0, ls_units_cap = 0;
+  uint32_t *ls_bits = nullptr, *ls_count = nullptr, *ls_chain = nullptr;
+  int32_t *ls_units = nullptr;
   // surrogate mode: candidates, their features and predictions, kept candidates
   size_t sur_cap = 0, kept_cap = 0;
   float *cand_geno = nullptr, *pred = nullptr, *kept_geno = nullptr, *kept_score = nullptr;
@@ -128,6 +134,11 @@ struct Workspace {
     dfree(deadline);
     dfree(lig_status);
     dfree(results);
+    dfree(ls_evals);
+    dfree(ls_bits);
+    dfree(ls_count);
+    dfree(ls_chain);
+    dfree(ls_units);
     dfree(cand_geno);
     dfree(pred);
     dfree(feats);

@@ -70,6 +70,8 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
     return fail(DOCK_EINVAL, "dock_batch_noalloc: probabilities out of [0, 1]");
   if (sp->mode != DOCK_MODE_PLAIN)
     return fail(DOCK_EINVAL, "dock_batch_noalloc: only the plain search (mode 0)");
+  if (sp->ls.rate != 0.0f)
+    return fail(DOCK_EINVAL, "dock_batch_noalloc: no local search (ls.rate must be 0)");
   if (sp->lanes_per_pose != 0)
     return fail(DOCK_EINVAL, "dock_batch_noalloc: lanes_per_pose must be 0 (picked by size)");
   const int nl = L->n_ligands, pop = sp->pop, gens = sp->generations;
@@ -235,7 +237,7 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
   }
   NA_CU(launch_finalize_impl(F, L->d_centroid, nl, pop, goff, geno[(gens - 1) & 1],
                              score[(gens - 1) & 1], lig_status, status, (uint64_t)pop * gens, 0,
-                             P->ox, P->oy, P->oz, results, s));
+                             nullptr, P->ox, P->oy, P->oz, results, s));
 #undef NA_CU
   return DOCK_OK;
 }

@@ -186,6 +186,7 @@ struct FinalArgs {
   const int32_t *lig_status;
   const int32_t *status;
   uint64_t exact_evals, surrogate_evals;
+  const unsigned long long *extra_evals;  // optional [n_ligands] (local-search probes)
   dock_result *out;
 };
 
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalArgs A) {
     int st = A.lig_status ? A.lig_status[lig] : 0;
     if (*A.status != 0) st = *A.status;
     R->status = st;
-    R->exact_evals = A.exact_evals;
+    R->exact_evals = A.exact_evals + (A.extra_evals ? A.extra_evals[lig] : 0ull);
     R->surrogate_evals = A.surrogate_evals;
   }
   if (tid < DOCK_N_BEST) {
@@ -268,8 +269,9 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalArgs A) {
 cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int n_ligands, int pop,
                                  const int64_t *geno_off, const float *genos, const float *scores,
                                  const int32_t *lig_status, const int32_t *status,
-                                 uint64_t exact_evals, uint64_t surrogate_evals, double ox,
-                                 double oy, double oz, dock_result *out, cudaStream_t s) {
+                                 uint64_t exact_evals, uint64_t surrogate_evals,
+                                 const unsigned long long *extra_evals, double ox, double oy,
+                                 double oz, dock_result *out, cudaStream_t s) {
   if (n_ligands == 0) return cudaSuccess;
   FinalArgs A;
   A.f = f;
@@ -284,6 +286,7 @@ cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int
   A.status = status;
   A.exact_evals = exact_evals;
   A.surrogate_evals = surrogate_evals;
+  A.extra_evals = extra_evals;
   A.out = out;
   finalize_kernel<<<n_ligands, 256, 0, s>>>(A);
   return cudaGetLastError();

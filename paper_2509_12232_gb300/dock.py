@@ -50,13 +50,26 @@ class dock_ligand_batch(C.Structure):
                 ("tors_b", P_i16), ("ligand_id", P_u64)]
 
 
+class dock_ls_params(C.Structure):
+    _fields_ = [("rate", C.c_float), ("max_its", C.c_int32), ("max_succ", C.c_int32),
+                ("max_fail", C.c_int32), ("rho", C.c_float), ("rho_lb", C.c_float)]
+
+
+def ls_params(rate=0.06, max_its=300, max_succ=4, max_fail=4, rho=1.0, rho_lb=0.01):
+    """Solis-Wets settings (AutoDock's published defaults)."""
+    return dock_ls_params(rate, max_its, max_succ, max_fail, rho, rho_lb)
+
+
+NO_LS = (0.0, 300, 4, 4, 1.0, 0.01)
+
+
 class dock_search_params(C.Structure):
     _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("p_cross", C.c_float),
                 ("p_mut", C.c_float), ("seed", C.c_uint64), ("lanes_per_pose", C.c_int32),
                 ("use_graph", C.c_int32), ("timeout_ns", C.c_uint64),
                 ("trace_genotypes", C.c_void_p), ("trace_scores", C.c_void_p),
                 ("mode", C.c_int32), ("candidates", C.c_int32), ("keep", C.c_int32),
-                ("surrogate", C.c_void_p)]
+                ("surrogate", C.c_void_p), ("ls", dock_ls_params), ("trace_ls", C.c_void_p)]
 
 
 DOCK_TUNE_MAX = 16
@@ -121,6 +134,8 @@ def lib():
         L.dock_job_destroy.restype = None
         L.dock_score.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp, vp, C.c_int32, vp]
         L.dock_score_pairwise.argtypes = [vp, vp, vp, vp, C.c_int64, vp, vp]
+        L.dock_local_search.argtypes = [vp, vp, C.POINTER(dock_ls_params), C.c_uint64, C.c_uint32,
+                                        vp, C.c_int64, vp, vp, vp, vp, vp]
         P_i64 = C.POINTER(C.c_int64)
         L.dock_ligands_info.argtypes = [vp, P_i32, P_i64, P_i64, P_i64, P_i64, P_i64]
         L.dock_batch_noalloc.argtypes = [vp, vp, C.POINTER(dock_search_params), vp, vp]
@@ -298,14 +313,16 @@ def dock_ligands_info(ligands: Ligands) -> dict:
 def dock_batch(pocket: Pocket, ligands: Ligands, pop: int, generations: int, p_cross=0.8,
                p_mut=0.02, seed=0, lanes_per_pose=0, use_graph=1, timeout_ns=0,
                trace_genotypes=None, trace_scores=None, stream=None, surrogate=None,
-               candidates=0, keep=0) -> Job:
+               candidates=0, keep=0, ls=None, trace_ls=None) -> Job:
     """Plain search, or the surrogate pre-screened search when `surrogate` is
     given (`candidates` children per ligand and generation, `keep` of them
-    scored exactly)."""
+    scored exactly). `ls` (a dock_ls_params, e.g. ls_params()) with a rate
+    > 0 makes the plain search Lamarckian (Solis-Wets refinement)."""
     mode = DOCK_MODE_SURROGATE if surrogate is not None else DOCK_MODE_PLAIN
     sp = dock_search_params(pop, generations, p_cross, p_mut, seed, lanes_per_pose, use_graph,
                             timeout_ns, _dptr(trace_genotypes), _dptr(trace_scores), mode,
-                            candidates, keep, surrogate.handle if surrogate is not None else None)
+                            candidates, keep, surrogate.handle if surrogate is not None else None,
+                            ls if ls is not None else dock_ls_params(*NO_LS), _dptr(trace_ls))
     h = C.c_void_p()
     check(lib().dock_batch(pocket.handle, ligands.handle, C.byref(sp), _stream(stream), C.byref(h)))
     return Job(h, ligands.n_ligands, keep=(pocket, ligands, surrogate))
@@ -320,7 +337,7 @@ def dock_batch_noalloc(pocket: Pocket, ligands: Ligands, results, pop: int, gene
     Asynchronous on stream."""
     sp = dock_search_params(pop, generations, p_cross, p_mut, seed, 0, 0, timeout_ns,
                             _dptr(trace_genotypes), _dptr(trace_scores), DOCK_MODE_PLAIN, 0, 0,
-                            None)
+                            None, dock_ls_params(*NO_LS), None)
     check(lib().dock_batch_noalloc(pocket.handle, ligands.handle, C.byref(sp), _dptr(results),
                                    _stream(stream)))
 
@@ -364,6 +381,18 @@ def dock_score_pairwise(pocket: Pocket, ligands: Ligands, pose_ligand, genotypes
     n = int(pose_ligand.shape[0]) if hasattr(pose_ligand, "shape") else int(genotypes.shape[0])
     check(lib().dock_score_pairwise(pocket.handle, ligands.handle, _dptr(pose_ligand),
                                     _dptr(genotypes), n, _dptr(scores), _stream(stream)))
+
+
+def dock_local_search(pocket: Pocket, ligands: Ligands, ls, seed: int, generation: int,
+                      pose_ligand, genotypes, scores, trace=None, evals=None, stream=None):
+    """Solis-Wets refinement of caller-given poses: genotypes ([n, 23] float32,
+    refined in place) of ligands pose_ligand ([n] int32); scores ([n] float32)
+    receive the refined scores; trace ([n, 2 + 2 max_its] float32) and evals
+    ([n] int32/uint32) are optional. Device tensors or pointers; asynchronous."""
+    n = int(pose_ligand.shape[0]) if hasattr(pose_ligand, "shape") else int(genotypes.shape[0])
+    check(lib().dock_local_search(pocket.handle, ligands.handle, C.byref(ls), seed, generation,
+                                  _dptr(pose_ligand), n, _dptr(genotypes), _dptr(scores),
+                                  _dptr(trace), _dptr(evals), _stream(stream)))
 
 
 def version() -> str:
@@ -450,7 +479,7 @@ def dock_autotune(pocket: Pocket, ligands: Ligands, pop: int, generations: int, 
     """Measure the search kernel's launch shapes on this ligand set and keep
     the fastest for later dock_batch calls; returns the measured table."""
     sp = dock_search_params(pop, generations, 0.8, 0.02, seed, 0, 0, 0, None, None,
-                            DOCK_MODE_PLAIN, 0, 0, None)
+                            DOCK_MODE_PLAIN, 0, 0, None, dock_ls_params(*NO_LS), None)
     t = dock_tune_table()
     check(lib().dock_autotune(pocket.handle, ligands.handle, C.byref(sp), _stream(stream), C.byref(t)))
     rows = [dict(threads=t.threads[i], atoms_per_lane=t.atoms_per_lane[i],

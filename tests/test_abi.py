@@ -59,6 +59,7 @@ def test_struct_layouts_match_header(tmp_path):
         "dock_pocket_desc": dock.dock_pocket_desc,
         "dock_ligand_batch": dock.dock_ligand_batch,
         "dock_search_params": dock.dock_search_params,
+        "dock_ls_params": dock.dock_ls_params,
         "dock_result": dock.dock_result,
         "dock_train_params": dock.dock_train_params,
         "dock_tune_table": dock.dock_tune_table,
