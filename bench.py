@@ -415,13 +415,147 @@ def run_grid(args, rank, world):
     return 0
 
 
+def run_pairwise(args, rank, world):
+    """Pairwise inter-energy scoring without maps (dock_score_pairwise): every
+    protein atom within 8 A of each ligand atom enters through the pair
+    terms, plus the intra-energy. c2 pocket and ligand set, 256 random poses
+    per ligand (256,000 poses per step) with translations in the cavity."""
+    import torch
+    from paper_2509_12232_gb300 import build, dock, synth
+    local = env_rank()[2]
+    torch.cuda.set_device(local)
+    build.build()
+    dock.lib()
+    stream = torch.cuda.current_stream()
+    pk, ligs, w = synth.make_workload(WORKLOAD, pocket=True)
+    pocket = dock.dock_create_pocket(pk.x, pk.y, pk.z, pk.q, pk.type, pk.center, pk.radius,
+                                     pk.spacing, synth.TYPE_PARAMS, stream=stream)
+    largs = (ligs.atom_off, ligs.x, ligs.y, ligs.z, ligs.q, ligs.type, ligs.parent, ligs.tors_off,
+             ligs.tors_b, ligs.ligand_id)
+    gl = dock.dock_load_ligands(pocket, *largs, stream=stream)
+    info = dock.dock_ligands_info(gl)
+    per = 256
+    nl = ligs.n_ligands
+    n = nl * per
+    rng = np.random.default_rng(7)
+    g = np.zeros((n, 23), np.float32)
+    g[:, :3] = rng.uniform(-0.5, 0.5, (n, 3)) * pk.radius
+    q = rng.normal(size=(n, 4))
+    g[:, 3:7] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    g[:, 7:] = rng.uniform(-np.pi, np.pi, (n, 16))
+    pl = np.repeat(np.arange(nl, dtype=np.int32), per)
+    dg = torch.from_numpy(g).cuda()
+    dpl = torch.from_numpy(pl).cuda()
+    sc = torch.zeros(n, dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        dock.dock_score_pairwise(pocket, gl, dpl, dg, sc, stream=stream)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        ev[i][0].record(stream)
+        dock.dock_score_pairwise(pocket, gl, dpl, dg, sc, stream=stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms_step = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    value = n / (ms_step / 1000.0)
+    # algorithmic work: the pose and intra pairs as in the grid scorer, plus every
+    # ligand-protein pair within the cutoff (34 flops, 4 MUFU each); the pairs
+    # within the cutoff are counted on 1,024 sampled poses (posed by dock_score)
+    idx = np.linspace(0, n - 1, 1024).astype(np.int64)
+    sub_g, sub_l = dg[idx].contiguous(), dpl[idx].contiguous()
+    coords = torch.zeros((len(idx), 128, 3), dtype=torch.float32, device="cuda")
+    tmp = torch.zeros(len(idx), dtype=torch.float32, device="cuda")
+    dock.dock_score(pocket, gl, sub_l, sub_g, tmp, coords=coords, stream=stream)
+    torch.cuda.synchronize()
+    prot = torch.from_numpy(np.stack([pk.x, pk.y, pk.z], 1).astype(np.float32)).cuda()
+    na = np.diff(ligs.atom_off)
+    inter_pairs = 0
+    for j, p in enumerate(idx.tolist()):
+        x = coords[j, :int(na[pl[p]])]
+        inter_pairs += int((torch.cdist(x, prot) < 8.0).sum().item())
+    inter_per_pose = inter_pairs / len(idx)
+    flops_pose, mufu_pose = work_per_pose(info, nl)
+    base = (flops_pose - info["n_atoms"] * FLOP_INTER_PER_ATOM) / nl
+    flops = n * (base + inter_per_pose * FLOP_PER_PAIR)
+    mufu = n * (mufu_pose / nl + inter_per_pose * MUFU_PER_PAIR)
+    peaks, peak_kind = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    mufu_peak = n_sm * 16 * sm_mhz * 1e6 / 1e12
+    ach = flops / (ms_step / 1000.0) / 1e12
+    achm = mufu / (ms_step / 1000.0) / 1e12
+    # end to end from host genotypes: upload, score, download
+    hg = torch.from_numpy(g).pin_memory()
+    hs = torch.zeros(n, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dg.copy_(hg, non_blocking=True)
+        dock.dock_score_pairwise(pocket, gl, dpl, dg, sc, stream=stream)
+        hs.copy_(sc, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    line = {"metric": "poses/s (pairwise inter-energy + intra-energy scoring, no grid maps)",
+            "value": round(value, 1), "unit": "poses/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "c2 pocket (4,000 atoms) and ligand set, 256 random poses per "
+                                   "ligand (%d poses)" % n,
+                       "l2": "flushed between steps (256 MiB write)",
+                       "protein_pairs_within_cutoff_per_pose": round(inter_per_pose, 1)},
+            "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2),
+                         "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
+                         "kernel": "score_pairwise_kernel",
+                         "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
+                         "mufu": {"achieved": round(achm, 4), "peak": round(mufu_peak, 4),
+                                  "unit": "Tops/s", "frac": round(achm / mufu_peak, 4)}},
+            "e2e": {"value": round(n / e2e_s, 1), "unit": "poses/s",
+                    "h2d_bytes_per_step": int(g.nbytes), "d2h_bytes_per_step": int(n * 4)},
+            "gpu_launches": args.steps, "clocks": clk}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = pairwise_cpu_baseline(ligs, pk, g, pl, args.cpu_baseline_seconds)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def pairwise_cpu_baseline(ligs, pk, g, pl, budget_s):
+    """The oracle's pairwise score (FP64 C, one core) on the first poses of
+    the same set, about budget_s seconds."""
+    from oracle import oracle as o
+    from paper_2509_12232_gb300 import synth
+    P = o.Params(synth.TYPE_PARAMS)
+    pks = o.pocket_from(pk)
+    lig_cache = {}
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and done < len(pl):
+        l = int(pl[done])
+        if l not in lig_cache:
+            lig_cache[l] = o.Ligand(**ligs.ligand(l))
+        lig = lig_cache[l]
+        xyz = o.pose(lig, g[done, :lig.n_genes], pk.center)
+        o.inter_pairwise(lig, P, pks, xyz)
+        o.intra(lig, P, xyz)
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "poses/s", "cores": 1, "kind": "oracle",
+            "sample": "first %d poses of the same set, %.1f s" % (done, dt)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="plain", choices=["plain", "lga", "surrogate", "mlp", "grid"],
+    ap.add_argument("--mode", default="plain",
+                    choices=["plain", "lga", "surrogate", "mlp", "grid", "pairwise"],
                     help="lga: the Lamarckian search (Solis-Wets); surrogate: pre-screened vs "
                          "plain comparison; mlp: the surrogate network's forward pass and training "
                          "step alone; grid: the pocket grid build (each its own JSON line)")
@@ -444,6 +578,8 @@ def main():
         return run_mlp(args, rank, world)
     if args.mode == "grid":
         return run_grid(args, rank, world)
+    if args.mode == "pairwise":
+        return run_pairwise(args, rank, world)
 
     import torch
     import torch.distributed as dist

@@ -805,9 +805,12 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   // local-search units: each ligand of a group R times (R warps share its
   // chains, about three chains per lane group), largest ligands first
   std::vector<int32_t> host_units;
-  int ls_lanes = 0;  // lanes per chain: 0 = the search group's
+  // lanes per chain (at least the search group's): more lanes shorten a
+  // chain's sequence of probes, the longest of which bounds a generation
+  int ls_lanes = 16;
   if (const char *e = getenv("DOCK_LS_LANES")) ls_lanes = atoi(e);
-  if (ls_lanes != 0 && ls_lanes != 1 && ls_lanes != 2 && ls_lanes != 4 && ls_lanes != 8)
+  if (ls_lanes != 0 && ls_lanes != 1 && ls_lanes != 2 && ls_lanes != 4 && ls_lanes != 8 &&
+      ls_lanes != 16 && ls_lanes != 32)
     return fail(DOCK_EINVAL, "dock_batch: DOCK_LS_LANES %d", ls_lanes);
   if (lamarck) {
     for (LaunchGroup &gr : groups) {

@@ -29,10 +29,13 @@ struct Words8 {
   uint32_t w[8];
 };
 
+// ROLLED: the ten rounds as a loop (the same values, less code where many
+// call sites are inlined).
+template <bool ROLLED = false>
 __device__ __forceinline__ Words8 rng_words(uint64_t seed, uint64_t lig, uint32_t gen,
                                             uint32_t ind, uint32_t slot) {
   uint64_t c0 = slot, c1 = ind, c2 = gen, c3 = lig, k0 = seed, k1 = 0;
-#pragma unroll
+#pragma unroll (ROLLED ? 1 : 10)
   for (int r = 0; r < 10; ++r) {
     const uint64_t m0 = 0xD2E7470EE14C6C93ULL, m1 = 0xCA5A826395121157ULL;
     uint64_t hi0 = __umul64hi(m0, c0), lo0 = m0 * c0;
@@ -55,10 +58,11 @@ __device__ __forceinline__ Words8 rng_words(uint64_t seed, uint64_t lig, uint32_
 
 // Irwin-Hall normal from the first 12 words of slots (s, s+1):
 // (sum of 12 top-24-bit words - 6 * 2^24) * 2^-24, converted round-to-nearest.
+template <bool ROLLED = false>
 __device__ __forceinline__ float rng_normal(uint64_t seed, uint64_t lig, uint32_t gen,
                                             uint32_t ind, uint32_t s) {
-  Words8 a = rng_words(seed, lig, gen, ind, s);
-  Words8 b = rng_words(seed, lig, gen, ind, s + 1);
+  Words8 a = rng_words<ROLLED>(seed, lig, gen, ind, s);
+  Words8 b = rng_words<ROLLED>(seed, lig, gen, ind, s + 1);
   int64_t S = 0;
 #pragma unroll
   for (int i = 0; i < 8; ++i) S += a.w[i] >> 8;

@@ -73,7 +73,8 @@ __device__ __forceinline__ void ls_turn(const LsArgs &A, const LigView &V, int G
   if (c.phase == 1) {
     const uint32_t gen = A.gen | kLsGenBit;
     for (int e = lane; e < G; e += L) {
-      const float z = rng_normal(A.seed, lig_id, gen, ind, 64u * (uint32_t)c.t + 2u * (uint32_t)e);
+      const float z =
+          rng_normal<true>(A.seed, lig_id, gen, ind, 64u * (uint32_t)c.t + 2u * (uint32_t)e);
       const float xi = __fadd_rn(B[e], __fmul_rn(__fmul_rn(c.rho, ls_sigma(e)), z));
       XI[e] = xi;
       Y[e] = wrap_gene(__fadd_rn(X[e], xi), e);
@@ -313,6 +314,8 @@ cudaError_t ls_occupancy(int threads, int L, int atoms_per_lane, int *blocks_per
     case 2: return ls_occupancy_l<2>(threads, smem, blocks_per_sm);
     case 4: return ls_occupancy_l<4>(threads, smem, blocks_per_sm);
     case 8: return ls_occupancy_l<8>(threads, smem, blocks_per_sm);
+    case 16: return ls_occupancy_l<16>(threads, smem, blocks_per_sm);
+    case 32: return ls_occupancy_l<32>(threads, smem, blocks_per_sm);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -337,6 +340,8 @@ cudaError_t launch_ls(const LsArgs &a, int blocks, int threads, int L, cudaStrea
     case 2: ls_kernel<2><<<blocks, threads, smem, s>>>(a); break;
     case 4: ls_kernel<4><<<blocks, threads, smem, s>>>(a); break;
     case 8: ls_kernel<8><<<blocks, threads, smem, s>>>(a); break;
+    case 16: ls_kernel<16><<<blocks, threads, smem, s>>>(a); break;
+    case 32: ls_kernel<32><<<blocks, threads, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

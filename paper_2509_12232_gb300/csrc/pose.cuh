@@ -103,16 +103,21 @@ __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], con
   }
   __syncwarp(gmask);
   // ---- torsions root to leaf, each about the current bond axis ------------
-#pragma unroll
-  for (int j = 0; j < DOCK_MAX_TORSIONS; ++j) {
-    if (j < V.k) {
+  // (a rolled loop keeps the code small; the angle is picked from the
+  // register genotype by selects, not by a dynamic index)
+#pragma unroll 1
+  for (int j = 0; j < V.k; ++j) {
+    {
       const TorInfo T = V.tors[j];
       const float4 pa = slot[T.a], pb = slot[T.b];
       float ux = pb.x - pa.x, uy = pb.y - pa.y, uz = pb.z - pa.z;
       const float il = rsqrt_ftz(ux * ux + uy * uy + uz * uz);
       ux *= il; uy *= il; uz *= il;
+      float theta = g[7];
+#pragma unroll
+      for (int q = 1; q < DOCK_MAX_TORSIONS; ++q) theta = j == q ? g[7 + q] : theta;
       float s, c;
-      __sincosf(g[7 + j], &s, &c);
+      __sincosf(theta, &s, &c);
       const float oc = 1.f - c;
       const float m00 = c + ux * ux * oc, m01 = ux * uy * oc - uz * s, m02 = ux * uz * oc + uy * s;
       const float m10 = uy * ux * oc + uz * s, m11 = c + uy * uy * oc, m12 = uy * uz * oc - ux * s;
