@@ -161,8 +161,9 @@ typedef struct dock_surrogate dock_surrogate;
  * mutation does and renormalise the quaternion; NaN scores count as +inf;
  * genotype arithmetic is correctly rounded FP32 (bit-exact with the CPU
  * oracle given the same scores). Random numbers: the GA's Philox counters
- * with the generation word OR 2^31 (normals of iteration t, gene e from slots
- * 64 t + 2 e, +1; the selection draw is word 0 of slot 63). */
+ * with the generation word OR 2^31 (the normal of iteration t, gene e is the
+ * Irwin-Hall sum of the twelve 16-bit halves of words 0-5 of slot 64 t + e;
+ * the selection draw is word 0 of slot 63). */
 typedef struct {
   float rate;                    /* dock_batch: probability that an individual
                                     is refined after scoring, every generation

@@ -666,9 +666,11 @@ void orc_ga_children(int k, int P, int n, float p_cross, float p_mut, uint64_t s
 /* A probe wraps torsions as the mutation does and renormalises the         */
 /* quaternion. NaN scores count as +inf. Genotype arithmetic is correctly    */
 /* rounded FP32 as in the GA. Random numbers: the GA's Philox counters with  */
-/* the generation word OR 2^31; the normal of gene e at iteration t uses     */
-/* slots 64 t + 2 e and 64 t + 2 e + 1; whether an individual is refined in  */
-/* a generation is decided by word 0 of slot 63 against the rate.            */
+/* the generation word OR 2^31. The normal of gene e at iteration t is the   */
+/* Irwin-Hall sum of the twelve 16-bit halves of words 0-5 of slot 64 t + e,  */
+/* (sum - 6 * 2^16) * 2^-16 (exact in float, variance 1); whether an         */
+/* individual is refined in a generation is decided by word 0 of slot 63     */
+/* against the rate.                                                         */
 /* ======================================================================= */
 typedef struct {
   float rate;                    /* probability an individual is refined      */
@@ -688,6 +690,15 @@ int orc_ls_selected(float rate, uint64_t seed, uint64_t lig, uint32_t gen, uint3
 }
 
 static float gene_sigma(int e) { return e < 3 ? 1.0f : (e < 7 ? 0.1f : 0.5f); }
+
+/* the local search's normal of gene e at iteration t (see above) */
+float orc_ls_normal(uint64_t seed, uint64_t lig, uint32_t gen, uint32_t ind, uint32_t t, int e) {
+  uint32_t w[8];
+  orc_rng_words(seed, lig, gen | LS_GEN_BIT, ind, 64u * t + (uint32_t)e, w);
+  int32_t S = 0;
+  for (int k = 0; k < 6; ++k) S += (int32_t)(w[k] & 0xffffu) + (int32_t)(w[k] >> 16);
+  return (float)(S - 6 * 65536) * 0x1p-16f;
+}
 
 static float nan_to_inf(float v) { return v != v ? INFINITY : v; }
 
@@ -714,7 +725,7 @@ int orc_solis_wets(int k, const orc_ls_params *p, uint64_t seed, uint64_t lig, u
   for (int e = 0; e < G; ++e) b[e] = 0.0f;
   for (t = 0; t < p->max_its && !(rho < p->rho_lb); ++t) {
     for (int e = 0; e < G; ++e) {
-      float z = orc_normal(seed, lig, gen | LS_GEN_BIT, ind, 64u * (uint32_t)t + 2u * (uint32_t)e);
+      float z = orc_ls_normal(seed, lig, gen, ind, (uint32_t)t, e);
       float step = (rho * gene_sigma(e)) * z;
       xi[e] = b[e] + step;
     }

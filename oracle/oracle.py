@@ -147,6 +147,8 @@ def _declare(L):
     L.orc_ga_children.restype = None
     L.orc_ga_children.argtypes = [C.c_int, C.c_int, C.c_int, C.c_float, C.c_float, C.c_uint64,
                                   C.c_uint64, C.c_uint32, P_f, P_f, P_f]
+    L.orc_ls_normal.restype = C.c_float
+    L.orc_ls_normal.argtypes = [C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int]
     L.orc_ls_selected.restype = C.c_int
     L.orc_ls_selected.argtypes = [C.c_float, C.c_uint64, C.c_uint64, C.c_uint32, C.c_uint32]
     L.orc_solis_wets.restype = C.c_int
@@ -427,6 +429,11 @@ class LsParams:
 def ls_selected(rate: float, seed: int, lig_id: int, gen: int, ind: int) -> bool:
     """Whether individual `ind` of generation `gen` is refined (Solis-Wets)."""
     return bool(lib().orc_ls_selected(rate, seed, lig_id, gen, ind))
+
+
+def ls_normal(seed: int, lig_id: int, gen: int, ind: int, t: int, e: int) -> float:
+    """The local search's N(0, 1) draw for gene e at iteration t."""
+    return lib().orc_ls_normal(seed, lig_id, gen, ind, t, e)
 
 
 def solis_wets(k: int, ls: LsParams, seed: int, lig_id: int, gen: int, ind: int, x0, f0,

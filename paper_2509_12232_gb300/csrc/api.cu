@@ -809,6 +809,10 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   // chain's sequence of probes, the longest of which bounds a generation
   int ls_lanes = 16;
   if (const char *e = getenv("DOCK_LS_LANES")) ls_lanes = atoi(e);
+  // chains a lane group is expected to run one after another (sets how many
+  // warps share a ligand's chains)
+  double ls_chains = 2.0;
+  if (const char *e = getenv("DOCK_LS_CHAINS")) ls_chains = std::max(0.25, atof(e));
   if (ls_lanes != 0 && ls_lanes != 1 && ls_lanes != 2 && ls_lanes != 4 && ls_lanes != 8 &&
       ls_lanes != 16 && ls_lanes != 32)
     return fail(DOCK_EINVAL, "dock_batch: DOCK_LS_LANES %d", ls_lanes);
@@ -818,7 +822,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
       gr.ls_apl = (gr.L * cfg.atoms_per_lane + gr.ls_L - 1) / gr.ls_L;
       const int gpw = 32 / gr.ls_L;
       const double expect = (double)sp->ls.rate * pop;
-      const int R = std::max(1, (int)std::ceil(expect / (3.0 * gpw)));
+      const int R = std::max(1, (int)std::ceil(expect / (ls_chains * gpw)));
       gr.ls_begin = (int32_t)host_units.size();
       int last = -1;
       for (int i = gr.begin; i < gr.begin + gr.count; ++i) {

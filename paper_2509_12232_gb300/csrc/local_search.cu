@@ -23,6 +23,17 @@ constexpr int kGeneStride = 24;              // floats per gene vector in shared
 
 __device__ __forceinline__ float ls_sigma(int e) { return e < 3 ? 1.0f : (e < 7 ? 0.1f : 0.5f); }
 
+// N(0, 1) draw of gene e at iteration t: Irwin-Hall sum of the twelve 16-bit
+// halves of words 0-5 of one Philox block (slot 64 t + e), exact in float.
+__device__ __forceinline__ float ls_normal(uint64_t seed, uint64_t lig_id, uint32_t gen,
+                                           uint32_t ind, uint32_t t, int e) {
+  const Words8 w = rng_words<true>(seed, lig_id, gen, ind, 64u * t + (uint32_t)e);
+  int32_t S = 0;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) S += (int32_t)(w.w[k] & 0xffffu) + (int32_t)(w.w[k] >> 16);
+  return __fmul_rn((float)(S - 6 * 65536), 0x1p-16f);
+}
+
 __device__ __forceinline__ float nan_to_inf(float v) {
   return v != v ? __int_as_float(0x7f800000) : v;
 }
@@ -73,8 +84,7 @@ __device__ __forceinline__ void ls_turn(const LsArgs &A, const LigView &V, int G
   if (c.phase == 1) {
     const uint32_t gen = A.gen | kLsGenBit;
     for (int e = lane; e < G; e += L) {
-      const float z =
-          rng_normal<true>(A.seed, lig_id, gen, ind, 64u * (uint32_t)c.t + 2u * (uint32_t)e);
+      const float z = ls_normal(A.seed, lig_id, gen, ind, (uint32_t)c.t, e);
       const float xi = __fadd_rn(B[e], __fmul_rn(__fmul_rn(c.rho, ls_sigma(e)), z));
       XI[e] = xi;
       Y[e] = wrap_gene(__fadd_rn(X[e], xi), e);

@@ -231,3 +231,17 @@ def test_bias_recursion_autocorrelation(direction):
     corr = float(np.corrcoef(a[0], a[1])[0, 1])
     want = 0.44 if direction == "forward" else -0.2
     assert abs(corr - want) < 0.05, corr
+
+
+def test_local_search_normal_is_irwin_hall_12():
+    # twelve 16-bit uniforms: mean 0, variance 1 (to 2^-32), excess kurtosis -6/60,
+    # support [-6, 6); values are multiples of 2^-16
+    z = np.array([o.ls_normal(5, 9, g, i, t, e) for g in range(2) for i in range(50)
+                  for t in range(10) for e in range(20)])
+    assert abs(z.mean()) < 5 / math.sqrt(len(z))
+    assert abs(z.var() - 1.0) < 0.03
+    kurt = np.mean((z - z.mean()) ** 4) / z.var() ** 2
+    assert abs(kurt - 2.9) < 0.08
+    assert np.all(np.abs(z) < 6) and np.all(np.round(z * 65536) == z * 65536)
+    # distinct genes, iterations and individuals draw distinct values
+    assert len(np.unique(z)) > 0.95 * len(z)
