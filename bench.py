@@ -13,6 +13,9 @@ its host-side preparation, the search, and the D2H copy of the results).
 Under torchrun each rank docks its own shard of the same size (weak scaling,
 no collective on the data path).
 
+--mode nogrid runs the same plain search with the pairwise inter-energy
+(every protein atom within 8 A, no maps) and prints its own line.
+
 --mode lga runs the same workload as the Lamarckian variant (Solis-Wets
 refinement of 6% of each generation, at most 300 iterations: AutoDock's
 settings) and prints its own line.
@@ -41,6 +44,8 @@ WORKLOAD = "c2"
 METRIC = "ligands/s (plain exact GA docking: 1,024 poses x 50 generations per ligand)"
 DESCR = ("1,000 synthetic ligands (10-60 heavy atoms, 0-12 torsions) vs a 4,000-atom pocket "
          "(16 A cavity, 86^3 x 7 grid maps), 1,024 poses x 50 generations, FP64 best-8 rescoring")
+METRIC_NOGRID = ("ligands/s (plain exact GA docking without grid maps: pairwise inter-energy, "
+                 "1,024 poses x 50 generations per ligand)")
 METRIC_LGA = ("ligands/s (Lamarckian GA docking: 1,024 poses x 50 generations per ligand, "
               "Solis-Wets on 6% of each generation, up to 300 iterations)")
 LS_DEFAULTS = dict(rate=0.06, max_its=300, max_succ=4, max_fail=4, rho=1.0, rho_lb=0.01)
@@ -157,6 +162,38 @@ def work_per_pose(info, n_lig):
              info["n_pairs"] * FLOP_PER_PAIR)
     mufu = n_lig * MUFU_PER_POSE + info["n_torsions"] * MUFU_PER_TORSION + info["n_pairs"] * MUFU_PER_PAIR
     return flops, mufu
+
+
+def inter_pairs_per_pose(dock, torch, pocket, gl, pk, ligs, w, trace, stream, n=512):
+    """Mean number of ligand-protein pairs within 8 A per scored pose of the
+    no-grid search: posed coordinates (dock_score) of n poses sampled from
+    generation 0 and n from the last generation of a traced search, averaged
+    (the count grows as the search moves poses against the protein)."""
+    goff = gl.geno_offsets(w.pop)
+    tot = int(goff[-1])
+    na = np.diff(ligs.atom_off)
+    prot = torch.from_numpy(np.stack([pk.x, pk.y, pk.z], 1).astype(np.float32)).cuda()
+    rng = np.random.default_rng(11)
+    means = []
+    for g in (0, w.generations - 1):
+        pop = trace[g * tot: (g + 1) * tot]
+        lig = rng.integers(0, ligs.n_ligands, n)
+        ind = rng.integers(0, w.pop, n)
+        genos = torch.zeros((n, 23), dtype=torch.float32, device="cuda")
+        for r in range(n):
+            G = 7 + ligs.n_tors(int(lig[r]))
+            base = int(goff[lig[r]]) + int(ind[r]) * G
+            genos[r, :G] = pop[base: base + G]
+        coords = torch.zeros((n, 128, 3), dtype=torch.float32, device="cuda")
+        sc = torch.zeros(n, dtype=torch.float32, device="cuda")
+        dock.dock_score(pocket, gl, torch.from_numpy(lig.astype(np.int32)).cuda(), genos, sc,
+                        coords=coords, stream=stream)
+        torch.cuda.synchronize()
+        cnt = 0
+        for r in range(n):
+            cnt += int((torch.cdist(coords[r, :int(na[lig[r]])], prot) < 8.0).sum().item())
+        means.append(cnt / n)
+    return float(np.mean(means))
 
 
 def run_reference(args, rank, world):
@@ -555,7 +592,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="plain",
-                    choices=["plain", "lga", "surrogate", "mlp", "grid", "pairwise"],
+                    choices=["plain", "lga", "nogrid", "surrogate", "mlp", "grid", "pairwise"],
                     help="lga: the Lamarckian search (Solis-Wets); surrogate: pre-screened vs "
                          "plain comparison; mlp: the surrogate network's forward pass and training "
                          "step alone; grid: the pocket grid build (each its own JSON line)")
@@ -621,11 +658,15 @@ def main():
                      for n in np.diff(ligs.atom_off)})
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
     lga = args.mode == "lga"
+    nogrid = args.mode == "nogrid"
     ls = dock.ls_params(**LS_DEFAULTS) if lga else None
+    inter = dock.DOCK_INTER_PAIRWISE if nogrid else dock.DOCK_INTER_GRID
+    if nogrid:
+        groups = [8]
 
-    def step():
+    def step(**kw):
         job = dock.dock_batch(pocket, gl, w.pop, w.generations, seed=0, use_graph=1, stream=stream,
-                              ls=ls)
+                              ls=ls, inter=inter, **kw)
         return job
 
     # warm-up
@@ -636,11 +677,19 @@ def main():
     # per-launch kernel times for the roofline (separate profiled pass); in
     # the Lamarckian search also the scorings per ligand (GA + local search)
     os.environ["DOCK_PROFILE_LAUNCHES"] = "1"
-    j = step()
+    trace = None
+    if nogrid:  # populations of every generation, for the pair count below
+        trace = torch.zeros(w.generations * int(gl.geno_offsets(w.pop)[-1]), dtype=torch.float32,
+                            device="cuda")
+    j = step(trace_genotypes=trace)
     ms_kernels, n_launch = dock.dock_job_kernel_time(j)
     evals_total = int(dock.dock_results(j)["exact_evals"].sum())
     j.close()
     del os.environ["DOCK_PROFILE_LAUNCHES"]
+    inter_per_pose = None
+    if nogrid:
+        inter_per_pose = inter_pairs_per_pose(dock, torch, pocket, gl, pk, ligs, w, trace, stream)
+        del trace
     # timed region
     clocks = Clocks(local)
     if world > 1:
@@ -678,7 +727,7 @@ def main():
     for _ in range(args.e2e_steps):
         g2 = dock.dock_load_ligands(pocket, *largs, stream=stream)
         j = dock.dock_batch(pocket, g2, w.pop, w.generations, seed=0, use_graph=1, stream=stream,
-                            ls=ls)
+                            ls=ls, inter=inter)
         dock.dock_results(j)
         j.close()
         g2.close()
@@ -702,18 +751,24 @@ def main():
     # poses scored per generation per ligand: pop (GA), plus in the Lamarckian
     # search the local-search probes (the mean per-pose work of the set)
     poses_gen = w.pop if not lga else evals_total / w.n_ligands / w.generations
+    if nogrid:
+        # no grid lookups; every ligand-protein pair within the cutoff instead
+        flops_pose += w.n_ligands * inter_per_pose * FLOP_PER_PAIR - info["n_atoms"] * FLOP_INTER_PER_ATOM
+        mufu_pose += w.n_ligands * inter_per_pose * MUFU_PER_PAIR
     ach_fp32 = flops_pose * poses_gen / per_gen_s / 1e12
     ach_mufu = mufu_pose * poses_gen / per_gen_s / 1e12
     roof = {"bound": "alu", "achieved": round(ach_fp32, 3), "peak": round(fp32_peak, 2),
             "unit": "TFLOP/s", "frac": round(ach_fp32 / fp32_peak, 4),
-            "traffic": None if lga else read_traffic(),
-            "kernel": "search_kernel + ls_kernel" if lga else "search_kernel",
+            "traffic": None if (lga or nogrid) else read_traffic(),
+            "kernel": ("search_kernel + ls_kernel" if lga else
+                       "search_kernel<8, pairwise>" if nogrid else "search_kernel"),
             "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
             "mufu": {"achieved": round(ach_mufu, 4), "peak": round(mufu_peak, 4), "unit": "Tops/s",
                      "frac": round(ach_mufu / mufu_peak, 4)},
             "generation_ms": round(per_gen_s * 1000, 4), "generations_timed": n_launch,
             "launches_per_generation": len(groups), "lanes_per_pose_groups": groups}
-    line = {"metric": METRIC_LGA if lga else METRIC, "value": round(value, 2), "unit": "ligands/s",
+    line = {"metric": METRIC_LGA if lga else METRIC_NOGRID if nogrid else METRIC,
+            "value": round(value, 2), "unit": "ligands/s",
             "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -730,10 +785,13 @@ def main():
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": args.steps * (w.generations * len(groups) * (2 if lga else 1) + 1),
             "clocks": clk}
+    if nogrid:
+        line["config"]["protein_pairs_within_cutoff_per_pose"] = round(inter_per_pose, 1)
+        line["config"]["inter"] = "pairwise over a cell list of 8 A cells (no maps)"
     if lga:
         line["config"]["local_search"] = dict(LS_DEFAULTS, method="Solis-Wets, Lamarckian")
         line["scorings_per_step"] = evals_total * world
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and not nogrid:
         line["cpu_baseline"] = cpu_baseline(args.cpu_baseline_seconds, lga=lga)
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -216,7 +216,17 @@ typedef struct {
                                     scores of the probes x + xi and x - xi (NaN
                                     when not evaluated); rows of individuals not
                                     refined are not written                     */
+  int32_t inter;                 /* DOCK_INTER_GRID: inter-energy by trilinear
+                                    lookup in the pocket's maps (Algorithm 2);
+                                    DOCK_INTER_PAIRWISE: the pairwise sum over
+                                    every protein atom within the cutoff, no
+                                    maps (plain GA only, 8 lanes per pose; the
+                                    best 8 are rescored with the FP64 pairwise
+                                    sum)                                        */
 } dock_search_params;
+
+#define DOCK_INTER_GRID 0
+#define DOCK_INTER_PAIRWISE 1
 
 #define DOCK_MODE_PLAIN 0
 #define DOCK_MODE_SURROGATE 1

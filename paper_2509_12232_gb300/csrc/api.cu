@@ -676,14 +676,15 @@ struct LaunchGroup {
 // same stream by its Solis-Wets launch over the same items (queue counter
 // 4 + group).
 static cudaError_t enqueue_search(Workspace &W, const SearchArgs &a, const std::vector<LaunchGroup> &groups,
-                                  int threads, cudaStream_t q, const LsArgs *ls = nullptr) {
+                                  int threads, cudaStream_t q, const LsArgs *ls = nullptr,
+                                  bool pairwise = false) {
   cudaError_t e = cudaSuccess;
   auto one = [&](size_t i, cudaStream_t st) {
     SearchArgs b = a;
     b.items = a.items + groups[i].begin;
     b.n_items = groups[i].count;
     b.counter = a.counter + i;
-    cudaError_t r = launch_search(b, groups[i].blocks, threads, groups[i].L, st);
+    cudaError_t r = launch_search(b, groups[i].blocks, threads, groups[i].L, st, pairwise);
     if (r != cudaSuccess || ls == nullptr) return r;
     if (groups[i].ls_count == 0) return r;
     LsArgs c = *ls;
@@ -738,7 +739,14 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
               sp->keep < 1 || sp->keep > sp->candidates || sp->pop + sp->keep > 16384))
     return fail(DOCK_EINVAL, "dock_batch: surrogate mode needs a surrogate, 1 <= keep <= "
                              "candidates <= %d and pop + keep <= 16384", DOCK_MAX_CANDIDATES);
-  const int forced = sp->lanes_per_pose;
+  if (sp->inter != DOCK_INTER_GRID && sp->inter != DOCK_INTER_PAIRWISE)
+    return fail(DOCK_EINVAL, "dock_batch: inter %d", sp->inter);
+  const bool pairwise = sp->inter == DOCK_INTER_PAIRWISE;
+  if (pairwise && (sur || sp->ls.rate != 0.0f))
+    return fail(DOCK_EINVAL, "dock_batch: the pairwise inter-energy needs the plain GA");
+  if (pairwise && sp->lanes_per_pose != 0 && sp->lanes_per_pose != 8)
+    return fail(DOCK_EINVAL, "dock_batch: the pairwise inter-energy runs 8 lanes per pose");
+  const int forced = pairwise ? 8 : sp->lanes_per_pose;
   if (forced != 0 && forced != 1 && forced != 2 && forced != 4 && forced != 8)
     return fail(DOCK_EINVAL, "dock_batch: lanes_per_pose %d", forced);
   if (!(sp->ls.rate >= 0.0f && sp->ls.rate <= 1.0f))
@@ -927,7 +935,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   CU(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, L->device));
   for (LaunchGroup &gr : groups) {
     int per_sm = 0;
-    CU(search_occupancy(cfg.threads, gr.L, cfg.atoms_per_lane, &per_sm));
+    CU(search_occupancy(cfg.threads, gr.L, cfg.atoms_per_lane, &per_sm, pairwise));
     if (per_sm < 1) return fail(DOCK_EINVAL, "dock_batch: launch shape does not fit an SM");
     gr.blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, gr.count));
     gr.ls_blocks = 0;
@@ -974,6 +982,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   A.status = W.status;
   A.lig_status = W.lig_status;
   A.deadline = sp->timeout_ns ? W.deadline : nullptr;
+  A.pw = pw_view(P);
 
   LsArgs LA{};
   if (lamarck) {
@@ -1020,6 +1029,8 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   F.cy = P->center[1];
   F.cz = P->center[2];
   F.params = P->d_params;
+  F.pairwise = pairwise ? 1 : 0;
+  F.pw = pw_view(P);
 
   const int C = sur ? sp->candidates : 0, K = sur ? sp->keep : 0;
   if (sur) {
@@ -1141,10 +1152,10 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
           J->ev.push_back(e0);
           J->ev.push_back(e1);
           CU(cudaEventRecord(e0, q));
-          CU(enqueue_search(W, a, groups, cfg.threads, q, lamarck ? &la : nullptr));
+          CU(enqueue_search(W, a, groups, cfg.threads, q, lamarck ? &la : nullptr, pairwise));
           CU(cudaEventRecord(e1, q));
         } else {
-          CU(enqueue_search(W, a, groups, cfg.threads, q, lamarck ? &la : nullptr));
+          CU(enqueue_search(W, a, groups, cfg.threads, q, lamarck ? &la : nullptr, pairwise));
         }
       }
       if (sp->trace_genotypes && total_genes)
@@ -1178,6 +1189,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     put(&sp->trace_scores, sizeof(void *));
     put(&sp->ls, sizeof sp->ls);
     put(&sp->trace_ls, sizeof(void *));
+    put(&sp->inter, sizeof sp->inter);
     const void *bufs[11] = {W.geno[0], W.geno[1], W.score[0], W.score[1], W.best, W.results,
                             W.ls_evals, W.ls_bits, W.ls_count, W.ls_chain, W.ls_units};
     put(bufs, sizeof bufs);
@@ -1285,6 +1297,8 @@ extern "C" int dock_score(dock_pocket *P, dock_ligands *L, const int32_t *pose_l
     F.cy = P->center[1];
     F.cz = P->center[2];
     F.params = P->d_params;
+    F.pairwise = 0;
+    F.pw = pw_view(P);
     CU(launch_score_fp64_impl(F, L->d_centroid, P->ox, P->oy, P->oz, pose_ligand, L->n_ligands, genos,
                               n_poses, scores64, s));
     return DOCK_OK;
@@ -1387,19 +1401,7 @@ extern "C" int dock_score_pairwise(dock_pocket *P, dock_ligands *L, const int32_
   A.genos = genos;
   A.n_poses = n_poses;
   A.scores = scores;
-  A.cprot = P->d_cprot;
-  A.cext = P->d_cext;
-  A.cell_start = P->d_cell_start;
-  A.lox = P->cell_lo[0];
-  A.loy = P->cell_lo[1];
-  A.loz = P->cell_lo[2];
-  A.inv_cs = 1.0f / 8.0f;
-  A.dx = P->cell_dims[0];
-  A.dy = P->cell_dims[1];
-  A.dz = P->cell_dims[2];
-  A.tpair = P->d_tpair;
-  A.tsv = P->d_tsv;
-  A.n_types = P->n_types;
+  A.pw = pw_view(P);
   CU(launch_score_pairwise(A, (cudaStream_t)stream));
   return DOCK_OK;
 }
@@ -1506,8 +1508,9 @@ extern "C" int dock_autotune(dock_pocket *P, dock_ligands *L, const dock_search_
   q.trace_genotypes = nullptr;
   q.trace_scores = nullptr;
   q.timeout_ns = 0;
-  q.ls.rate = 0.0f;  // the launch shape of the search kernel alone
+  q.ls.rate = 0.0f;  // the launch shape of the grid search kernel alone
   q.trace_ls = nullptr;
+  q.inter = DOCK_INTER_GRID;
   for (int ti = 0; ti < 2; ++ti)
     for (int ai = 0; ai < 5; ++ai) {
       const int apl = kApl[ai], thr = kThreads[ti];

@@ -11,10 +11,14 @@ namespace dk {
 
 // ---- AutoDock4 free-energy constants (the scoring form the paper's muDock
 // ---- is "functionally equivalent" to, Section V) ----------------------------
-constexpr float kWVdw = 0.1662f, kWHb = 0.1209f, kWElec = 0.1406f, kWSol = 0.1322f;
+// (double: the FP64 paths use them as they are; FP32 code rounds explicitly)
+constexpr double kWVdw = 0.1662, kWHb = 0.1209, kWElec = 0.1406, kWSol = 0.1322;
 constexpr double kCoulomb = 332.06363, kQasp = 0.01097, kSigma = 3.6;
 constexpr double kDielA = -8.5525, kDielEps0 = 78.4, kDielK = 7.7839, kDielLambda = 0.003627;
 constexpr double kDielB = kDielEps0 - kDielA;
+// sqrt(W_elec 332.06363) = sqrt(46.688146378) rounded to float: a posed atom
+// carries its charge times this, so a pair's Coulomb factor is one product
+constexpr float kChargeScale = 6.8328725f;
 // Readings of what the paper leaves open.
 constexpr float kCutoff2 = 64.0f;   // (8 A)^2 non-bonded cutoff
 constexpr float kRmin2 = 0.25f;     // distances floored at 0.5 A

@@ -66,6 +66,19 @@ struct GridView {
   int32_t n_types;
 };
 
+// The protein for the pairwise inter-energy: atoms sorted by 8 A cell (x
+// fastest): cprot {x, y, z, q}, cext {S_j = solpar + 0.01097 |q|, V_j, type,
+// 0}; the atoms of cell c are [cell_start[c], cell_start[c + 1]).
+struct PwView {
+  const float4 *cprot, *cext;
+  const int32_t *cell_start;
+  float lox, loy, loz, inv_cs;
+  int32_t dx, dy, dz;
+  const float4 *tpair;      // [T][T] {c12, c6, c10, cap} weights folded in
+  const float2 *tsv;        // [T] {solpar, vol}
+  int32_t n_types;
+};
+
 struct SearchArgs {
   // ligands
   const LigInfo *ligs;
@@ -99,6 +112,7 @@ struct SearchArgs {
   int32_t *status;          // device status word
   int32_t *lig_status;      // [n_ligands]
   const uint64_t *deadline;  // device globaltimer deadline, NULL = none
+  PwView pw;                // the protein of the pairwise inter-energy (no-grid search)
 };
 
 // Solis-Wets refinement (local_search.cu). Batch mode (units != nullptr):
@@ -193,16 +207,7 @@ struct PairwiseArgs {
   const float *genos;       // [n_poses][DOCK_MAX_GENES]
   int64_t n_poses;
   float *scores;
-  // protein atoms sorted by 8 A cell (x fastest): cprot {x, y, z, q}, cext
-  // {S_j = solpar + 0.01097 |q|, V_j, type, 0}; the atoms of cell c are
-  // [cell_start[c], cell_start[c + 1])
-  const float4 *cprot, *cext;
-  const int32_t *cell_start;
-  float lox, loy, loz, inv_cs;
-  int32_t dx, dy, dz;
-  const float4 *tpair;      // [T][T] {c12, c6, c10, cap} weights folded in
-  const float2 *tsv;        // [T] {solpar, vol}
-  int32_t n_types;
+  PwView pw;
 };
 cudaError_t launch_score_pairwise(const PairwiseArgs &a, cudaStream_t s);
 
@@ -218,6 +223,8 @@ struct Fp64Args {
   double h;                        // grid spacing (exact)
   double cx, cy, cz;
   const dock_type_params *params;  // device [n_types]
+  int32_t pairwise;                // 1: inter-energy by the pairwise sum over pw
+  PwView pw;
 };
 
 // Launchers (defined in the .cu files).
@@ -243,7 +250,8 @@ cudaError_t launch_intra_const(LigInfo *ligs, int n_ligands, const float4 *atoms
 
 // One launch of the search kernel instantiated for L lanes per pose; every
 // item of a.items has a.items[i].lanes == L.
-cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, int L, cudaStream_t s);
+cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, int L, cudaStream_t s,
+                          bool pairwise = false);
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
 cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int n_ligands, int pop,
                                  const int64_t *geno_off, const float *genos, const float *scores,

@@ -18,7 +18,8 @@ int dk_surrogate_predict_raw(dock_surrogate *S, const uint16_t *features, int64_
 namespace dk {
 // Records the message returned by dock_last_error() for this thread; returns st.
 int vset_error(int st, const char *fmt, va_list ap);
-cudaError_t search_occupancy(int threads, int L, int atoms_per_lane, int *blocks_per_sm);
+cudaError_t search_occupancy(int threads, int L, int atoms_per_lane, int *blocks_per_sm,
+                             bool pairwise = false);
 cudaError_t launch_set_deadline(uint64_t *deadline, uint64_t timeout_ns, cudaStream_t s);
 }  // namespace dk
 
@@ -87,6 +88,24 @@ inline GridView grid_view(const dock_pocket *p) {
   g.plane_elems = 2 * (p->n - 1) * (p->n - 1);
   g.n_types = p->n_types;
   return g;
+}
+
+inline PwView pw_view(const dock_pocket *p) {
+  PwView w;
+  w.cprot = p->d_cprot;
+  w.cext = p->d_cext;
+  w.cell_start = p->d_cell_start;
+  w.lox = p->cell_lo[0];
+  w.loy = p->cell_lo[1];
+  w.loz = p->cell_lo[2];
+  w.inv_cs = 1.0f / 8.0f;
+  w.dx = p->cell_dims[0];
+  w.dy = p->cell_dims[1];
+  w.dz = p->cell_dims[2];
+  w.tpair = p->d_tpair;
+  w.tsv = p->d_tsv;
+  w.n_types = p->n_types;
+  return w;
 }
 
 struct Workspace {

@@ -72,6 +72,8 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
     return fail(DOCK_EINVAL, "dock_batch_noalloc: only the plain search (mode 0)");
   if (sp->ls.rate != 0.0f)
     return fail(DOCK_EINVAL, "dock_batch_noalloc: no local search (ls.rate must be 0)");
+  if (sp->inter != DOCK_INTER_GRID)
+    return fail(DOCK_EINVAL, "dock_batch_noalloc: grid inter-energy only (inter must be 0)");
   if (sp->lanes_per_pose != 0)
     return fail(DOCK_EINVAL, "dock_batch_noalloc: lanes_per_pose must be 0 (picked by size)");
   const int nl = L->n_ligands, pop = sp->pop, gens = sp->generations;
@@ -181,6 +183,7 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
   A.status = status;
   A.lig_status = lig_status;
   A.deadline = sp->timeout_ns ? deadline : nullptr;
+  A.pw = pw_view(P);
   Fp64Args F;
   F.ligs = L->d_info;
   F.atoms = L->d_atoms_raw;
@@ -194,6 +197,8 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
   F.cy = P->center[1];
   F.cz = P->center[2];
   F.params = P->d_params;
+  F.pairwise = 0;
+  F.pw = pw_view(P);
 
 #define NA_CU(call)                                                                   \
   do {                                                                                \

@@ -94,7 +94,7 @@ __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], con
   const float tx = cx + g[0], ty = cy + g[1], tz = cz + g[2];
   // w of a row: the atom's charge scaled by sqrt(W_elec 332.06363), so that a
   // pair's qq is the product of its two rows' w
-  const float kq = (float)sqrt((double)kWElec * kCoulomb);
+  const float kq = kChargeScale;
   for (int a = lane; a < V.n; a += L) {
     const float4 p = __ldg(V.atoms + a);
     slot[a] = make_float4(r00 * p.x + r01 * p.y + r02 * p.z + tx,
@@ -177,6 +177,92 @@ __device__ __forceinline__ float score_posed(const LigView &V, const GridView &G
   }
   for (; m < np_l; ++m) acc.add(W.term(m));
   // ---- combine the group's compensated sums --------------------------------
+  float s = acc.s, c = acc.c;
+#pragma unroll
+  for (int off = 1; off < L; off <<= 1) {
+    const float so = __shfl_xor_sync(gmask, s, off);
+    const float co = __shfl_xor_sync(gmask, c, off);
+    float t, e;
+    two_sum(s, so, t, e);
+    s = t;
+    c = __fsub_rn(__fadd_rn(c, co), e);
+  }
+  __syncwarp(gmask);
+  return __fsub_rn(s, c);
+}
+
+// Inclusive cell range [lo, hi] of the cells within one cell of coordinate u
+// (cell units) on an axis of d cells; empty (lo > hi) far outside.
+__device__ __forceinline__ void cell_range(float u, int d, int &lo, int &hi) {
+  const float c = floorf(fminf(fmaxf(u, -4.0f), (float)d + 4.0f));
+  lo = max((int)c - 1, 0);
+  hi = min((int)c + 1, d - 1);
+}
+
+// The pairwise inter-energy of this lane's atoms (lane, lane + L, ...): every
+// protein atom within the 8 A cutoff through the pair terms (Algorithm 2's
+// inter loop over nearby protein atoms), nine contiguous cell ranges per atom
+// (cells ordered x fastest). tp / sv: the type-pair and per-type tables (in
+// shared or global memory).
+template <int L>
+__device__ __forceinline__ void pairwise_inter(const LigView &V, const PwView &W,
+                                               const float4 *slot, int lane, const float4 *tp,
+                                               const float2 *sv, Kahan &acc) {
+  const float kElec = (float)((double)kWElec * kCoulomb);
+  const int T = W.n_types;
+  for (int a = lane; a < V.n; a += L) {
+    const float4 p = slot[a];
+    const int ti = V.types[a];
+    const float qi = __ldg(&V.atoms[a].w);
+    const float qe = kElec * qi;
+    const float2 svi = sv[ti];
+    const float si = (float)kWSol * (svi.x + (float)kQasp * fabsf(qi));  // W_sol S_i
+    const float vi = (float)kWSol * svi.y;                               // W_sol V_i
+    int x0, x1, y0, y1, z0, z1;
+    cell_range((p.x - W.lox) * W.inv_cs, W.dx, x0, x1);
+    cell_range((p.y - W.loy) * W.inv_cs, W.dy, y0, y1);
+    cell_range((p.z - W.loz) * W.inv_cs, W.dz, z0, z1);
+    Kahan ai;
+    for (int cz = z0; cz <= z1; ++cz)
+      for (int cy = y0; cy <= y1; ++cy) {
+        if (x0 > x1) break;
+        const int row = (cz * W.dy + cy) * W.dx;
+        const int j1 = __ldg(W.cell_start + row + x1 + 1);
+        for (int j = __ldg(W.cell_start + row + x0); j < j1; ++j) {
+          const float4 b = __ldg(W.cprot + j);
+          const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
+          const float r2 = dx * dx + dy * dy + dz * dz;
+          if (r2 < kCutoff2) {
+            const float4 ex = __ldg(W.cext + j);  // {S_j, V_j, type, 0}
+            const float4 c = tp[ti * T + (int)ex.z];
+            const float rec[8] = {c.x, c.y, c.z, c.w, qe * b.w, fmaf(si, ex.y, ex.x * vi),
+                                  0.0f, 0.0f};
+            ai.add(pair_energy(r2, rec));
+          }
+        }
+      }
+    acc.add(ai.value());
+  }
+}
+
+// Algorithm 2 with the pairwise inter-energy (no maps) for the posed ligand in
+// `slot`: intra pairs as in score_posed, then pairwise_inter; every lane of
+// the group returns the same FP32 score.
+template <int L>
+__device__ __forceinline__ float score_posed_pw(const LigView &V, const PwView &W,
+                                                const float4 *slot, int lane, unsigned gmask,
+                                                const float4 *tp, const float2 *sv) {
+  Kahan acc;
+  if (lane == 0) acc.add(V.intra_const);
+  PairWalker<L> Wk(V, slot, lane);
+  const int np_l = V.n_pairs > lane ? (V.n_pairs - lane + L - 1) / L : 0;
+  int m = 0;
+  for (; m + 3 < np_l; m += 4) {
+    const float e0 = Wk.term(m), e1 = Wk.term(m + 1), e2 = Wk.term(m + 2), e3 = Wk.term(m + 3);
+    acc.add((e0 + e1) + (e2 + e3));
+  }
+  for (; m < np_l; ++m) acc.add(Wk.term(m));
+  pairwise_inter<L>(V, W, slot, lane, tp, sv, acc);
   float s = acc.s, c = acc.c;
 #pragma unroll
   for (int off = 1; off < L; off <<= 1) {

@@ -107,6 +107,43 @@ __device__ bool grid_energy64(const GridView64 &G, int t, double q, double x, do
   return true;
 }
 
+// FP64 pairwise inter-energy of this lane's atoms (lane, lane + 32, ...):
+// every protein atom within the cutoff of the cell list, the pair terms in
+// FP64 (the no-grid search's rescoring).
+__device__ double pairwise_inter64(const Fp64Args &F, const float4 *atoms, const uint8_t *types,
+                                   int n, const double *xyz) {
+  const PwView &W = F.pw;
+  const double inv_cs = (double)W.inv_cs;
+  auto range = [](double u, int d, int &lo, int &hi) {
+    const double c = floor(fmin(fmax(u, -4.0), (double)d + 4.0));
+    lo = max((int)c - 1, 0);
+    hi = min((int)c + 1, d - 1);
+  };
+  double e = 0.0;
+  for (int a = threadIdx.x & 31; a < n; a += 32) {
+    const double x = xyz[3 * a], y = xyz[3 * a + 1], z = xyz[3 * a + 2];
+    int x0, x1, y0, y1, z0, z1;
+    range((x - (double)W.lox) * inv_cs, W.dx, x0, x1);
+    range((y - (double)W.loy) * inv_cs, W.dy, y0, y1);
+    range((z - (double)W.loz) * inv_cs, W.dz, z0, z1);
+    for (int cz = z0; cz <= z1; ++cz)
+      for (int cy = y0; cy <= y1; ++cy) {
+        if (x0 > x1) break;
+        const int row = (cz * W.dy + cy) * W.dx;
+        const int j1 = W.cell_start[row + x1 + 1];
+        for (int j = W.cell_start[row + x0]; j < j1; ++j) {
+          const float4 b = W.cprot[j];
+          const double dx = x - (double)b.x, dy = y - (double)b.y, dz = z - (double)b.z;
+          const double r = sqrt(dx * dx + dy * dy + dz * dz);
+          if (r < 8.0)
+            e += pair_energy64(F.params, types[a], (int)W.cext[j].z, (double)atoms[a].w, (double)b.w,
+                               r);
+        }
+      }
+  }
+  return e;
+}
+
 // Pose + score of one genotype in FP64 by one warp. xyz: smem [128][3].
 __device__ double pose_score_fp64_warp(const float *geno, const LigInfo &li, const Fp64Args &F,
                                        const GridView64 &G, const double *cent, double *xyz) {
@@ -147,12 +184,17 @@ __device__ double pose_score_fp64_warp(const float *geno, const LigInfo &li, con
     __syncwarp();
   }
   double e = 0.0;
-  for (int a = lane; a < li.n; a += 32) {
-    double v;
-    if (grid_energy64(G, types[a], (double)atoms[a].w, xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2], v))
-      e += v;
-    else
-      e += (double)kEout;
+  if (F.pairwise) {
+    e = pairwise_inter64(F, atoms, types, li.n, xyz);
+  } else {
+    for (int a = lane; a < li.n; a += 32) {
+      double v;
+      if (grid_energy64(G, types[a], (double)atoms[a].w, xyz[3 * a], xyz[3 * a + 1], xyz[3 * a + 2],
+                        v))
+        e += v;
+      else
+        e += (double)kEout;
+    }
   }
   for (int p = lane; p < li.n_pairs_all; p += 32) {
     const uint32_t idx = F.pair_idx[li.pair_off + p];

@@ -38,8 +38,9 @@ __device__ __forceinline__ int fetch_item(const SearchArgs &A) {
   return it;
 }
 
-// One work item for the pose slot of this thread, L lanes per pose.
-template <int L>
+// One work item for the pose slot of this thread, L lanes per pose; PW: the
+// inter-energy is the pairwise sum over the protein cell list (no maps).
+template <int L, bool PW>
 __device__ __forceinline__ void search_item(const SearchArgs &A, const Item &item, float4 *smem4) {
   const int S = blockDim.x / L;
   const int lane = threadIdx.x & (L - 1);
@@ -71,8 +72,13 @@ __device__ __forceinline__ void search_item(const SearchArgs &A, const Item &ite
     if (e < G && (e & (L - 1)) == lane) gout[e] = g[e];
   const LigView V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors);
   float4 *sl = smem4 + slot * slot_stride(L, A.atoms_per_lane);
-  const float score = pose_and_score<L>(g, V, A.moves, A.grid, A.cx, A.cy, A.cz, sl, lane, gmask,
-                                        nullptr);
+  float score;
+  if constexpr (PW) {
+    apply_pose<L>(g, V, A.moves, A.cx, A.cy, A.cz, sl, lane, gmask);
+    score = score_posed_pw<L>(V, A.pw, sl, lane, gmask, A.pw.tpair, A.pw.tsv);
+  } else {
+    score = pose_and_score<L>(g, V, A.moves, A.grid, A.cx, A.cy, A.cz, sl, lane, gmask, nullptr);
+  }
   if (lane == 0) {
     A.score_next[soff + ind] = score;
     const unsigned long long key =
@@ -82,7 +88,7 @@ __device__ __forceinline__ void search_item(const SearchArgs &A, const Item &ite
 }
 
 // One launch per lanes-per-pose group: all its items have L lanes per pose.
-template <int L>
+template <int L, bool PW = false>
 __global__ void __launch_bounds__(128, 5) search_kernel(const SearchArgs A) {
   extern __shared__ float4 smem4[];
   __shared__ int s_item;
@@ -94,24 +100,29 @@ __global__ void __launch_bounds__(128, 5) search_kernel(const SearchArgs A) {
     if (it >= A.n_items) break;
     int next = 0;
     if (threadIdx.x == 0) next = fetch_item(A);  // overlaps with this item
-    search_item<L>(A, A.items[it], smem4);
+    search_item<L, PW>(A, A.items[it], smem4);
     if (threadIdx.x == 0) s_item = next;
     __syncthreads();
   }
 }
 
-template <int L>
+template <int L, bool PW = false>
 static cudaError_t search_occupancy_l(int threads, int smem, int *blocks_per_sm) {
   // called outside stream capture before any launch of the instantiation
-  cudaError_t e = cudaFuncSetAttribute(search_kernel<L>,
+  cudaError_t e = cudaFuncSetAttribute(search_kernel<L, PW>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<L>, threads,
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, search_kernel<L, PW>, threads,
                                                        smem);
 }
 
-cudaError_t search_occupancy(int threads, int L, int atoms_per_lane, int *blocks_per_sm) {
+cudaError_t search_occupancy(int threads, int L, int atoms_per_lane, int *blocks_per_sm,
+                             bool pairwise) {
   const int smem = slots_bytes(threads, L, atoms_per_lane);
+  if (pairwise) {
+    if (L != 8) return cudaErrorInvalidValue;
+    return search_occupancy_l<8, true>(threads, smem, blocks_per_sm);
+  }
   switch (L) {
     case 1: return search_occupancy_l<1>(threads, smem, blocks_per_sm);
     case 2: return search_occupancy_l<2>(threads, smem, blocks_per_sm);
@@ -121,8 +132,14 @@ cudaError_t search_occupancy(int threads, int L, int atoms_per_lane, int *blocks
   }
 }
 
-cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, int L, cudaStream_t s) {
+cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, int L, cudaStream_t s,
+                          bool pairwise) {
   const int smem = slots_bytes(threads, L, a.atoms_per_lane);
+  if (pairwise) {
+    if (L != 8) return cudaErrorInvalidValue;
+    search_kernel<8, true><<<blocks, threads, smem, s>>>(a);
+    return cudaGetLastError();
+  }
   switch (L) {
     case 1: search_kernel<1><<<blocks, threads, smem, s>>>(a); break;
     case 2: search_kernel<2><<<blocks, threads, smem, s>>>(a); break;

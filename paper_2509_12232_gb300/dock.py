@@ -69,7 +69,11 @@ class dock_search_params(C.Structure):
                 ("use_graph", C.c_int32), ("timeout_ns", C.c_uint64),
                 ("trace_genotypes", C.c_void_p), ("trace_scores", C.c_void_p),
                 ("mode", C.c_int32), ("candidates", C.c_int32), ("keep", C.c_int32),
-                ("surrogate", C.c_void_p), ("ls", dock_ls_params), ("trace_ls", C.c_void_p)]
+                ("surrogate", C.c_void_p), ("ls", dock_ls_params), ("trace_ls", C.c_void_p),
+                ("inter", C.c_int32)]
+
+
+DOCK_INTER_GRID, DOCK_INTER_PAIRWISE = 0, 1
 
 
 DOCK_TUNE_MAX = 16
@@ -313,16 +317,18 @@ def dock_ligands_info(ligands: Ligands) -> dict:
 def dock_batch(pocket: Pocket, ligands: Ligands, pop: int, generations: int, p_cross=0.8,
                p_mut=0.02, seed=0, lanes_per_pose=0, use_graph=1, timeout_ns=0,
                trace_genotypes=None, trace_scores=None, stream=None, surrogate=None,
-               candidates=0, keep=0, ls=None, trace_ls=None) -> Job:
+               candidates=0, keep=0, ls=None, trace_ls=None, inter=0) -> Job:
     """Plain search, or the surrogate pre-screened search when `surrogate` is
     given (`candidates` children per ligand and generation, `keep` of them
     scored exactly). `ls` (a dock_ls_params, e.g. ls_params()) with a rate
-    > 0 makes the plain search Lamarckian (Solis-Wets refinement)."""
+    > 0 makes the plain search Lamarckian (Solis-Wets refinement). inter =
+    DOCK_INTER_PAIRWISE scores with the pairwise inter-energy (no maps)."""
     mode = DOCK_MODE_SURROGATE if surrogate is not None else DOCK_MODE_PLAIN
     sp = dock_search_params(pop, generations, p_cross, p_mut, seed, lanes_per_pose, use_graph,
                             timeout_ns, _dptr(trace_genotypes), _dptr(trace_scores), mode,
                             candidates, keep, surrogate.handle if surrogate is not None else None,
-                            ls if ls is not None else dock_ls_params(*NO_LS), _dptr(trace_ls))
+                            ls if ls is not None else dock_ls_params(*NO_LS), _dptr(trace_ls),
+                            inter)
     h = C.c_void_p()
     check(lib().dock_batch(pocket.handle, ligands.handle, C.byref(sp), _stream(stream), C.byref(h)))
     return Job(h, ligands.n_ligands, keep=(pocket, ligands, surrogate))
