@@ -787,7 +787,7 @@ def main():
             "clocks": clk}
     if nogrid:
         line["config"]["protein_pairs_within_cutoff_per_pose"] = round(inter_per_pose, 1)
-        line["config"]["inter"] = "pairwise over a cell list of 8 A cells (no maps)"
+        line["config"]["inter"] = "pairwise over a protein cell list (8 A rows in y-z, 1 A cells in x, rows trimmed to the cutoff chord; no maps)"
     if lga:
         line["config"]["local_search"] = dict(LS_DEFAULTS, method="Solis-Wets, Lamarckian")
         line["scorings_per_step"] = evals_total * world

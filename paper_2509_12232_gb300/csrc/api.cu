@@ -139,12 +139,12 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
   CU(dalloc(&P->d_params, P->n_types));
   CU(cudaMemcpyAsync(P->d_params, P->params.data(), sizeof(dock_type_params) * P->n_types,
                      cudaMemcpyHostToDevice, s));
-  // ---- protein atoms by 8 A cell and the type-pair tables (grid build and
-  // ---- pairwise scorer) -------------------------------------------------------
+  // ---- protein atoms by cell (kCellX in x, kCellYZ in y and z) and the
+  // ---- type-pair tables (grid build and pairwise scorer) ----------------------
   std::vector<float4> cprot((size_t)d->n_atoms), cext((size_t)d->n_atoms);
   std::vector<int32_t> cell_start;
   {
-    const double cs = 8.0;
+    const double cs3[3] = {kCellX, kCellYZ, kCellYZ};
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     for (int m = 0; m < 3; ++m) {
       const float *c = m == 0 ? d->x : (m == 1 ? d->y : d->z);
@@ -155,7 +155,7 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
         hi[m] = std::max(hi[m], (double)c[i]);
       }
       P->cell_lo[m] = (float)(lo[m] - 0.5);
-      const double dm = std::floor((hi[m] - (double)P->cell_lo[m]) / cs) + 1.0;
+      const double dm = std::floor((hi[m] - (double)P->cell_lo[m]) / cs3[m]) + 1.0;
       if (dm > 4096) return fail(DOCK_EINVAL, "dock_create_pocket: protein extent too large");
       P->cell_dims[m] = (int)dm;
     }
@@ -168,7 +168,7 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
       const float c3[3] = {d->x[i], d->y[i], d->z[i]};
       for (int m = 0; m < 3; ++m)
         ci[m] = std::min(P->cell_dims[m] - 1,
-                         std::max(0, (int)std::floor(((double)c3[m] - P->cell_lo[m]) / cs)));
+                         std::max(0, (int)std::floor(((double)c3[m] - P->cell_lo[m]) / cs3[m])));
       cell_of[i] = (ci[2] * P->cell_dims[1] + ci[1]) * P->cell_dims[0] + ci[0];
       ++cell_start[(size_t)cell_of[i] + 1];
     }
@@ -226,14 +226,7 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
     GridBuildArgs G;
     G.cprot = P->d_cprot;
     G.cext = P->d_cext;
-    G.cell_start = P->d_cell_start;
-    G.lox = P->cell_lo[0];
-    G.loy = P->cell_lo[1];
-    G.loz = P->cell_lo[2];
-    G.inv_cs = 1.0f / 8.0f;
-    G.dx = P->cell_dims[0];
-    G.dy = P->cell_dims[1];
-    G.dz = P->cell_dims[2];
+    G.cells = cell_grid(P);
     G.coef = d_gcoef;
     G.tsv = d_gtsv;
     G.n_types = P->n_types;

@@ -452,6 +452,55 @@ __device__ __forceinline__ float grid_finish(const Lookup &L) {
   return p0 + L.fz * (p1 - p0);
 }
 
+// ---------------------------------------------------------------------------
+// Cutoff search in the protein cell list (CellGrid). f(j0, j1) is called for
+// each contiguous atom range that can hold an atom within sqrt(rc2) of some
+// point of the box [xl, xh] x [yl, yh] x [zl, zh] (a point: lo = hi): the rows
+// (cy, cz) from one y-z cell below the box to one above (the y-z cell edge
+// equals the 8 A cutoff), a row skipped when its y-z square is sqrt(rc2) or
+// farther from the box's y-z rectangle, and in a kept row the x cells that
+// meet [xl - e, xh + e], e the half chord of the cutoff sphere at that
+// distance. rc2 carries a margin over the cutoff that covers the FP32
+// rounding of these bounds; the caller's pair test decides.
+// ---------------------------------------------------------------------------
+constexpr float kCutoffSearch2 = 64.016f;  // (8 A + 1e-3 A)^2
+
+__device__ __forceinline__ int cell_floor(float u, int d) {
+  return (int)floorf(fminf(fmaxf(u, -4.0f), (float)d + 4.0f));  // NaN -> -4
+}
+
+template <class F>
+__device__ __forceinline__ void cutoff_ranges_box(const CellGrid &C, float xl, float xh, float yl,
+                                                  float yh, float zl, float zh, float rc2, F &&f) {
+  const int y0 = max(cell_floor((yl - C.loy) * (1.0f / kCellYZ), C.dy) - 1, 0);
+  const int y1 = min(cell_floor((yh - C.loy) * (1.0f / kCellYZ), C.dy) + 1, C.dy - 1);
+  const int z0 = max(cell_floor((zl - C.loz) * (1.0f / kCellYZ), C.dz) - 1, 0);
+  const int z1 = min(cell_floor((zh - C.loz) * (1.0f / kCellYZ), C.dz) + 1, C.dz - 1);
+  const float uxl = (xl - C.lox) * (1.0f / kCellX), uxh = (xh - C.lox) * (1.0f / kCellX);
+  for (int cz = z0; cz <= z1; ++cz) {
+    const float c0 = fmaf((float)cz, kCellYZ, C.loz);
+    const float dzv = fmaxf(fmaxf(c0 - zh, zl - (c0 + kCellYZ)), 0.0f);
+    for (int cy = y0; cy <= y1; ++cy) {
+      const float b0 = fmaf((float)cy, kCellYZ, C.loy);
+      const float dyv = fmaxf(fmaxf(b0 - yh, yl - (b0 + kCellYZ)), 0.0f);
+      const float d2 = fmaf(dyv, dyv, dzv * dzv);
+      if (!(d2 < rc2)) continue;
+      const float e = sqrtf(rc2 - d2) * (1.0f / kCellX);
+      const int xa = max((int)floorf(fminf(fmaxf(uxl - e, -1.0f), (float)C.dx)), 0);
+      const int xb = min((int)floorf(fminf(fmaxf(uxh + e, -1.0f), (float)C.dx)), C.dx - 1);
+      if (xa > xb) continue;
+      const int row = (cz * C.dy + cy) * C.dx;
+      f(__ldg(C.cell_start + row + xa), __ldg(C.cell_start + row + xb + 1));
+    }
+  }
+}
+
+template <class F>
+__device__ __forceinline__ void cutoff_ranges(const CellGrid &C, float px, float py, float pz,
+                                              float rc2, F &&f) {
+  cutoff_ranges_box(C, px, px, py, py, pz, pz, rc2, static_cast<F &&>(f));
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

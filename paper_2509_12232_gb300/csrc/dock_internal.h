@@ -66,14 +66,23 @@ struct GridView {
   int32_t n_types;
 };
 
-// The protein for the pairwise inter-energy: atoms sorted by 8 A cell (x
-// fastest): cprot {x, y, z, q}, cext {S_j = solpar + 0.01097 |q|, V_j, type,
-// 0}; the atoms of cell c are [cell_start[c], cell_start[c + 1]).
+// Protein atoms by cell: cells are kCellX wide in x and kCellYZ in y and z
+// (x fastest); the atoms of cell c are [cell_start[c], cell_start[c + 1]).
+// A row (cy, cz) is dx consecutive cells, so any x interval of a row is one
+// contiguous atom range; the fine x cells let a lookup keep only the cells
+// that meet the chord of the cutoff sphere.
+constexpr float kCellX = 1.0f, kCellYZ = 8.0f;
+struct CellGrid {
+  const int32_t *cell_start;
+  float lox, loy, loz;  // corner of cell (0, 0, 0)
+  int32_t dx, dy, dz;
+};
+
+// The protein for the pairwise inter-energy: atoms sorted by cell, cprot {x,
+// y, z, q}, cext {S_j = solpar + 0.01097 |q|, V_j, type, 0}.
 struct PwView {
   const float4 *cprot, *cext;
-  const int32_t *cell_start;
-  float lox, loy, loz, inv_cs;
-  int32_t dx, dy, dz;
+  CellGrid cells;
   const float4 *tpair;      // [T][T] {c12, c6, c10, cap} weights folded in
   const float2 *tsv;        // [T] {solpar, vol}
   int32_t n_types;
@@ -230,10 +239,8 @@ struct Fp64Args {
 // Launchers (defined in the .cu files).
 // Grid maps from the protein cell list (grid.cu).
 struct GridBuildArgs {
-  const float4 *cprot, *cext;  // cell-sorted protein atoms, as in PairwiseArgs
-  const int32_t *cell_start;
-  float lox, loy, loz, inv_cs;
-  int32_t dx, dy, dz;
+  const float4 *cprot, *cext;  // cell-sorted protein atoms, as in PwView
+  CellGrid cells;
   const double4 *coef;         // [T][T] {c12, c6, c10, w EMAX}, weights folded in
   const double2 *tsv;          // [T] {solpar, vol}
   int32_t n_types, n;

@@ -1,9 +1,10 @@
 // Grid-map construction (Section V: the inter-energy is memoised in 3-D maps
 // around the fixed protein, one per ligand atom type, as AutoGrid does).
 //
-// One thread per node, nodes tiled 8 x 8 x 4 per block so a block's nodes
-// share their neighbour cells of the protein cell list (8 A cells; the three
-// x-neighbours of a cell are one contiguous atom range, nine ranges per node).
+// One thread per node, nodes tiled 8 x 8 x 4 per block; the 8 x 4 nodes of a
+// warp walk the atom ranges of cutoff_ranges_box over their bounding box (at
+// most nine rows of 8 A y-z cells, each trimmed in x to the chord of the
+// cutoff sphere), so their loops and loads stay uniform.
 // A float32 distance test prefilters, the kept pairs are evaluated and summed
 // in FP64 and the node values are rounded to FP32 once:
 //   M_t = sum_j min(c12 r^-12 - c6 r^-6 - c10 r^-10, w EMAX) + W_sol (solpar_t V_j + S_j V_t) g(r)
@@ -19,12 +20,6 @@ namespace dk {
 
 namespace {
 
-__device__ __forceinline__ void cell_span(float u, int d, int &lo, int &hi) {
-  const float c = floorf(fminf(fmaxf(u, -4.0f), (float)d + 4.0f));
-  lo = max((int)c - 1, 0);
-  hi = min((int)c + 1, d - 1);
-}
-
 __global__ void __launch_bounds__(256) grid_build_kernel(const GridBuildArgs A) {
   __shared__ double4 s_coef[DOCK_MAX_TYPES * DOCK_MAX_TYPES];  // {c12, c6, c10, w EMAX}
   __shared__ double2 s_sv[DOCK_MAX_TYPES];                      // {solpar, vol}
@@ -36,6 +31,13 @@ __global__ void __launch_bounds__(256) grid_build_kernel(const GridBuildArgs A) 
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   const int iy = blockIdx.y * blockDim.y + threadIdx.y;
   const int iz = blockIdx.z * blockDim.z + threadIdx.z;
+  // the nodes of this warp (8 x 4 x 1 of the 8 x 8 x 4 block) share one cell
+  // walk over their bounding box: uniform ranges, broadcast loads
+  const int wy = blockIdx.y * 8 + ((tid >> 5) & 1) * 4;
+  const float bxl = (float)(A.ox + (blockIdx.x * 8) * A.h);
+  const float bxh = (float)(A.ox + (blockIdx.x * 8 + 7) * A.h);
+  const float byl = (float)(A.oy + wy * A.h), byh = (float)(A.oy + (wy + 3) * A.h);
+  const float bz = (float)(A.oz + iz * A.h);
   if (ix >= A.n || iy >= A.n || iz >= A.n) return;
   const double px = A.ox + ix * A.h, py = A.oy + iy * A.h, pz = A.oz + iz * A.h;
   const float pxf = (float)px, pyf = (float)py, pzf = (float)pz;
@@ -45,44 +47,36 @@ __global__ void __launch_bounds__(256) grid_build_kernel(const GridBuildArgs A) 
   double E = 0.0, D = 0.0;
   const double inv2s2 = 1.0 / (2.0 * kSigma * kSigma);
   const double kE = (double)kWElec * kCoulomb, kD = (double)kWSol * kQasp;
-  int x0, x1, y0, y1, z0, z1;
-  cell_span((pxf - A.lox) * A.inv_cs, A.dx, x0, x1);
-  cell_span((pyf - A.loy) * A.inv_cs, A.dy, y0, y1);
-  cell_span((pzf - A.loz) * A.inv_cs, A.dz, z0, z1);
-  for (int cz = z0; cz <= z1; ++cz)
-    for (int cy = y0; cy <= y1; ++cy) {
-      if (x0 > x1) break;
-      const int row = (cz * A.dy + cy) * A.dx;
-      const int j1 = __ldg(A.cell_start + row + x1 + 1);
-      for (int j = __ldg(A.cell_start + row + x0); j < j1; ++j) {
-        const float4 p = __ldg(A.cprot + j);
-        const float dxf = pxf - p.x, dyf = pyf - p.y, dzf = pzf - p.z;
-        if (dxf * dxf + dyf * dyf + dzf * dzf > 64.5f) continue;
-        const double dx = px - (double)p.x, dy = py - (double)p.y, dz = pz - (double)p.z;
-        const double r2 = dx * dx + dy * dy + dz * dz;
-        if (!(r2 < 64.0)) continue;
-        const double r2c = r2 < 0.25 ? 0.25 : r2;  // r floored at 0.5 A
-        const double r = sqrt(r2c);
-        const double ir2 = 1.0 / r2c, ir4 = ir2 * ir2, ir6 = ir4 * ir2;
-        const double ir10 = ir6 * ir4, ir12 = ir6 * ir6;
-        const float4 ex = __ldg(A.cext + j);  // {S_j, V_j, type, 0}
-        const int tj = (int)ex.z;
-        const double qj = p.w, vj = ex.y;
-        const double g = exp(-r2c * inv2s2);
-        const double aj = (double)kWSol * vj * g, bj = (double)kWSol * (double)ex.x * g;
+  cutoff_ranges_box(A.cells, bxl, bxh, byl, byh, bz, bz, kCutoffSearch2, [&](int j0, int j1) {
+    for (int j = j0; j < j1; ++j) {
+      const float4 p = __ldg(A.cprot + j);
+      const float dxf = pxf - p.x, dyf = pyf - p.y, dzf = pzf - p.z;
+      if (dxf * dxf + dyf * dyf + dzf * dzf > 64.5f) continue;
+      const double dx = px - (double)p.x, dy = py - (double)p.y, dz = pz - (double)p.z;
+      const double r2 = dx * dx + dy * dy + dz * dz;
+      if (!(r2 < 64.0)) continue;
+      const double r2c = r2 < 0.25 ? 0.25 : r2;  // r floored at 0.5 A
+      const double r = sqrt(r2c);
+      const double ir2 = 1.0 / r2c, ir4 = ir2 * ir2, ir6 = ir4 * ir2;
+      const double ir10 = ir6 * ir4, ir12 = ir6 * ir6;
+      const float4 ex = __ldg(A.cext + j);  // {S_j, V_j, type, 0}
+      const int tj = (int)ex.z;
+      const double qj = p.w, vj = ex.y;
+      const double g = exp(-r2c * inv2s2);
+      const double aj = (double)kWSol * vj * g, bj = (double)kWSol * (double)ex.x * g;
 #pragma unroll
-        for (int t = 0; t < DOCK_MAX_TYPES; ++t) {
-          if (t < T) {
-            const double4 c = s_coef[t * T + tj];
-            const double raw = c.x * ir12 - c.y * ir6 - c.z * ir10;
-            m[t] += (raw > c.w ? c.w : raw) + s_sv[t].x * aj + s_sv[t].y * bj;
-          }
+      for (int t = 0; t < DOCK_MAX_TYPES; ++t) {
+        if (t < T) {
+          const double4 c = s_coef[t * T + tj];
+          const double raw = c.x * ir12 - c.y * ir6 - c.z * ir10;
+          m[t] += (raw > c.w ? c.w : raw) + s_sv[t].x * aj + s_sv[t].y * bj;
         }
-        const double diel = kDielA + kDielB / (1.0 + kDielK * exp(-kDielLambda * kDielB * r));
-        E += kE * qj / (diel * r);
-        D += kD * vj * g;
       }
+      const double diel = kDielA + kDielB / (1.0 + kDielK * exp(-kDielLambda * kDielB * r));
+      E += kE * qj / (diel * r);
+      D += kD * vj * g;
     }
+  });
   const int64_t nn = (int64_t)A.n * A.n * A.n;
   const int64_t node = ((int64_t)iz * A.n + iy) * A.n + ix;
   A.fpm[node] = make_float2((float)(E + D), (float)(E - D));

@@ -90,18 +90,23 @@ inline GridView grid_view(const dock_pocket *p) {
   return g;
 }
 
+inline CellGrid cell_grid(const dock_pocket *p) {
+  CellGrid c;
+  c.cell_start = p->d_cell_start;
+  c.lox = p->cell_lo[0];
+  c.loy = p->cell_lo[1];
+  c.loz = p->cell_lo[2];
+  c.dx = p->cell_dims[0];
+  c.dy = p->cell_dims[1];
+  c.dz = p->cell_dims[2];
+  return c;
+}
+
 inline PwView pw_view(const dock_pocket *p) {
   PwView w;
   w.cprot = p->d_cprot;
   w.cext = p->d_cext;
-  w.cell_start = p->d_cell_start;
-  w.lox = p->cell_lo[0];
-  w.loy = p->cell_lo[1];
-  w.loz = p->cell_lo[2];
-  w.inv_cs = 1.0f / 8.0f;
-  w.dx = p->cell_dims[0];
-  w.dy = p->cell_dims[1];
-  w.dz = p->cell_dims[2];
+  w.cells = cell_grid(p);
   w.tpair = p->d_tpair;
   w.tsv = p->d_tsv;
   w.n_types = p->n_types;

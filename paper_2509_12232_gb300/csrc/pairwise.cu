@@ -2,9 +2,9 @@
 // atom within the 8 A cutoff of a ligand atom enters through the pair terms
 // (Algorithm 2's inter loop over nearby protein atoms, the sum the grid maps
 // of Section V approximate), plus the intra-energy; FP32 with compensated
-// sums. Protein atoms come from a cell list with 8 A cells (cells ordered x
-// fastest, so the three x-neighbours of a cell are one contiguous atom range:
-// nine ranges per ligand atom).
+// sums. Protein atoms come from the cell list of cutoff_ranges: at most nine
+// rows of 8 A y-z cells per ligand atom, each trimmed in x (1 A cells) to the
+// chord of the cutoff sphere.
 #include "pose.cuh"
 
 namespace dk {

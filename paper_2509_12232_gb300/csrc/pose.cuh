@@ -191,19 +191,10 @@ __device__ __forceinline__ float score_posed(const LigView &V, const GridView &G
   return __fsub_rn(s, c);
 }
 
-// Inclusive cell range [lo, hi] of the cells within one cell of coordinate u
-// (cell units) on an axis of d cells; empty (lo > hi) far outside.
-__device__ __forceinline__ void cell_range(float u, int d, int &lo, int &hi) {
-  const float c = floorf(fminf(fmaxf(u, -4.0f), (float)d + 4.0f));
-  lo = max((int)c - 1, 0);
-  hi = min((int)c + 1, d - 1);
-}
-
 // The pairwise inter-energy of this lane's atoms (lane, lane + L, ...): every
 // protein atom within the 8 A cutoff through the pair terms (Algorithm 2's
-// inter loop over nearby protein atoms), nine contiguous cell ranges per atom
-// (cells ordered x fastest). tp / sv: the type-pair and per-type tables (in
-// shared or global memory).
+// inter loop over nearby protein atoms), found through cutoff_ranges. tp /
+// sv: the type-pair and per-type tables (in shared or global memory).
 template <int L>
 __device__ __forceinline__ void pairwise_inter(const LigView &V, const PwView &W,
                                                const float4 *slot, int lane, const float4 *tp,
@@ -218,29 +209,21 @@ __device__ __forceinline__ void pairwise_inter(const LigView &V, const PwView &W
     const float2 svi = sv[ti];
     const float si = (float)kWSol * (svi.x + (float)kQasp * fabsf(qi));  // W_sol S_i
     const float vi = (float)kWSol * svi.y;                               // W_sol V_i
-    int x0, x1, y0, y1, z0, z1;
-    cell_range((p.x - W.lox) * W.inv_cs, W.dx, x0, x1);
-    cell_range((p.y - W.loy) * W.inv_cs, W.dy, y0, y1);
-    cell_range((p.z - W.loz) * W.inv_cs, W.dz, z0, z1);
     Kahan ai;
-    for (int cz = z0; cz <= z1; ++cz)
-      for (int cy = y0; cy <= y1; ++cy) {
-        if (x0 > x1) break;
-        const int row = (cz * W.dy + cy) * W.dx;
-        const int j1 = __ldg(W.cell_start + row + x1 + 1);
-        for (int j = __ldg(W.cell_start + row + x0); j < j1; ++j) {
-          const float4 b = __ldg(W.cprot + j);
-          const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
-          const float r2 = dx * dx + dy * dy + dz * dz;
-          if (r2 < kCutoff2) {
-            const float4 ex = __ldg(W.cext + j);  // {S_j, V_j, type, 0}
-            const float4 c = tp[ti * T + (int)ex.z];
-            const float rec[8] = {c.x, c.y, c.z, c.w, qe * b.w, fmaf(si, ex.y, ex.x * vi),
-                                  0.0f, 0.0f};
-            ai.add(pair_energy(r2, rec));
-          }
+    cutoff_ranges(W.cells, p.x, p.y, p.z, kCutoffSearch2, [&](int j0, int j1) {
+      for (int j = j0; j < j1; ++j) {
+        const float4 b = __ldg(W.cprot + j);
+        const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < kCutoff2) {
+          const float4 ex = __ldg(W.cext + j);  // {S_j, V_j, type, 0}
+          const float4 c = tp[ti * T + (int)ex.z];
+          const float rec[8] = {c.x, c.y, c.z, c.w, qe * b.w, fmaf(si, ex.y, ex.x * vi),
+                                0.0f, 0.0f};
+          ai.add(pair_energy(r2, rec));
         }
       }
+    });
     acc.add(ai.value());
   }
 }

@@ -113,8 +113,10 @@ __device__ bool grid_energy64(const GridView64 &G, int t, double q, double x, do
 __device__ double pairwise_inter64(const Fp64Args &F, const float4 *atoms, const uint8_t *types,
                                    int n, const double *xyz) {
   const PwView &W = F.pw;
-  const double inv_cs = (double)W.inv_cs;
-  auto range = [](double u, int d, int &lo, int &hi) {
+  const CellGrid &C = W.cells;
+  // the cell ranges of cutoff_ranges, bounds in FP64 (margin as there)
+  const double rc2 = (double)kCutoffSearch2;
+  auto span = [](double u, int d, int &lo, int &hi) {
     const double c = floor(fmin(fmax(u, -4.0), (double)d + 4.0));
     lo = max((int)c - 1, 0);
     hi = min((int)c + 1, d - 1);
@@ -122,24 +124,34 @@ __device__ double pairwise_inter64(const Fp64Args &F, const float4 *atoms, const
   double e = 0.0;
   for (int a = threadIdx.x & 31; a < n; a += 32) {
     const double x = xyz[3 * a], y = xyz[3 * a + 1], z = xyz[3 * a + 2];
-    int x0, x1, y0, y1, z0, z1;
-    range((x - (double)W.lox) * inv_cs, W.dx, x0, x1);
-    range((y - (double)W.loy) * inv_cs, W.dy, y0, y1);
-    range((z - (double)W.loz) * inv_cs, W.dz, z0, z1);
-    for (int cz = z0; cz <= z1; ++cz)
+    const double ux = (x - (double)C.lox) / (double)kCellX;
+    int y0, y1, z0, z1;
+    span((y - (double)C.loy) / (double)kCellYZ, C.dy, y0, y1);
+    span((z - (double)C.loz) / (double)kCellYZ, C.dz, z0, z1);
+    for (int cz = z0; cz <= z1; ++cz) {
+      const double zl = (double)C.loz + cz * (double)kCellYZ;
+      const double dzv = fmax(fmax(zl - z, z - (zl + (double)kCellYZ)), 0.0);
       for (int cy = y0; cy <= y1; ++cy) {
-        if (x0 > x1) break;
-        const int row = (cz * W.dy + cy) * W.dx;
-        const int j1 = W.cell_start[row + x1 + 1];
-        for (int j = W.cell_start[row + x0]; j < j1; ++j) {
+        const double yl = (double)C.loy + cy * (double)kCellYZ;
+        const double dyv = fmax(fmax(yl - y, y - (yl + (double)kCellYZ)), 0.0);
+        const double d2 = dyv * dyv + dzv * dzv;
+        if (!(d2 < rc2)) continue;
+        const double h = sqrt(rc2 - d2) / (double)kCellX;
+        const int xa = max((int)floor(fmin(fmax(ux - h, -1.0), (double)C.dx)), 0);
+        const int xb = min((int)floor(fmin(fmax(ux + h, -1.0), (double)C.dx)), C.dx - 1);
+        if (xa > xb) continue;
+        const int row = (cz * C.dy + cy) * C.dx;
+        const int j1 = C.cell_start[row + xb + 1];
+        for (int j = C.cell_start[row + xa]; j < j1; ++j) {
           const float4 b = W.cprot[j];
           const double dx = x - (double)b.x, dy = y - (double)b.y, dz = z - (double)b.z;
           const double r = sqrt(dx * dx + dy * dy + dz * dz);
           if (r < 8.0)
-            e += pair_energy64(F.params, types[a], (int)W.cext[j].z, (double)atoms[a].w, (double)b.w,
-                               r);
+            e += pair_energy64(F.params, types[a], (int)W.cext[j].z, (double)atoms[a].w,
+                               (double)b.w, r);
         }
       }
+    }
   }
   return e;
 }
