@@ -650,7 +650,9 @@ def main():
         os.environ["DOCK_THREADS"], os.environ["DOCK_ATOMS_PER_LANE"] = str(t_), str(a_)
         picked_by = "--shape"
     else:
-        tune = dock.dock_autotune(pocket, gl, w.pop, 4, stream=stream)
+        tune = dock.dock_autotune(pocket, gl, w.pop, 4, stream=stream,
+                                  inter=dock.DOCK_INTER_PAIRWISE if args.mode == "nogrid"
+                                  else dock.DOCK_INTER_GRID)
         shape = tune["table"][tune["best"]]
         picked_by = "dock_autotune"
     # one search launch per lanes-per-pose group L (smallest L in 1, 2, 4, 8
@@ -663,8 +665,6 @@ def main():
     nogrid = args.mode == "nogrid"
     ls = dock.ls_params(**LS_DEFAULTS) if lga else None
     inter = dock.DOCK_INTER_PAIRWISE if nogrid else dock.DOCK_INTER_GRID
-    if nogrid:
-        groups = [8]
 
     def step(**kw):
         job = dock.dock_batch(pocket, gl, w.pop, w.generations, seed=0, use_graph=1, stream=stream,
@@ -776,7 +776,7 @@ def main():
             "unit": "TFLOP/s", "frac": round(ach_fp32 / fp32_peak, 4),
             "traffic": None if (lga or nogrid) else read_traffic(),
             "kernel": ("search_kernel + ls_kernel" if lga else
-                       "search_kernel<8, pairwise>" if nogrid else "search_kernel"),
+                       "search_kernel<L, pairwise>" if nogrid else "search_kernel"),
             "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
             "mufu": {"achieved": round(ach_mufu, 4), "peak": round(mufu_peak, 4), "unit": "Tops/s",
                      "frac": round(ach_mufu / mufu_peak, 4)},

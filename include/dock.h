@@ -220,9 +220,8 @@ typedef struct {
                                     lookup in the pocket's maps (Algorithm 2);
                                     DOCK_INTER_PAIRWISE: the pairwise sum over
                                     every protein atom within the cutoff, no
-                                    maps (plain GA only, 8 lanes per pose; the
-                                    best 8 are rescored with the FP64 pairwise
-                                    sum)                                        */
+                                    maps (plain GA only; the best 8 are
+                                    rescored with the FP64 pairwise sum)        */
 } dock_search_params;
 
 #define DOCK_INTER_GRID 0
@@ -436,7 +435,8 @@ typedef struct {
   int32_t best;                            /* index of the chosen shape       */
 } dock_tune_table;
 
-/* Times the plain search on this ligand set for each candidate launch shape
+/* Times the plain search (with the inter-energy params->inter names; no local
+ * search) on this ligand set for each candidate launch shape
  * (CTA threads in {64, 128} x shared-memory atoms per lane in {8 .. 32}; a
  * ligand of n atoms then runs with the smallest L in {1, 2, 4, 8} lanes per
  * pose with L * atoms_per_lane >= n), picks the fastest (ties to the earlier
@@ -444,7 +444,8 @@ typedef struct {
  * dock_batch calls with lanes_per_pose = 0 use it. Runs short searches
  * (min(max(generations, 2), 4) generations) on stream and waits for them;
  * results do not depend on the shape beyond FP32 summation order.
- * Errors: DOCK_EINVAL (surrogate mode or forced lanes), DOCK_ENOMEM, DOCK_ECUDA. */
+ * Errors: DOCK_EINVAL (surrogate mode, forced lanes, or an invalid inter),
+ * DOCK_ENOMEM, DOCK_ECUDA. */
 int dock_autotune(dock_pocket *pocket, dock_ligands *ligands, const dock_search_params *params,
                   void *stream, dock_tune_table *table);
 

@@ -737,9 +737,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   const bool pairwise = sp->inter == DOCK_INTER_PAIRWISE;
   if (pairwise && (sur || sp->ls.rate != 0.0f))
     return fail(DOCK_EINVAL, "dock_batch: the pairwise inter-energy needs the plain GA");
-  if (pairwise && sp->lanes_per_pose != 0 && sp->lanes_per_pose != 8)
-    return fail(DOCK_EINVAL, "dock_batch: the pairwise inter-energy runs 8 lanes per pose");
-  const int forced = pairwise ? 8 : sp->lanes_per_pose;
+  const int forced = sp->lanes_per_pose;
   if (forced != 0 && forced != 1 && forced != 2 && forced != 4 && forced != 8)
     return fail(DOCK_EINVAL, "dock_batch: lanes_per_pose %d", forced);
   if (!(sp->ls.rate >= 0.0f && sp->ls.rate <= 1.0f))
@@ -1501,9 +1499,8 @@ extern "C" int dock_autotune(dock_pocket *P, dock_ligands *L, const dock_search_
   q.trace_genotypes = nullptr;
   q.trace_scores = nullptr;
   q.timeout_ns = 0;
-  q.ls.rate = 0.0f;  // the launch shape of the grid search kernel alone
+  q.ls.rate = 0.0f;  // the launch shape of the search kernel alone (grid or pairwise inter)
   q.trace_ls = nullptr;
-  q.inter = DOCK_INTER_GRID;
   for (int ti = 0; ti < 2; ++ti)
     for (int ai = 0; ai < 5; ++ai) {
       const int apl = kApl[ai], thr = kThreads[ti];

@@ -120,8 +120,13 @@ cudaError_t search_occupancy(int threads, int L, int atoms_per_lane, int *blocks
                              bool pairwise) {
   const int smem = slots_bytes(threads, L, atoms_per_lane);
   if (pairwise) {
-    if (L != 8) return cudaErrorInvalidValue;
-    return search_occupancy_l<8, true>(threads, smem, blocks_per_sm);
+    switch (L) {
+      case 1: return search_occupancy_l<1, true>(threads, smem, blocks_per_sm);
+      case 2: return search_occupancy_l<2, true>(threads, smem, blocks_per_sm);
+      case 4: return search_occupancy_l<4, true>(threads, smem, blocks_per_sm);
+      case 8: return search_occupancy_l<8, true>(threads, smem, blocks_per_sm);
+      default: return cudaErrorInvalidValue;
+    }
   }
   switch (L) {
     case 1: return search_occupancy_l<1>(threads, smem, blocks_per_sm);
@@ -136,8 +141,13 @@ cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, int L, c
                           bool pairwise) {
   const int smem = slots_bytes(threads, L, a.atoms_per_lane);
   if (pairwise) {
-    if (L != 8) return cudaErrorInvalidValue;
-    search_kernel<8, true><<<blocks, threads, smem, s>>>(a);
+    switch (L) {
+      case 1: search_kernel<1, true><<<blocks, threads, smem, s>>>(a); break;
+      case 2: search_kernel<2, true><<<blocks, threads, smem, s>>>(a); break;
+      case 4: search_kernel<4, true><<<blocks, threads, smem, s>>>(a); break;
+      case 8: search_kernel<8, true><<<blocks, threads, smem, s>>>(a); break;
+      default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
   }
   switch (L) {

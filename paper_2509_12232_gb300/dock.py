@@ -481,11 +481,12 @@ def dock_surrogate_train(s: Surrogate, features, scores, epochs=2, batch=4096, l
 
 
 def dock_autotune(pocket: Pocket, ligands: Ligands, pop: int, generations: int, seed=0,
-                  stream=None) -> dict:
-    """Measure the search kernel's launch shapes on this ligand set and keep
-    the fastest for later dock_batch calls; returns the measured table."""
+                  stream=None, inter=0) -> dict:
+    """Measure the search kernel's launch shapes on this ligand set (for the
+    inter-energy `inter` names) and keep the fastest for later dock_batch
+    calls; returns the measured table."""
     sp = dock_search_params(pop, generations, 0.8, 0.02, seed, 0, 0, 0, None, None,
-                            DOCK_MODE_PLAIN, 0, 0, None, dock_ls_params(*NO_LS), None)
+                            DOCK_MODE_PLAIN, 0, 0, None, dock_ls_params(*NO_LS), None, inter)
     t = dock_tune_table()
     check(lib().dock_autotune(pocket.handle, ligands.handle, C.byref(sp), _stream(stream), C.byref(t)))
     rows = [dict(threads=t.threads[i], atoms_per_lane=t.atoms_per_lane[i],

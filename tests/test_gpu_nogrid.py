@@ -55,7 +55,10 @@ def _oracle(setup, l, genos):
     return np.array(score), np.array(margin)
 
 
-def test_nogrid_search_replay(dock, setup):
+@pytest.mark.parametrize("lanes", [0, 8, 2])
+def test_nogrid_search_replay(dock, setup, lanes):
+    """lanes 0: lanes per pose picked by ligand size (several launch groups);
+    8 and 2: every ligand forced to that many lanes per pose."""
     ligs, gl, pocket = setup["ligs"], setup["gl"], setup["pocket"]
     nl, pop, gens, seed = ligs.n_ligands, 48, 4, 3
     goff = gl.geno_offsets(pop)
@@ -64,7 +67,7 @@ def test_nogrid_search_replay(dock, setup):
     ts = torch.zeros(gens * nl * pop, dtype=torch.float32, device="cuda")
     job = dock.dock_batch(pocket, gl, pop, gens, seed=seed, trace_genotypes=tg, trace_scores=ts,
                           stream=torch.cuda.current_stream(), inter=dock.DOCK_INTER_PAIRWISE,
-                          **SEARCH)
+                          lanes_per_pose=lanes, **SEARCH)
     res = dock.dock_results(job)
     tg, ts = tg.cpu().numpy(), ts.cpu().numpy()
     R = setup["pk"].radius
@@ -137,7 +140,7 @@ def test_nogrid_invalid_settings(dock, setup):
     with pytest.raises(dock.DockError):
         dock.dock_batch(pocket, gl, 16, 2, inter=2)
     with pytest.raises(dock.DockError):
-        dock.dock_batch(pocket, gl, 16, 2, inter=dock.DOCK_INTER_PAIRWISE, lanes_per_pose=4)
+        dock.dock_batch(pocket, gl, 16, 2, inter=dock.DOCK_INTER_PAIRWISE, lanes_per_pose=3)
     with pytest.raises(dock.DockError):
         dock.dock_batch(pocket, gl, 16, 2, inter=dock.DOCK_INTER_PAIRWISE,
                         ls=dock.ls_params(rate=0.1))
