@@ -11,11 +11,14 @@
 //   - one thread issues tcgen05.mma (M = 128, N = 256, K = 16 per instruction)
 //     into a 256-column FP32 accumulator in tensor memory and commits it to an
 //     mbarrier;
-//   - warps w and w + 4 read accumulator lanes 32 (w mod 4) .. + 31 (columns
-//     0-127 and 128-255) with tcgen05.ld, add the bias, apply GELU, round to
-//     BF16 and store the activations in the same layout as the next layer's A
-//     operand; after the third layer each thread forms half of its row's
-//     output (a dot product with the FP32 w4) and the halves are added.
+//   - the 16 warps drain the accumulator, warp w reading lanes 32 (w mod 4) ..
+//     + 31 (the lane quarter its position in the warp group may access) and
+//     columns 64 (w / 4) .. + 63 with tcgen05.ld; they add the bias, apply
+//     GELU, round to BF16 and store the activations in the same layout as the
+//     next layer's A operand; after the third layer each thread forms a
+//     quarter of its row's output (a dot product with the FP32 w4) and the
+//     quarters are added. Four warps per scheduler keep the epilogue, the
+//     kernel's longest phase, issuing while some wait on their loads.
 // Every mbarrier wait is bounded (one second of globaltimer); a timeout sets
 // *err, skips the rest of the CTA's tiles (the caller fills the output with
 // NaN beforehand) and releases the tensor memory after waiting, again
@@ -31,12 +34,12 @@ namespace mlp {
 namespace {
 
 constexpr int TM = 128;        // rows per tile (MMA M)
-constexpr int kThreads = 256;  // warps w and w + 4 read accumulator lanes 32 w .. 32 w + 31
-                               // (columns 0-127 and 128-255)
+constexpr int kThreads = 512;  // warp w: accumulator lanes 32 (w mod 4) .., columns 64 (w / 4) ..
+constexpr int kParts = kThreads / 128;  // column quarters of a row
 constexpr int XH_BYTES = TM * HIDDEN * 2;       // feature tile (32 KB) or hidden tile (64 KB)
 constexpr int W_BYTES = HIDDEN * HIDDEN * 2;    // one layer's weights (at most 128 KB)
-constexpr int SMEM_BYTES = XH_BYTES + W_BYTES + 64 + TM * 4 + 4 * HIDDEN * 4;
-// + output partial sums, biases b1..b3 and w4
+constexpr int SMEM_BYTES = XH_BYTES + W_BYTES + 64 + (kParts - 1) * TM * 4 + 4 * HIDDEN * 4;
+// + output partial sums of quarters 1-3, biases b1..b3 and w4
 constexpr int WC_L2 = HIDDEN * FEATURES;        // element offsets of layers 2, 3 in the weights
 constexpr int WC_L3 = WC_L2 + HIDDEN * HIDDEN;
 constexpr int kCopyChunk = 16384;               // bytes per bulk copy
@@ -200,9 +203,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + XH_BYTES + W_BYTES);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
   float *ypart = reinterpret_cast<float *>(sm + XH_BYTES + W_BYTES + 64);
-  float *s_par = ypart + TM;  // b1, b2, b3, w4 (256 each)
+  float *s_par = ypart + (kParts - 1) * TM;  // b1, b2, b3, w4 (256 each)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;  // accumulator lanes 32 quad.., columns 128 half..
+  const int quad = warp & 3, part = warp >> 2;  // accumulator lanes 32 quad.., columns 64 part..
   const uint32_t bar_w = smem_u32(&bars[0]), bar_m = smem_u32(&bars[1]);
   const uint32_t s_xh = smem_u32(xh), s_w = smem_u32(sm + XH_BYTES);
   if (tid == 0) {
@@ -244,11 +247,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   // feature tile t: a warp moves 8 rows x 4 chunks of 16 bytes per step (full
   // 32-byte sectors) into registers, stored later in the K-major core-matrix
   // layout (K = 128); the next tile's rows are read during the last epilogue
-  uint4 xr[8];
+  constexpr int kXSteps = 64 / (kThreads / 32);
+  uint4 xr[kXSteps];
   auto load_x = [&](int64_t t) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int v = warp + 8 * i;
+    for (int i = 0; i < kXSteps; ++i) {
+      const int v = warp + (kThreads / 32) * i;
       const int row = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
       const int64_t gr = t * TM + row;
       xr[i] = gr < n ? __ldg(reinterpret_cast<const uint4 *>(X + gr * FEATURES) + chunk)
@@ -261,15 +265,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int v = warp + 8 * i;
+    for (int i = 0; i < kXSteps; ++i) {
+      const int v = warp + (kThreads / 32) * i;
       const int row = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
       *reinterpret_cast<uint4 *>(xh + canon_off(row, 8 * chunk, FEATURES)) = xr[i];
     }
     fence_proxy_async();
     __syncthreads();
     const int row = 32 * quad + lane;                  // this thread's row (accumulator lane)
-    float yrow = half ? 0.0f : b4;
+    float yrow = part ? 0.0f : b4;
     for (int layer = 0; layer < 3 && ok; ++layer) {
       const int K = layer == 0 ? FEATURES : HIDDEN;
       // this layer's weights are in shared memory (the outcome of every wait
@@ -303,8 +307,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---- epilogue: bias + GELU -> BF16 (next A operand) or the output --
       const float *bias = s_par + HIDDEN * layer;
       const float *w4 = s_par + 3 * HIDDEN;
-      // four chunks of 32 columns; the read of chunk j + 1 is in flight while
-      // chunk j is processed
+      // two chunks of 32 columns; the read of the second is in flight while
+      // the first is processed
       uint32_t ra[32], rb[32];
       auto chunk = [&](int cc, const uint32_t (&r)[32]) {
 #pragma unroll
@@ -334,25 +338,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
         }
       };
-      const int c0 = 4 * half;
+      const int c0 = 2 * part;
       tmem_ld32(t_lane + 32u * c0, ra);
       tmem_wait(ra);
       tmem_ld32(t_lane + 32u * (c0 + 1), rb);
       chunk(c0, ra);
       tmem_wait(rb);
-      tmem_ld32(t_lane + 32u * (c0 + 2), ra);
       chunk(c0 + 1, rb);
-      tmem_wait(ra);
-      tmem_ld32(t_lane + 32u * (c0 + 3), rb);
-      chunk(c0 + 2, ra);
-      tmem_wait(rb);
-      chunk(c0 + 3, rb);
       if (layer < 2) fence_proxy_async();
-      else if (half) ypart[row] = yrow;
+      else if (part) ypart[(part - 1) * TM + row] = yrow;
       fence_before_sync();
       __syncthreads();
     }
-    if (ok && !half && t * TM + row < n) y[t * TM + row] = yrow + ypart[row];
+    if (ok && !part && t * TM + row < n)
+      y[t * TM + row] = yrow + (ypart[row] + (ypart[TM + row] + ypart[2 * TM + row]));
   }
   // ---- teardown: let copies and products in flight finish, free TMEM ------
   if (w_pending) mbar_wait(bar_w, ph_w);
