@@ -46,6 +46,16 @@ WORKLOAD = "c2"
 METRIC = "ligands/s (plain exact GA docking: 1,024 poses x 50 generations per ligand)"
 DESCR = ("1,000 synthetic ligands (10-60 heavy atoms, 0-12 torsions) vs a 4,000-atom pocket "
          "(16 A cavity, 86^3 x 7 grid maps), 1,024 poses x 50 generations, FP64 best-8 rescoring")
+# --workload c3: the uneven batch (one persistent launch per lanes-per-pose
+# group and generation, graph-captured, autotuned shape) at its full size
+WORKLOADS = {
+    "c2": (METRIC, DESCR),
+    "c3": ("ligands/s (plain exact GA docking of an uneven batch: 512 poses x 30 generations "
+           "per ligand)",
+           "100,000 synthetic ligands (heavy atoms lognormal, mean 30, sd 10, clipped to 8-100; "
+           "Poisson(5) torsions, at most 16) vs a 4,000-atom pocket (16 A cavity, 86^3 x 7 grid "
+           "maps), 512 poses x 30 generations, FP64 best-8 rescoring"),
+}
 METRIC_NOGRID = ("ligands/s (plain exact GA docking without grid maps: pairwise inter-energy, "
                  "1,024 poses x 50 generations per ligand)")
 METRIC_LGA = ("ligands/s (Lamarckian GA docking: 1,024 poses x 50 generations per ligand, "
@@ -598,6 +608,10 @@ def main():
                     help="lga: the Lamarckian search (Solis-Wets); surrogate: pre-screened vs "
                          "plain comparison; mlp: the surrogate network's forward pass and training "
                          "step alone; grid: the pocket grid build (each its own JSON line)")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
+                    help="c2 (default): 1,000 ligands x 1,024 poses x 50 generations; c3: the "
+                         "uneven batch, 100,000 ligands x 512 poses x 30 generations "
+                         "(plain, lga and nogrid modes)")
     ap.add_argument("--ref-ligands-per-core", type=int, default=1)
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -608,6 +622,9 @@ def main():
                     help="THREADSxATOMS_PER_LANE launch shape instead of dock_autotune's pick "
                          "(profiling runs)")
     args = ap.parse_args()
+    global WORKLOAD, METRIC, DESCR
+    WORKLOAD = args.workload
+    METRIC, DESCR = WORKLOADS[WORKLOAD]
     rank, world, local = env_rank()
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -774,7 +791,7 @@ def main():
     ach_mufu = mufu_pose * poses_gen / per_gen_s / 1e12
     roof = {"bound": "alu", "achieved": round(ach_fp32, 3), "peak": round(fp32_peak, 2),
             "unit": "TFLOP/s", "frac": round(ach_fp32 / fp32_peak, 4),
-            "traffic": None if (lga or nogrid) else read_traffic(),
+            "traffic": None if (lga or nogrid or WORKLOAD != "c2") else read_traffic(),
             "kernel": ("search_kernel + ls_kernel" if lga else
                        "search_kernel<L, pairwise>" if nogrid else "search_kernel"),
             "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
@@ -782,7 +799,10 @@ def main():
                      "frac": round(ach_mufu / mufu_peak, 4)},
             "generation_ms": round(per_gen_s * 1000, 4), "generations_timed": n_launch,
             "launches_per_generation": len(groups), "lanes_per_pose_groups": groups}
-    line = {"metric": METRIC_LGA if lga else METRIC_NOGRID if nogrid else METRIC,
+    metric = METRIC_LGA if lga else METRIC_NOGRID if nogrid else METRIC
+    metric = metric.replace("1,024 poses x 50 generations",
+                            "{:,} poses x {} generations".format(w.pop, w.generations))
+    line = {"metric": metric,
             "value": round(value, 2), "unit": "ligands/s",
             "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 3),
