@@ -23,51 +23,55 @@ __device__ __forceinline__ float sel16(const float (&g)[DOCK_MAX_GENES], int j) 
 }
 
 // Features of the pose in `slot` by the 8 lanes of a group, into the
-// group's shared row f[128] (FP32), deterministic: counts by ballots, shell
-// charge sums by shuffle trees in a fixed order.
+// group's shared row f[128] (FP32), deterministic: the (type, shell) counts
+// by integer shared-memory atomics (exact in any order), the shell sums of q
+// and |q| per lane in atom order, then over the lanes by a fixed shuffle tree.
 __device__ __forceinline__ void pose_features(const float (&g)[DOCK_MAX_GENES], const LigView &V,
                                               const float4 *slot, int lane, unsigned gmask,
                                               float cx, float cy, float cz, float radius, float *f) {
   const float inv_w = 8.0f / radius;
-  float cnt[7];
+  int *hist = reinterpret_cast<int *>(f);  // f[0..55] hold the counts until converted
 #pragma unroll
-  for (int i = 0; i < 7; ++i) cnt[i] = 0.0f;
-  float qs = 0.0f, aqs = 0.0f;  // this lane owns shell `lane`
-  for (int base = 0; base < V.n; base += kFeatL) {
-    const int a = base + lane;
-    int bin = -1, sh = -1;
-    float q = 0.0f;
-    if (a < V.n) {
-      const float4 p = slot[a];
-      const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
-      sh = min((int)(sqrtf(dx * dx + dy * dy + dz * dz) * inv_w), 7);
-      const int t = V.types[a];
-      bin = t < 7 ? t * 8 + sh : -1;
-      q = __ldg(&V.atoms[a].w);
-    }
+  for (int i = 0; i < 7; ++i) hist[i * 8 + lane] = 0;
+  __syncwarp(gmask);
+  float qs[8], aqs[8];
 #pragma unroll
-    for (int b = 0; b < 56; ++b) {
-      const unsigned m = __ballot_sync(gmask, bin == b);
-      if ((b & 7) == lane) cnt[b >> 3] += (float)__popc(m);
-    }
+  for (int s = 0; s < 8; ++s) qs[s] = aqs[s] = 0.0f;
+  for (int a = lane; a < V.n; a += kFeatL) {
+    const float4 p = slot[a];
+    const float dx = p.x - cx, dy = p.y - cy, dz = p.z - cz;
+    const int sh = min((int)(sqrtf(dx * dx + dy * dy + dz * dz) * inv_w), 7);
+    const int t = V.types[a];
+    if (t < 7) atomicAdd(&hist[t * 8 + sh], 1);
+    const float q = __ldg(&V.atoms[a].w);
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      float v = sh == s ? q : 0.0f, av = sh == s ? fabsf(q) : 0.0f;
-#pragma unroll
-      for (int o = 1; o < kFeatL; o <<= 1) {
-        v += __shfl_xor_sync(gmask, v, o);
-        av += __shfl_xor_sync(gmask, av, o);
-      }
-      if (s == lane) {
-        qs += v;
-        aqs += av;
+      if (sh == s) {
+        qs[s] += q;
+        aqs[s] += fabsf(q);
       }
     }
   }
+  // lane s ends with shell s's sums (the same tree for every shell)
+  float myq = 0.0f, myaq = 0.0f;
 #pragma unroll
-  for (int i = 0; i < 7; ++i) f[i * 8 + lane] = cnt[i] * 0.125f;
-  f[56 + lane] = qs;
-  f[64 + lane] = aqs;
+  for (int s = 0; s < 8; ++s) {
+    float v = qs[s], av = aqs[s];
+#pragma unroll
+    for (int o = 1; o < kFeatL; o <<= 1) {
+      v += __shfl_xor_sync(gmask, v, o);
+      av += __shfl_xor_sync(gmask, av, o);
+    }
+    if (s == lane) {
+      myq = v;
+      myaq = av;
+    }
+  }
+  __syncwarp(gmask);
+#pragma unroll
+  for (int i = 0; i < 7; ++i) f[i * 8 + lane] = (float)hist[i * 8 + lane] * 0.125f;
+  f[56 + lane] = myq;
+  f[64 + lane] = myaq;
   // torsions: lane j writes slots j and j + 8
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
