@@ -352,7 +352,7 @@ int dock_batch_noalloc(dock_pocket *pocket, dock_ligands *ligands, const dock_se
                        dock_result *results, void *stream);
 
 /* ------------------------------------------------------------------------ */
-/* Learned pre-screen (not in the paper: the build's surrogate configuration) */
+/* Learned pre-screen (not in the paper: an MLP surrogate of the exact score) */
 /* ------------------------------------------------------------------------ */
 /* Per-pose features (128 values, BF16, row-major [pose][128]):
  *   [0, 56)    atom counts / 8 per (type t < 7, radial shell s < 8) around the

@@ -1,10 +1,10 @@
 /*
  * Plain FP64 oracle of the learned surrogate that pre-screens candidate
- * poses (the build's configuration 4: an MLP 128 -> 256 -> 256 -> 256 -> 1
- * with GELU on per-pose features, trained on (features, exact score) pairs).
+ * poses: an MLP 128 -> 256 -> 256 -> 256 -> 1 with GELU on per-pose
+ * features, trained on (features, exact score) pairs.
  *
  * TEST INFRASTRUCTURE ONLY (see oracle.c). The paper itself has no learned
- * component; what these functions compute is fixed by that configuration:
+ * component; these functions compute the surrogate as designed here:
  *
  * Features of one posed ligand (128 values, in this order):
  *   [0, 56)    atom counts / 8 per (type t < 7, radial shell s < 8) around the
