@@ -55,12 +55,18 @@ def _oracle(setup, l, genos):
     return np.array(score), np.array(margin)
 
 
-@pytest.mark.parametrize("lanes", [0, 8, 2])
+@pytest.mark.parametrize("lanes", [0, 8, 2, "tuned"])
 def test_nogrid_search_replay(dock, setup, lanes):
     """lanes 0: lanes per pose picked by ligand size (several launch groups);
-    8 and 2: every ligand forced to that many lanes per pose."""
+    8 and 2: every ligand forced to that many lanes per pose; tuned: the
+    launch shape dock_autotune picks for the no-grid search."""
     ligs, gl, pocket = setup["ligs"], setup["gl"], setup["pocket"]
     nl, pop, gens, seed = ligs.n_ligands, 48, 4, 3
+    if lanes == "tuned":
+        tune = dock.dock_autotune(pocket, gl, pop, 2, stream=torch.cuda.current_stream(),
+                                  inter=dock.DOCK_INTER_PAIRWISE)
+        assert len(tune["table"]) >= 2 and 0 <= tune["best"] < len(tune["table"])
+        lanes = 0
     goff = gl.geno_offsets(pop)
     tot = int(goff[-1])
     tg = torch.zeros(gens * tot, dtype=torch.float32, device="cuda")
