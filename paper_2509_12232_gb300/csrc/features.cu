@@ -13,6 +13,9 @@ constexpr int kFeatL = 8;         // lanes per pose
 constexpr int kFeatThreads = 128;
 constexpr int kFeatSlots = kFeatThreads / kFeatL;
 constexpr int kFeatApl = DOCK_MAX_ATOMS / kFeatL;
+// shared feature rows kFeatRow floats apart: the rows of the four poses of a
+// warp start 8 banks apart, so a warp's lane-indexed writes do not collide
+constexpr int kFeatRow = DOCK_N_FEATURES + 8;
 
 __device__ __forceinline__ float sel16(const float (&g)[DOCK_MAX_GENES], int j) {
   float v = 0.0f;
@@ -129,7 +132,7 @@ struct FeatArgs {
 template <bool FROM_GA>
 __global__ void __launch_bounds__(kFeatThreads) feat_kernel(const FeatArgs A) {
   __shared__ float4 s_col[slots_bytes(kFeatThreads, kFeatL, kFeatApl) / 16];
-  __shared__ float s_f[kFeatSlots][DOCK_N_FEATURES];
+  __shared__ __align__(16) float s_f[kFeatSlots][kFeatRow];
   const int lane = threadIdx.x & (kFeatL - 1), slot = threadIdx.x / kFeatL;
   int lig;
   int64_t row;
@@ -175,16 +178,18 @@ __global__ void __launch_bounds__(kFeatThreads) feat_kernel(const FeatArgs A) {
   float *f = s_f[slot];
   pose_features(g, V, sl, lane, gmask, A.cx, A.cy, A.cz, A.radius, f);
   __syncwarp(gmask);
-  // 128 values -> BF16, 16 per lane (two 16-byte stores)
-  __nv_bfloat16 *out = A.features + row * DOCK_N_FEATURES + lane * 16;
-  uint32_t w[8];
+  // 128 values -> BF16: lane l converts the four-value chunks l + 8 m (one
+  // 16-byte shared read each, the group's eight reads on distinct banks) and
+  // stores them as 8-byte pieces (64 contiguous bytes per group and m)
+  __nv_bfloat16 *out = A.features + row * DOCK_N_FEATURES;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(f[lane * 16 + 2 * i], f[lane * 16 + 2 * i + 1]);
-    w[i] = *reinterpret_cast<const uint32_t *>(&h);
+  for (int m = 0; m < 4; ++m) {
+    const int c = lane + 8 * m;
+    const float4 v = *reinterpret_cast<const float4 *>(f + 4 * c);
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(v.x, v.y), h1 = __floats2bfloat162_rn(v.z, v.w);
+    reinterpret_cast<uint2 *>(out)[c] = make_uint2(*reinterpret_cast<const uint32_t *>(&h0),
+                                                   *reinterpret_cast<const uint32_t *>(&h1));
   }
-  reinterpret_cast<uint4 *>(out)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-  reinterpret_cast<uint4 *>(out)[1] = make_uint4(w[4], w[5], w[6], w[7]);
   if (!FROM_GA && A.scores) {
     const float sc = score_posed<kFeatL>(V, A.grid, sl, lane, gmask, nullptr);
     if (lane == 0) A.scores[row] = sc;
