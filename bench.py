@@ -88,6 +88,43 @@ def src_hash():
     return h.hexdigest()[:16]
 
 
+def read_profile():
+    """key = value pairs of the committed ncu summary of one search generation
+    (the search-kernel launches of one generation, one per lanes-per-pose
+    group), if it was taken on the current kernel source, else None."""
+    p = os.path.join(ROOT, "profiles", "search_kernel_c2.txt")
+    if not os.path.exists(p):
+        return None
+    kv, sect = {}, ""
+    for line in open(p):
+        line = line.strip()
+        if line.startswith("[") and line.endswith("]"):
+            sect = line[1:-1] + "."
+        elif "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[sect + k.strip()] = v.strip()
+    return kv if kv.get("source_hash") == src_hash() else None
+
+
+def read_issue(per_gen_s, n_sm, sm_mhz):
+    """Warp instructions of one generation (ncu summary) over its measured
+    time, against the SMs' issue rate (4 schedulers x 1 warp instruction per
+    cycle); None when the summary is not of the current source."""
+    kv = read_profile()
+    if kv is None:
+        return None
+    try:
+        inst = sum(float(v) for k, v in kv.items() if k.endswith(".warp_instructions"))
+    except ValueError:
+        return None
+    peak = n_sm * 4 * sm_mhz * 1e6 / 1e9
+    ach = inst / per_gen_s / 1e9
+    return {"achieved": round(ach, 1), "peak": round(peak, 1), "unit": "G warp instructions/s",
+            "frac": round(ach / peak, 4),
+            "source": "ncu warp instructions per generation (profiles/search_kernel_c2.txt) / "
+                      "measured generation time"}
+
+
 def read_traffic():
     """DRAM bytes per search generation (the search-kernel launches of one
     generation, one per lanes-per-pose group) from the committed ncu summary,
@@ -797,6 +834,8 @@ def main():
             "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
             "mufu": {"achieved": round(ach_mufu, 4), "peak": round(mufu_peak, 4), "unit": "Tops/s",
                      "frac": round(ach_mufu / mufu_peak, 4)},
+            "issue": None if (lga or nogrid or WORKLOAD != "c2") else read_issue(per_gen_s, n_sm,
+                                                                                 sm_mhz),
             "generation_ms": round(per_gen_s * 1000, 4), "generations_timed": n_launch,
             "launches_per_generation": len(groups), "lanes_per_pose_groups": groups}
     metric = METRIC_LGA if lga else METRIC_NOGRID if nogrid else METRIC
