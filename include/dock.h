@@ -222,6 +222,19 @@ typedef struct {
                                     every protein atom within the cutoff, no
                                     maps (plain GA only; the best 8 are
                                     rescored with the FP64 pairwise sum)        */
+  const float *resume_genotypes; /* optional device: a saved population, that of
+                                    generation resume_from, in the layout of one
+                                    generation of trace_genotypes; the search
+                                    then runs generations resume_from + 1 ..
+                                    generations - 1 only, bit-identical to the
+                                    search that saved it (the GA's random
+                                    numbers depend on seed, ligand, generation
+                                    and individual alone; the trace arrays get
+                                    the generations run). Plain GA without local
+                                    search; NULL = start from generation 0      */
+  const float *resume_scores;    /* device [n_ligands*pop]: that population's
+                                    FP32 scores (trace_scores of the generation) */
+  int32_t resume_from;           /* 0 .. generations - 2 (with resume_genotypes) */
 } dock_search_params;
 
 #define DOCK_INTER_GRID 0

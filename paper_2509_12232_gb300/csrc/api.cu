@@ -737,6 +737,11 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   const bool pairwise = sp->inter == DOCK_INTER_PAIRWISE;
   if (pairwise && (sur || sp->ls.rate != 0.0f))
     return fail(DOCK_EINVAL, "dock_batch: the pairwise inter-energy needs the plain GA");
+  const bool resume = sp->resume_genotypes != nullptr;
+  if (resume && (sur || sp->ls.rate != 0.0f || !sp->resume_scores || sp->resume_from < 0 ||
+                 sp->resume_from > sp->generations - 2))
+    return fail(DOCK_EINVAL, "dock_batch: resume needs the plain GA without local search, "
+                             "scores, and 0 <= resume_from <= generations - 2");
   const int forced = sp->lanes_per_pose;
   if (forced != 0 && forced != 1 && forced != 2 && forced != 4 && forced != 8)
     return fail(DOCK_EINVAL, "dock_batch: lanes_per_pose %d", forced);
@@ -1106,6 +1111,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     return DOCK_OK;
   };
 
+  const int g_first = resume ? sp->resume_from + 1 : 0;  // first generation this call runs
   auto enqueue = [&](cudaStream_t q) -> int {
     CU(cudaMemsetAsync(W.counters, 0, sizeof(uint32_t) * gens * 8, q));
     if (lamarck) {
@@ -1119,7 +1125,18 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     CU(cudaMemsetAsync(W.status, 0, sizeof(int32_t), q));
     CU(cudaMemsetAsync(W.lig_status, 0, sizeof(int32_t) * (size_t)nl, q));
     if (sp->timeout_ns) CU(launch_set_deadline(W.deadline, sp->timeout_ns, q));
-    for (int g = 0; g < gens; ++g) {
+    if (resume) {
+      // the saved generation becomes the previous one of the first generation run
+      const int g = sp->resume_from;
+      if (total_genes)
+        CU(cudaMemcpyAsync(W.geno[g & 1], sp->resume_genotypes, sizeof(float) * total_genes,
+                           cudaMemcpyDeviceToDevice, q));
+      if (n_scores)
+        CU(cudaMemcpyAsync(W.score[g & 1], sp->resume_scores, sizeof(float) * n_scores,
+                           cudaMemcpyDeviceToDevice, q));
+      CU(launch_best_keys(W.score[g & 1], nl, pop, W.best + (size_t)g * nl, q));
+    }
+    for (int g = g_first; g < gens; ++g) {
       SearchArgs a = A;
       a.gen = g;
       a.counter = W.counters + (size_t)g * 8;  // 4 search + 4 local-search queues
@@ -1158,7 +1175,8 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     }
     CU(launch_finalize_impl(F, L->d_centroid, nl, pop, W.geno_off, W.geno[(gens - 1) & 1],
                             W.score[(gens - 1) & 1], W.lig_status, W.status,
-                            sur ? (uint64_t)pop + (uint64_t)(gens - 1) * K : (uint64_t)pop * gens,
+                            sur ? (uint64_t)pop + (uint64_t)(gens - 1) * K
+                                : (uint64_t)pop * (uint64_t)(gens - g_first),
                             sur ? (uint64_t)(gens - 1) * C : 0, lamarck ? W.ls_evals : nullptr,
                             P->ox, P->oy, P->oz, W.results, q));
     return DOCK_OK;
@@ -1181,6 +1199,9 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     put(&sp->ls, sizeof sp->ls);
     put(&sp->trace_ls, sizeof(void *));
     put(&sp->inter, sizeof sp->inter);
+    put(&sp->resume_genotypes, sizeof(void *));
+    put(&sp->resume_scores, sizeof(void *));
+    put(&g_first, sizeof g_first);
     const void *bufs[11] = {W.geno[0], W.geno[1], W.score[0], W.score[1], W.best, W.results,
                             W.ls_evals, W.ls_bits, W.ls_count, W.ls_chain, W.ls_units};
     put(bufs, sizeof bufs);

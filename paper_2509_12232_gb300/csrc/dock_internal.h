@@ -260,6 +260,11 @@ cudaError_t launch_intra_const(LigInfo *ligs, int n_ligands, const float4 *atoms
 cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, int L, cudaStream_t s,
                           bool pairwise = false);
 cudaError_t launch_score(const ScoreArgs &a, cudaStream_t s);
+// Best key ((score key << 32) | index, the search kernel's atomicMin key) of
+// each ligand's population scores [n_ligands][pop]: a resumed search's
+// elitism reads it for the saved generation.
+cudaError_t launch_best_keys(const float *scores, int n_ligands, int pop,
+                             unsigned long long *best, cudaStream_t s);
 cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int n_ligands, int pop,
                                  const int64_t *geno_off, const float *genos, const float *scores,
                                  const int32_t *lig_status, const int32_t *status,

@@ -70,6 +70,8 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
     return fail(DOCK_EINVAL, "dock_batch_noalloc: probabilities out of [0, 1]");
   if (sp->mode != DOCK_MODE_PLAIN)
     return fail(DOCK_EINVAL, "dock_batch_noalloc: only the plain search (mode 0)");
+  if (sp->resume_genotypes != nullptr)
+    return fail(DOCK_EINVAL, "dock_batch_noalloc: no resume (resume_genotypes must be NULL)");
   if (sp->ls.rate != 0.0f)
     return fail(DOCK_EINVAL, "dock_batch_noalloc: no local search (ls.rate must be 0)");
   if (sp->inter != DOCK_INTER_GRID)

@@ -320,6 +320,32 @@ __global__ void __launch_bounds__(256) finalize_kernel(const FinalArgs A) {
   }
 }
 
+// One warp per ligand: the minimum of (score key << 32) | index.
+__global__ void best_keys_kernel(const float *scores, int n_ligands, int pop,
+                                 unsigned long long *best) {
+  const int lig = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  if (lig >= n_ligands) return;  // whole warps
+  const int lane = threadIdx.x & 31;
+  const float *sc = scores + (int64_t)lig * pop;
+  unsigned long long k = ~0ull;
+  for (int i = lane; i < pop; i += 32) {
+    const unsigned long long c = ((unsigned long long)score_key(sc[i]) << 32) | (uint32_t)i;
+    k = c < k ? c : k;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long c = __shfl_xor_sync(0xffffffffu, k, o);
+    k = c < k ? c : k;
+  }
+  if (lane == 0) best[lig] = k;
+}
+
+cudaError_t launch_best_keys(const float *scores, int n_ligands, int pop,
+                             unsigned long long *best, cudaStream_t s) {
+  if (n_ligands == 0) return cudaSuccess;
+  best_keys_kernel<<<(n_ligands + 7) / 8, 256, 0, s>>>(scores, n_ligands, pop, best);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_finalize_impl(const Fp64Args &f, const double *centroids, int n_ligands, int pop,
                                  const int64_t *geno_off, const float *genos, const float *scores,
                                  const int32_t *lig_status, const int32_t *status,

@@ -70,7 +70,8 @@ class dock_search_params(C.Structure):
                 ("trace_genotypes", C.c_void_p), ("trace_scores", C.c_void_p),
                 ("mode", C.c_int32), ("candidates", C.c_int32), ("keep", C.c_int32),
                 ("surrogate", C.c_void_p), ("ls", dock_ls_params), ("trace_ls", C.c_void_p),
-                ("inter", C.c_int32)]
+                ("inter", C.c_int32), ("resume_genotypes", C.c_void_p),
+                ("resume_scores", C.c_void_p), ("resume_from", C.c_int32)]
 
 
 DOCK_INTER_GRID, DOCK_INTER_PAIRWISE = 0, 1
@@ -317,18 +318,21 @@ def dock_ligands_info(ligands: Ligands) -> dict:
 def dock_batch(pocket: Pocket, ligands: Ligands, pop: int, generations: int, p_cross=0.8,
                p_mut=0.02, seed=0, lanes_per_pose=0, use_graph=1, timeout_ns=0,
                trace_genotypes=None, trace_scores=None, stream=None, surrogate=None,
-               candidates=0, keep=0, ls=None, trace_ls=None, inter=0) -> Job:
+               candidates=0, keep=0, ls=None, trace_ls=None, inter=0, resume=None) -> Job:
     """Plain search, or the surrogate pre-screened search when `surrogate` is
     given (`candidates` children per ligand and generation, `keep` of them
     scored exactly). `ls` (a dock_ls_params, e.g. ls_params()) with a rate
     > 0 makes the plain search Lamarckian (Solis-Wets refinement). inter =
-    DOCK_INTER_PAIRWISE scores with the pairwise inter-energy (no maps)."""
+    DOCK_INTER_PAIRWISE scores with the pairwise inter-energy (no maps).
+    resume = (genotypes, scores, generation): continue a plain search from a
+    saved generation (device tensors in the trace layout of one generation)."""
     mode = DOCK_MODE_SURROGATE if surrogate is not None else DOCK_MODE_PLAIN
+    rg, rs, rf = (None, None, 0) if resume is None else resume
     sp = dock_search_params(pop, generations, p_cross, p_mut, seed, lanes_per_pose, use_graph,
                             timeout_ns, _dptr(trace_genotypes), _dptr(trace_scores), mode,
                             candidates, keep, surrogate.handle if surrogate is not None else None,
                             ls if ls is not None else dock_ls_params(*NO_LS), _dptr(trace_ls),
-                            inter)
+                            inter, _dptr(rg), _dptr(rs), rf)
     h = C.c_void_p()
     check(lib().dock_batch(pocket.handle, ligands.handle, C.byref(sp), _stream(stream), C.byref(h)))
     return Job(h, ligands.n_ligands, keep=(pocket, ligands, surrogate))

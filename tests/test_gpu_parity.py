@@ -222,6 +222,49 @@ def test_edge_ligands_ragged_population(dock, c1):
     _replay(dock, side, gl, c1["pocket"], pop=2, gens=2, seed=12)
 
 
+@pytest.mark.parametrize("use_graph", [0, 1])
+def test_resume_from_saved_generation_is_bit_exact(dock, c1, use_graph):
+    """A search resumed from a saved generation (its genotypes and scores, as
+    traced) runs the remaining generations bit-identically to the search that
+    saved it: the GA's random numbers depend on (seed, ligand, generation,
+    individual) alone, and elitism reads the saved generation's best."""
+    rng = np.random.Generator(np.random.Philox(31))
+    ligs = synth.make_ligands(rng, [24, 11, 37], [4, 2, 6], id_base=500)
+    gl = gpu_ligands(dock, c1["pocket"], ligs)
+    nl, pop, gens, seed, r = ligs.n_ligands, 96, 7, 11, 3
+    tot = int(gl.geno_offsets(pop)[-1])
+    stream = torch.cuda.current_stream()
+    tg = torch.zeros(gens * tot, dtype=torch.float32, device="cuda")
+    ts = torch.zeros(gens * nl * pop, dtype=torch.float32, device="cuda")
+    full = dock.dock_results(dock.dock_batch(c1["pocket"], gl, pop, gens, seed=seed,
+                                             use_graph=use_graph, trace_genotypes=tg,
+                                             trace_scores=ts, stream=stream, **SEARCH))
+    saved = (tg[r * tot:(r + 1) * tot].clone(), ts[r * nl * pop:(r + 1) * nl * pop].clone(), r)
+    tg2 = torch.full_like(tg, float("nan"))
+    ts2 = torch.full_like(ts, float("nan"))
+    res = dock.dock_results(dock.dock_batch(c1["pocket"], gl, pop, gens, seed=seed,
+                                            use_graph=use_graph, trace_genotypes=tg2,
+                                            trace_scores=ts2, stream=stream, resume=saved,
+                                            **SEARCH))
+    a, b = tg.cpu().numpy(), tg2.cpu().numpy()
+    np.testing.assert_array_equal(a[(r + 1) * tot:].view(np.uint32),
+                                  b[(r + 1) * tot:].view(np.uint32))
+    assert np.isnan(b[:(r + 1) * tot]).all()  # generations not run are not written
+    a, b = ts.cpu().numpy(), ts2.cpu().numpy()
+    np.testing.assert_array_equal(a[(r + 1) * nl * pop:].view(np.uint32),
+                                  b[(r + 1) * nl * pop:].view(np.uint32))
+    for f in ("ligand_id", "best_index", "best_fp32", "best_fp64", "genotype", "n_genes", "status"):
+        np.testing.assert_array_equal(res[f], full[f], err_msg=f)
+    assert np.all(res["exact_evals"] == pop * (gens - r - 1))
+    # a saved generation must leave at least one generation to run
+    with pytest.raises(dock.DockError):
+        dock.dock_batch(c1["pocket"], gl, pop, gens, seed=seed, stream=stream,
+                        resume=(saved[0], saved[1], gens - 1))
+    with pytest.raises(dock.DockError):
+        dock.dock_batch(c1["pocket"], gl, pop, gens, seed=seed, stream=stream, resume=saved,
+                        ls=dock.ls_params(rate=0.1))
+
+
 def test_empty_batch(dock, c1):
     ligs = synth.make_ligands(np.random.default_rng(0), [], [])
     gl = gpu_ligands(dock, c1["pocket"], ligs)
