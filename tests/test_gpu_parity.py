@@ -59,6 +59,24 @@ def test_grid_maps_match_oracle(dock, c1):
     assert np.all(maps[..., 3] == 0)
 
 
+@pytest.mark.parametrize("cfg", ["c2", "c5"])
+def test_grid_maps_match_oracle_full_pockets(dock, cfg):
+    """Every node of the c2 pocket's maps (4,000 atoms, 86^3 nodes) and the
+    c5 pocket's (10,000 atoms, 107^3) against the oracle's FP64 maps."""
+    pk, _, _ = synth.make_workload(cfg, n_ligands=1)
+    pocket = gpu_pocket(dock, pk)
+    g = o.grid_build(o.pocket_from(pk), o.Params(synth.TYPE_PARAMS))
+    n, origin, ptr = pocket.grid()
+    assert (n, n, n) == g.n
+    np.testing.assert_allclose(origin, g.origin, atol=1e-5)
+    T = synth.N_TYPES
+    maps = d2h(ptr, T * n ** 3 * 4, np.float32).reshape(T, n, n, n, 4)
+    for t in range(T):
+        assert np.all(within(maps[t, ..., 0], g.maps[t], rel=1e-6, abs_=1e-6)), t
+    assert np.all(within(maps[0, ..., 1], g.maps[T], rel=1e-6, abs_=1e-6))
+    assert np.all(within(maps[0, ..., 2], g.maps[T + 1], rel=1e-6, abs_=1e-6))
+
+
 def _pose_set(k, n_poses, seed):
     g = np.concatenate([o.ga_init(k, 256, 12.0, seed + s, 77) for s in range((n_poses + 255) // 256)])
     g = g[:n_poses]
