@@ -333,3 +333,103 @@ def test_five_atom_chain_single_pair():
         r = np.linalg.norm(xyz[0] - xyz[4])
         e = o.pair_terms(P, 0, 6, np.float32(0.3), np.float32(-0.2), r)[3]
         assert o.intra(lig, P, xyz)[0] == pytest.approx(e, rel=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Energies worked by hand from the published constants
+# ---------------------------------------------------------------------------
+# Constants (AutoDock4 free-energy function): W_vdw 0.1662, W_hb 0.1209,
+# W_elec 0.1406, Coulomb 332.06363, W_sol 0.1322, charge factor 0.01097,
+# sigma 3.6 A; Mehler-Solmajer eps(r) = A + B / (1 + k exp(-lambda B r)) with
+# A = -8.5525, B = 78.4 - A = 86.9525, k = 7.7839, lambda = 0.003627.
+# Type parameters as the table stores them (float32): C  R 4.0, eps 0.15,
+# V 33.51, solpar -0.00143; N  R 3.5, eps 0.16, V 22.45, solpar -0.00162;
+# OA R 3.2, eps 0.2, V 17.16, solpar -0.00251, acceptor (R_hb 2.8,
+# eps_hb 5.0); ND R 3.5, eps 0.16, V 22.45, solpar -0.00162, donor.
+# The expected values below were worked out with a calculator from these
+# numbers alone; a wrong weight, Coulomb constant, dielectric constant,
+# Gaussian width or charge factor moves them far outside the tolerance.
+HAND_REL = 1e-9
+
+# C (q = +0.3) - OA (q = -0.2). At r = 3.0:
+#   R = (4.0 + 3.2) / 2 = 3.6, eps = sqrt(0.15 * 0.2) = 0.173205085
+#   (R/r)^6 = 1.2^6 = 2.985984, (R/r)^12 = 8.916101
+#   vdW   = 0.1662 * 0.173205085 * (8.916101 - 2 * 2.985984)      =  0.0847518276
+#   eps(3.0) = -8.5525 + 86.9525 / (1 + 7.7839 e^(-0.94611)) = 13.0665815
+#   elec  = 0.1406 * 332.06363 * 0.3 * (-0.2) / (13.0665815 * 3.0)  = -0.0714619142
+#   S_C = -0.00143 + 0.01097 * 0.3 = 0.001861, S_OA = -0.00251 + 0.01097 * 0.2 = -0.000316
+#   desol = 0.1322 * (0.001861 * 17.16 - 0.000316 * 33.51) * e^(-9 / 25.92) = 0.00199408257
+# r = 4.5 and 7.5 the same way (eps(4.5) = 21.6080016, eps(7.5) = 41.6784561).
+HAND_C_OA = {
+    3.0: (0.0847518275659137, -0.07146191420970993, 0.0019940825682854693),
+    4.5: (-0.013114308112479827, -0.028809171270011997, 0.001291954646314351),
+    7.5: (-0.0006998502190770031, -0.008961588449148133, 0.0003221517446985739),
+}
+# ND (donor, q = -0.1) - OA (acceptor, q = +0.25): the 12-10 form with the
+# acceptor's R_hb = 2.8 and eps_hb = 5.0 in place of 12-6, weight W_hb:
+#   r = 2.8 (the well): 0.1209 * (5 * 5 - 6 * 5) = -0.6045
+#   r = 3.5: 0.1209 * (25 * 0.8^12 - 30 * 0.8^10) = -0.181741517
+HAND_ND_OA = {
+    2.8: (-0.6044999999999897, -0.034570216107120175, -0.00036684879328593946),
+    3.5: (-0.18174151725421814, -0.021203327309545793, -0.0003094544371384055),
+}
+
+
+@pytest.mark.parametrize("r", sorted(HAND_C_OA))
+def test_hand_worked_pair_energies_c_oa(r):
+    t = o.pair_terms(P, 0, 4, 0.3, -0.2, r)
+    vdw, el, ds = HAND_C_OA[r]
+    assert t[0] == pytest.approx(vdw, rel=HAND_REL)
+    assert t[1] == pytest.approx(el, rel=HAND_REL)
+    assert t[2] == pytest.approx(ds, rel=HAND_REL)
+    assert t[3] == pytest.approx(vdw + el + ds, rel=HAND_REL)
+
+
+@pytest.mark.parametrize("r", sorted(HAND_ND_OA))
+def test_hand_worked_pair_energies_hbond(r):
+    vdw, el, ds = HAND_ND_OA[r]
+    for ti, tj, qi, qj in ((6, 4, -0.1, 0.25), (4, 6, 0.25, -0.1)):  # either order
+        t = o.pair_terms(P, ti, tj, np.float32(qi), np.float32(qj), r)
+        assert t[0] == pytest.approx(vdw, rel=HAND_REL)
+        assert t[1] == pytest.approx(el, rel=1e-7)   # charges rounded to float32
+        assert t[2] == pytest.approx(ds, rel=1e-7)
+
+
+def test_hand_worked_cap():
+    """C-C at r = 1.0: the raw 12-6 value 0.15 (4^12 - 2 * 4^6) = 2,515,353.6
+    is above the 1e5 cap, so the term is 0.1662 * 1e5 = 16,620."""
+    t = o.pair_terms(P, 0, 0, np.float32(0.1), np.float32(0.1), 1.0)
+    assert o.disp_raw(P, 0, 0, 1.0) == pytest.approx(2515353.6, rel=1e-7)
+    assert t[0] == pytest.approx(16620.0, rel=1e-12)
+    assert t[1] == pytest.approx(0.10451006276147873, rel=1e-7)
+    assert t[2] == pytest.approx(-0.0028387348615425963, rel=1e-7)
+
+
+def test_hand_worked_three_atom_ligand_with_one_torsion():
+    """A 3-atom chain C-OA-ND with the bond 0-1 rotatable, posed by hand.
+
+    Input atoms (0, 0, 0), (1.5, 0, 0), (3, 1.5, 0), centroid (1.5, 0.5, 0).
+    Genotype: t = (1, 2, -0.5), q = (1, 0, 0, 1) (90 degrees about z after
+    normalising: (x, y, z) -> (-y, x, z)), theta = pi/2, pocket centre 0.
+    Rigid motion: R (x - c) + t gives (1.5, 0.5, -0.5), (1.5, 2, -0.5),
+    (0, 3.5, -0.5). The torsion turns atom 2 by +90 degrees about the axis
+    0 -> 1 (+y, right hand: (x, y, z) -> (z, y, -x) relative to atom 0):
+    (-1.5, 3, 0) -> (0, 3, 1.5), so atom 2 ends at (1.5, 3.5, 1.0).
+    Intra: no pair is more than three bonds apart, so 0.
+    Inter against an OA (q -0.4) at (1.5, 3.5, 4) and an N (q 0.3) at
+    (-3, 0.5, -0.5); distances and pair sums (vdW/H-bond + elec + desolv):
+      C -OA 5.408327: -0.0266800741583   C -N 4.5:      0.0188785676229
+      OA-OA 4.743416:  0.0476088909293   OA-N 4.743416: -0.0426424907423
+      ND-OA 3.0 (12-10, H-bond): -0.54317659352   ND-N 5.612486: 0.00662980631573
+    total -0.539381893553."""
+    lig = o.Ligand(x=[0.0, 1.5, 3.0], y=[0.0, 0.0, 1.5], z=[0.0] * 3, q=[0.2, -0.3, 0.1],
+                   type=[0, 4, 6], parent=[-1, 0, 1], tors_b=[1])
+    theta = np.float32(np.pi / 2)   # float32: cos(theta) = -4.4e-8
+    xyz = o.pose(lig, [1.0, 2.0, -0.5, 1.0, 0.0, 0.0, 1.0, theta], [0.0, 0.0, 0.0])
+    np.testing.assert_allclose(xyz, [[1.5, 0.5, -0.5], [1.5, 2.0, -0.5], [1.5, 3.5, 1.0]],
+                               atol=1e-6)
+    assert o.intra(lig, P, xyz)[0] == 0.0
+    pk = o.PocketS([1.5, -3.0], [3.5, 0.5], [4.0, -0.5], [-0.4, 0.3], [4, 2], (0, 0, 0), 10.0)
+    exact = np.array([[1.5, 0.5, -0.5], [1.5, 2.0, -0.5], [1.5, 3.5, 1.0]])
+    assert o.inter_pairwise(lig, P, pk, exact) == pytest.approx(-0.539381893552913, rel=1e-9)
+    assert o.inter_pairwise(lig, P, pk, xyz) == pytest.approx(-0.539381893552913, rel=1e-6)

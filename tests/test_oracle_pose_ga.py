@@ -324,3 +324,51 @@ def test_free_run_best_never_worsens():
     r5 = o.dock_batch(ligs, P, pks, grid, pop=64, generations=6, seed=0)
     assert r5["best64"][0, 0] <= r1["best64"][0, 0] + 1e-9
     assert np.all(np.diff(r5["best64"][0]) >= -1e-6)    # best 8 sorted by FP32 score
+
+
+def test_ga_mutation_scale_per_gene_class():
+    """Every gene mutated (p_mut = 1), no crossover, all parents equal: each
+    child's change is sigma z with z ~ N(0, 1) (Irwin-Hall), sigma = 1 A for the
+    translation, 0.1 for each quaternion component and 0.5 rad for a torsion.
+    The quaternion is renormalised after its step: from the identity parent
+    (1, 0, 0, 0), component i of the child over component 0 is
+    0.1 z_i / (1 + 0.1 z_0), whose standard deviation is 0.1 (1 + 0.03)^(1/2)
+    to second order. Scales of 0.5, 2 or 0.05 times the right one fail."""
+    k, pop = 6, 4096
+    parent = np.zeros(7 + k, np.float32)
+    parent[3] = 1.0
+    parent[7:] = 0.25
+    prev = np.tile(parent, (pop, 1))
+    nxt = o.ga_step(k, pop, 0.0, 1.0, 21, 9, 3, prev, np.zeros(pop, np.float32))
+    child = nxt[1:].astype(np.float64)
+    dt = child[:, :3].ravel()
+    assert np.std(dt) == pytest.approx(1.0, rel=0.03)
+    assert abs(np.mean(dt)) < 0.05
+    ratio = (child[:, 4:7] / child[:, 3:4]).ravel()
+    assert np.std(ratio) == pytest.approx(0.1 * math.sqrt(1.03), rel=0.03)
+    norms = np.linalg.norm(child[:, 3:7], axis=1)
+    np.testing.assert_allclose(norms, 1.0, atol=1e-6)
+    # parent torsions 0.25, steps at most 0.5 * 6 = 3 < pi: no wrap happens
+    dth = (child[:, 7:] - 0.25).ravel()
+    assert np.std(dth) == pytest.approx(0.5, rel=0.03)
+    assert np.max(np.abs(dth)) <= 3.0 + 1e-6
+    # elitism keeps individual 0 unchanged
+    np.testing.assert_array_equal(nxt[0], parent)
+
+
+def test_ga_torsion_wrap():
+    """A torsion pushed past pi comes back by one turn of 2 pi_f."""
+    k, pop = 2, 2048
+    parent = np.zeros(9, np.float32)
+    parent[3] = 1.0
+    parent[7:] = np.float32(3.0)
+    prev = np.tile(parent, (pop, 1))
+    nxt = o.ga_step(k, pop, 0.0, 1.0, 5, 1, 1, prev, np.zeros(pop, np.float32))
+    th = nxt[1:, 7:].astype(np.float64).ravel()
+    assert np.all(th >= -np.pi - 1e-6) and np.all(th <= np.pi + 1e-6)
+    wrapped = th < 0
+    # P(3 + 0.5 z > pi) = P(z > 0.2832) = erfc(0.2832 / sqrt 2) / 2 = 0.3885
+    assert wrapped.mean() == pytest.approx(0.5 * math.erfc((math.pi - 3.0) / (0.5 * math.sqrt(2))),
+                                           abs=0.03)
+    # a wrapped value is the unwrapped one minus 2 pi: it sits just above -pi
+    assert np.all(th[wrapped] < -np.pi + 3.0)
