@@ -405,7 +405,12 @@ typedef struct {
   float lr;            /* Adam learning rate (1e-3); beta 0.9 / 0.999, eps 1e-8 */
   float score_clip;    /* targets are min(score, clip), standardised by their
                           mean and standard deviation over the training set    */
-  uint64_t seed;       /* order of the rows                                   */
+  uint64_t seed;       /* order of the rows: batch position r visits row
+                          pi(r), pi a bijection of [0, n) keyed by seed (a
+                          four-round Feistel network on 2h-bit words, 4^h >= n,
+                          round function the SplitMix64 mix of R xor
+                          mix(seed + (i + 1) 0x9E3779B97F4A7C15) mod 2^h,
+                          cycle-walked into [0, n)); the same every epoch     */
 } dock_train_params;
 
 /* Creates a network with He-normal weights drawn from seed and zero biases. */
@@ -428,8 +433,10 @@ int dock_surrogate_predict(dock_surrogate *surrogate, const uint16_t *features, 
 int dock_surrogate_gradients(dock_surrogate *surrogate, const uint16_t *features,
                              const float *targets, int32_t n, float *grad, float *loss,
                              void *stream);
-/* Trains with Adam on (features [n][128] BF16, exact scores [n]) device
- * arrays; loss_per_epoch (host, optional, [epochs]) gets the loss of each
+/* Trains with Adam (Kingma & Ba 2015: m, v with bias correction by step
+ * count t from 1; FP32 masters, moments and update) on (features [n][128]
+ * BF16, exact scores [n]) device arrays, one step per batch of the row order
+ * above; loss_per_epoch (host, optional, [epochs]) gets the loss of each
  * epoch's last batch in standardised units. Waits for the stream. */
 int dock_surrogate_train(dock_surrogate *surrogate, const uint16_t *features,
                          const float *scores, int64_t n, const dock_train_params *params,

@@ -57,6 +57,7 @@ P_u8 = C.POINTER(C.c_uint8)
 P_i16 = C.POINTER(C.c_int16)
 P_i32 = C.POINTER(C.c_int32)
 P_u64 = C.POINTER(C.c_uint64)
+P_i64 = C.POINTER(C.c_int64)
 
 
 class OrcParams(C.Structure):
@@ -172,6 +173,11 @@ def _declare_surrogate(L):
     L.orc_mlp_backward.argtypes = [P_d, C.c_int, P_d, P_d, P_d]
     L.orc_mlp_n_params.restype = C.c_int
     L.orc_mlp_n_params.argtypes = []
+    L.orc_adam_step.restype = None
+    L.orc_adam_step.argtypes = [P_d, P_d, P_d, P_d, C.c_int64, C.c_double, C.c_double, C.c_double,
+                                C.c_double, C.c_int]
+    L.orc_train_order.restype = None
+    L.orc_train_order.argtypes = [C.c_uint64, C.c_int64, P_i64]
 
 
 def _p(a, t):
@@ -570,3 +576,25 @@ def mlp_backward(params, X, T):
     g = np.zeros_like(p)
     loss = lib().orc_mlp_backward(_p(p, P_d), X.shape[0], _p(X, P_d), _p(T, P_d), _p(g, P_d))
     return loss, g
+
+
+def adam_step(p, m, v, g, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One FP64 Adam step in place on float64 arrays p, m, v (step t >= 1)."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = _c(g, np.float64)
+    lib().orc_adam_step(_p(p, P_d), _p(m, P_d), _p(v, P_d), _p(g, P_d), p.size, lr, b1, b2, eps, t)
+
+
+def train_order(seed: int, n: int) -> np.ndarray:
+    """Row visited at each position of a training run (a permutation of n)."""
+    out = np.zeros(n, np.int64)
+    lib().orc_train_order(C.c_uint64(seed), n, _p(out, P_i64))
+    return out
+
+
+def standardize_targets(scores, clip: float):
+    """(mean, std) of min(score, clip) over the training set, in FP64."""
+    t = np.minimum(np.asarray(scores, np.float64), clip)
+    mean = t.mean()
+    return mean, float(np.sqrt(max((t * t).mean() - mean * mean, 1e-12)))

@@ -20,6 +20,16 @@
  * y = h3 W4 + b4, gelu(z) = z (1 + erf(z / sqrt 2)) / 2. Parameters are packed
  * W1[128][256], b1[256], W2[256][256], b2[256], W3[256][256], b3[256],
  * W4[256], b4 (W stored [in][out]). Loss = mean over the batch of (y - t)^2.
+ *
+ * Training (per pocket, on (features, exact score) pairs):
+ *   target t = (min(score, clip) - mean) / std, mean and std of min(score,
+ *   clip) over the training set;
+ *   rows visited in one fixed order per run (orc_train_order, a keyed
+ *   bijection of [0, n)) in batches, the same order every epoch;
+ *   per batch one Adam step (Kingma & Ba, ICLR 2015, Algorithm 1):
+ *     m = b1 m + (1 - b1) g,  v = b2 v + (1 - b2) g^2,
+ *     p = p - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+ *   with lr 1e-3, b1 0.9, b2 0.999, eps 1e-8 and t the step count from 1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -167,3 +177,57 @@ double orc_mlp_backward(const double *params, int n, const double *X, const doub
 }
 
 int orc_mlp_n_params(void) { return N_PARAMS; }
+
+/* ======================================================================= */
+/* Training: Adam step and the order of the training rows                   */
+/* ======================================================================= */
+
+/* One Adam step (Kingma & Ba 2015, Algorithm 1) on n parameters in FP64;
+ * t is the step number (1 for the first step). */
+void orc_adam_step(double *p, double *m, double *v, const double *g, int64_t n, double lr,
+                   double b1, double b2, double eps, int t) {
+  const double c1 = 1.0 - pow(b1, t), c2 = 1.0 - pow(b2, t);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    const double mh = m[i] / c1, vh = v[i] / c2;
+    p[i] -= lr * mh / (sqrt(vh) + eps);
+  }
+}
+
+/* SplitMix64 output mix (Steele, Lea & Flood, OOPSLA 2014). */
+static uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* The order in which training visits its n rows: row r of the visit is
+ * out[r] = pi(r), pi a bijection of [0, n) keyed by seed. pi is a balanced
+ * four-round Feistel network on 2h-bit words (4^h the smallest power of four
+ * >= n; Luby & Rackoff 1988), round i mapping (L, R) to
+ * (R, L xor (mix64(R xor K_i) mod 2^h)) with K_i = mix64(seed + (i + 1)
+ * 0x9E3779B97F4A7C15), restricted to [0, n) by cycle walking (Black &
+ * Rogaway 2002): values >= n are encrypted again until one falls below n. */
+uint64_t orc_train_order_one(uint64_t seed, uint64_t n, uint64_t r) {
+  int h = 1;
+  while ((1ULL << (2 * h)) < n) ++h;
+  const uint64_t mask = (1ULL << h) - 1;
+  uint64_t K[4];
+  for (int i = 0; i < 4; ++i) K[i] = mix64(seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ULL);
+  uint64_t x = r;
+  do {
+    uint64_t L = x >> h, R = x & mask;
+    for (int i = 0; i < 4; ++i) {
+      const uint64_t t = L ^ (mix64(R ^ K[i]) & mask);
+      L = R;
+      R = t;
+    }
+    x = (L << h) | R;
+  } while (x >= n);
+  return x;
+}
+
+void orc_train_order(uint64_t seed, int64_t n, int64_t *out) {
+  for (int64_t r = 0; r < n; ++r) out[r] = (int64_t)orc_train_order_one(seed, (uint64_t)n, (uint64_t)r);
+}

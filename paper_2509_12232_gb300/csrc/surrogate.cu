@@ -8,7 +8,6 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
-#include <numeric>
 #include <random>
 #include <vector>
 
@@ -40,16 +39,70 @@ static int sfail(int st, const char *fmt, ...) {
 namespace {
 constexpr int kMaxTrainBatch = 65536;
 
-__global__ void gather_rows_kernel(const __nv_bfloat16 *X, const float *t, const int64_t *idx,
-                                   int64_t n_src, int rows, int rows_valid, __nv_bfloat16 *Xb,
-                                   float *tb, float t_mean, float t_inv_std, float t_clip) {
+// SplitMix64 output mix (Steele, Lea & Flood, OOPSLA 2014).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Training visits its n rows in the order r -> pi(r): a keyed bijection of
+// [0, n), a balanced four-round Feistel network on 2h-bit words (4^h >= n;
+// Luby & Rackoff) with round keys K_i = mix64(seed + (i + 1) golden-ratio
+// increment) and round function mix64(R ^ K_i) mod 2^h, restricted to
+// [0, n) by cycle walking (Black & Rogaway): a value >= n is encrypted
+// again. Each row's source is computed where it is gathered, so no order
+// array is drawn on the host or copied.
+struct TrainOrder {
+  uint64_t n, mask, K[4];
+  int h;
+};
+
+static TrainOrder make_train_order(uint64_t seed, uint64_t n) {
+  TrainOrder o;
+  o.n = n;
+  o.h = 1;
+  while ((1ULL << (2 * o.h)) < n) ++o.h;
+  o.mask = (1ULL << o.h) - 1;
+  for (int i = 0; i < 4; ++i) {
+    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    o.K[i] = z ^ (z >> 31);
+  }
+  return o;
+}
+
+__device__ __forceinline__ uint64_t train_row(const TrainOrder &o, uint64_t r) {
+  uint64_t x = r;
+  // a cycle of the permutation of [0, 4^h) through x returns below n
+  for (uint64_t walk = 0; walk <= (o.mask + 1) * (o.mask + 1); ++walk) {
+    uint64_t L = x >> o.h, R = x & o.mask;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const uint64_t t = L ^ (mix64(R ^ o.K[i]) & o.mask);
+      L = R;
+      R = t;
+    }
+    x = (L << o.h) | R;
+    if (x < o.n) return x;
+  }
+  return o.n;  // unreachable: the row is then skipped (zeros)
+}
+
+// Gathers `rows` rows (r < rows_valid real, the rest zero) into the batch:
+// with use_order, row r is training row pi(r0 + r), else row r.
+__global__ void gather_rows_kernel(const __nv_bfloat16 *X, const float *t, int use_order,
+                                   TrainOrder o, int64_t r0, int64_t n_src, int rows,
+                                   int rows_valid, __nv_bfloat16 *Xb, float *tb, float t_mean,
+                                   float t_inv_std, float t_clip) {
   // one warp per row: 128 bf16 = 256 bytes = 32 lanes x 8 bytes
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (r >= rows) return;
   uint2 v = make_uint2(0, 0);
   float tv = 0.0f;
   if (r < rows_valid) {
-    const int64_t src = idx ? idx[r] : r;
+    const int64_t src = use_order ? (int64_t)train_row(o, (uint64_t)(r0 + r)) : r;
     if (src < n_src) {
       v = reinterpret_cast<const uint2 *>(X + src * FEATURES)[lane];
       if (t) tv = (fminf(t[src], t_clip) - t_mean) * t_inv_std;
@@ -100,7 +153,6 @@ struct dock_surrogate {
   __nv_bfloat16 *X = nullptr, *H[3] = {nullptr, nullptr, nullptr}, *dZ[3] = {nullptr, nullptr, nullptr};
   float *Z[3] = {nullptr, nullptr, nullptr}, *y = nullptr, *t = nullptr, *part = nullptr,
         *outg = nullptr;
-  int64_t *idx = nullptr;
   double *stats = nullptr;
   int step = 0;
   float t_mean = 0.0f, t_std = 1.0f, t_clip = 1e30f;
@@ -123,7 +175,6 @@ struct dock_surrogate {
       if (Z[l]) cudaFree(Z[l]);
     }
     if (X) cudaFree(X);
-    if (idx) cudaFree(idx);
     if (stats) cudaFree(stats);
   }
 };
@@ -327,8 +378,8 @@ extern "C" int dock_surrogate_gradients(dock_surrogate *S, const uint16_t *featu
   if (st != DOCK_OK) return st;
   // targets used as given (identity standardisation)
   gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(
-      reinterpret_cast<const __nv_bfloat16 *>(features), targets, nullptr, n, rows, n, S->X, S->t,
-      0.0f, 1.0f, 3.0e38f);
+      reinterpret_cast<const __nv_bfloat16 *>(features), targets, 0, TrainOrder{}, 0, n, rows,
+      n, S->X, S->t, 0.0f, 1.0f, 3.0e38f);
   SCU(cudaGetLastError());
   if ((st = forward(S, rows, true, s)) != DOCK_OK) return st;
   if ((st = backward(S, rows, n, s)) != DOCK_OK) return st;
@@ -364,15 +415,8 @@ extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features,
   S->t_mean = (float)mean;
   S->t_std = (float)std::sqrt(var);
   S->t_clip = clip;
-  // one shuffled order for the run, drawn from the seed
-  std::vector<int64_t> perm((size_t)n);
-  std::iota(perm.begin(), perm.end(), 0);
-  std::mt19937_64 rng(tp->seed);
-  std::shuffle(perm.begin(), perm.end(), rng);
-  if (S->idx) cudaFree(S->idx);
-  S->idx = nullptr;
-  SCU(cudaMalloc(&S->idx, sizeof(int64_t) * n));
-  SCU(cudaMemcpyAsync(S->idx, perm.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, s));
+  // one order of the rows for the run, keyed by the seed (the same every epoch)
+  const TrainOrder ord = make_train_order(tp->seed, (uint64_t)n);
   const __nv_bfloat16 *F = reinterpret_cast<const __nv_bfloat16 *>(features);
   const int B = tp->batch;
   const int64_t steps_per_epoch = (n + B - 1) / B;
@@ -383,7 +427,8 @@ extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features,
       const int valid = (int)std::min<int64_t>(B, n - r0);
       const int rows = (valid + 127) / 128 * 128;
       gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(
-          F, scores, S->idx + r0, n, rows, valid, S->X, S->t, S->t_mean, 1.0f / S->t_std, clip);
+          F, scores, 1, ord, r0, n, rows, valid, S->X, S->t,
+          S->t_mean, 1.0f / S->t_std, clip);
       SCU(cudaGetLastError());
       if ((st = forward(S, rows, true, s)) != DOCK_OK) return st;
       if ((st = backward(S, rows, valid, s)) != DOCK_OK) return st;

@@ -125,3 +125,52 @@ def test_features_definition(posed):
     assert f[116] == pytest.approx(lig.n / 100) and f[117] == pytest.approx(lig.k / 16)
     assert np.all(f[118:] == 0)
     assert f[:56].sum() == pytest.approx(lig.n / 8)
+
+
+# ---------------------------------------------------------------------------
+# Training: Adam and the order of the training rows
+# ---------------------------------------------------------------------------
+def test_adam_step_equals_torch_adam_float64():
+    """Five steps of the oracle's Adam equal torch.optim.Adam's (float64,
+    lr 1e-3, betas (0.9, 0.999), eps 1e-8, bias-corrected) on the same
+    gradients, including tiny and zero gradients where eps matters."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    n = 4000
+    p = rng.normal(size=n)
+    m = np.zeros(n)
+    v = np.zeros(n)
+    tp = torch.tensor(p.copy(), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([tp], lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    for t in range(1, 6):
+        g = rng.normal(size=n) * np.exp(rng.uniform(-20, 2, size=n))
+        g[:7] = 0.0
+        o.adam_step(p, m, v, g, t)
+        tp.grad = torch.tensor(g, dtype=torch.float64)
+        opt.step()
+        np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-13, atol=1e-16)
+    # the first step moves every parameter with |g| >> eps by lr, against g
+    p2, m2, v2 = np.zeros(3), np.zeros(3), np.zeros(3)
+    o.adam_step(p2, m2, v2, np.array([5.0, -2e-3, 0.0]), 1)
+    np.testing.assert_allclose(p2, [-1e-3 * 5 / (5 + 1e-8), 1e-3 * 2e-3 / (2e-3 + 1e-8), 0.0],
+                               rtol=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 16, 100, 128, 1000, 1024, 4097, 65536])
+def test_train_order_is_a_permutation(n):
+    """A permutation of [0, n) for sizes with and without cycle walking
+    (n = 1024 = 4^5 and 65536 = 4^8 use the Feistel network alone, so it
+    must be a bijection itself)."""
+    p = o.train_order(11, n)
+    np.testing.assert_array_equal(np.sort(p), np.arange(n))
+
+
+def test_train_order_depends_on_seed_and_looks_shuffled():
+    from scipy.stats import chisquare, spearmanr
+    n = 1000
+    a, b = o.train_order(1, n), o.train_order(2, n)
+    assert (a != b).mean() > 0.9
+    assert abs(spearmanr(np.arange(n), a)[0]) < 0.1
+    # where row 0 lands, over many seeds, is uniform over ten bins
+    pos = np.array([int(np.nonzero(o.train_order(s, n) == 0)[0][0]) for s in range(400)])
+    assert chisquare(np.bincount(pos * 10 // n, minlength=10)).pvalue > 1e-3
