@@ -10,7 +10,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import MARGIN, PARAMS, gpu_ligands, within
+from helpers import MARGIN, PARAMS, branch_ok, gpu_ligands, pairwise_jumps, within
 from oracle import oracle as o
 from paper_2509_12232_gb300 import synth
 
@@ -55,6 +55,16 @@ def _oracle(setup, l, genos):
     return np.array(score), np.array(margin)
 
 
+def _check_near(setup, l, genos, got, ref, ok, near, **bar):
+    """Poses within the margin of the cutoff that miss the bar must meet it
+    against one of their branch values."""
+    lig = o.Ligand(**setup["ligs"].ligand(l))
+    for i in np.nonzero(~ok & near)[0]:
+        xyz = o.pose(lig, genos[i], setup["pk"].center)
+        ok[i] = branch_ok(got[i], ref[i], pairwise_jumps(lig, setup["P"], setup["pks"], xyz), **bar)
+    return ok
+
+
 @pytest.mark.parametrize("lanes", [0, 8, 2, "tuned"])
 def test_nogrid_search_replay(dock, setup, lanes):
     """lanes 0: lanes per pose picked by ligand size (several launch groups);
@@ -97,8 +107,8 @@ def test_nogrid_search_replay(dock, setup, lanes):
                                           err_msg="ligand %d generation %d" % (l, g))
             ref, margin = _oracle(setup, l, geno(g))
             near = margin < MARGIN
-            ok = within(scores(g), ref)
-            bad = np.nonzero(~ok & ~near)[0]
+            ok = _check_near(setup, l, geno(g), scores(g), ref, within(scores(g), ref), near)
+            bad = np.nonzero(~ok)[0]
             assert bad.size == 0, (l, g, bad[:5], scores(g)[bad[:5]], ref[bad[:5]])
             near_total += int(near.sum())
             checked += pop
@@ -109,7 +119,9 @@ def test_nogrid_search_replay(dock, setup, lanes):
         assert r["best_index"].tolist() == order
         ref64, margin64 = _oracle(setup, l, geno(gens - 1)[order])
         ok64 = np.abs(r["best_fp64"] - ref64) <= 1e-9 * np.maximum(1.0, np.abs(ref64))
-        assert np.all(ok64 | (margin64 < MARGIN)), (l, r["best_fp64"], ref64)
+        ok64 = _check_near(setup, l, geno(gens - 1)[order], r["best_fp64"], ref64, ok64,
+                           margin64 < MARGIN, rel=1e-9, abs_=1e-9)
+        assert np.all(ok64), (l, r["best_fp64"], ref64)
         assert int(r["exact_evals"]) == pop * gens
     # a pose of the 70-atom ligand has ~2,000 intra pairs and often protein atoms
     # near 8 A: a pair within the margin occurs in a few percent of the poses

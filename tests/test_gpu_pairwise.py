@@ -8,7 +8,7 @@ counted apart (FP32 and FP64 geometry may fall on opposite sides)."""
 import numpy as np
 import pytest
 
-from helpers import MARGIN, PARAMS, gpu_ligands, within
+from helpers import MARGIN, PARAMS, branch_ok, gpu_ligands, pairwise_jumps, within
 from oracle import oracle as o
 from paper_2509_12232_gb300 import synth
 
@@ -81,12 +81,15 @@ def test_pairwise_scores_match_oracle(dock, setup, l):
     got = _gpu(dock, setup, setup["pocket"], l, genos)
     near = margin < MARGIN
     ok = within(got, ref)
-    assert np.all(ok | near), (np.nonzero(~ok & ~near)[0][:5], got[~ok & ~near][:5], ref[~ok & ~near][:5])
+    lig = o.Ligand(**setup["ligs"].ligand(l))
+    for i in np.nonzero(~ok & near)[0]:
+        xyz = o.pose(lig, genos[i, :lig.n_genes], pk.center)
+        ok[i] = branch_ok(got[i], ref[i], pairwise_jumps(lig, setup["P"], setup["pks"], xyz))
+    assert np.all(ok), (np.nonzero(~ok)[0][:5], got[~ok][:5], ref[~ok][:5])
     # about 430 of a pose's ligand-protein distances per A lie near 8 A, so a
     # pair within the margin is expected in ~10-16% of the poses; there the two
-    # sides may differ by one pair's energy at the cutoff
+    # sides may differ by one pair's energy at the cutoff (a branch value)
     assert near.mean() <= 0.3
-    assert np.all(np.abs(got[near] - ref[near]) <= 0.5 + 1e-4 * np.abs(ref[near]))
     # most poses have protein atoms within the cutoff (the test is not vacuous)
     assert np.mean(np.abs(inter) > 1e-2) > 0.5
 

@@ -18,7 +18,7 @@ import os
 import numpy as np
 import pytest
 
-from helpers import MARGIN, OracleSide, gpu_ligands, gpu_pocket, within
+from helpers import MARGIN, OracleSide, branch_jumps, branch_ok, gpu_ligands, gpu_pocket, within
 from paper_2509_12232_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -77,8 +77,10 @@ def test_search_score_precision(dock, cfg):
             sel = rng.choice(pop, min(pop, 64), replace=False)
             ref = side.score(l, genos[sel])
             far = ref["margin"] >= MARGIN
-            near += int((~far).sum())
-            near_ok += int((~far & within(sc[sel], ref["score"])).sum())
+            for i in np.nonzero(~far)[0]:
+                near += 1
+                near_ok += int(branch_ok(float(sc[sel[i]]), ref["score"][i],
+                                         branch_jumps(side, l, genos[sel[i]])))
             e32.append(sc[sel][far].astype(np.float64))
             e64.append(ref["score"][far])
         r = res[l]
@@ -87,7 +89,11 @@ def test_search_score_precision(dock, cfg):
         over = np.abs(r["best_fp64"] - ref["score"]) / np.maximum(1e-4,
                                                                   1e-5 * np.abs(ref["score"]))
         r64_bar = max(r64_bar, float(over[far].max()) if far.any() else 0.0)
-        assert np.all(within(r["best_fp64"], ref["score"], rel=1e-5, abs_=1e-4) | ~far), l
+        ok64 = within(r["best_fp64"], ref["score"], rel=1e-5, abs_=1e-4)
+        for i in np.nonzero(~ok64 & ~far)[0]:
+            ok64[i] = branch_ok(r["best_fp64"][i], ref["score"][i],
+                                branch_jumps(side, l, r["genotype"][i, :G]), rel=1e-5, abs_=1e-4)
+        assert np.all(ok64), l
     e32, e64 = np.concatenate(e32), np.concatenate(e64)
     err = np.abs(e32 - e64)
     bar = np.maximum(1e-3, 1e-4 * np.abs(e64))
@@ -106,5 +112,7 @@ def test_search_score_precision(dock, cfg):
     _report(line)
     assert np.all(ok), (cfg, np.nonzero(~ok)[0][:5], e32[~ok][:5], e64[~ok][:5])
     # a pose within 2e-4 A of a grid face or of the 8 A cutoff may take the
-    # other branch in FP32; such poses must stay rare (about 1% of them here)
+    # other branch in FP32; such poses must stay rare (about 1% of them here),
+    # and each must meet the bar against one of its branch values
     assert near <= max(2, (n + near) // 50)
+    assert near_ok == near, (cfg, near, near_ok)

@@ -13,7 +13,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import OracleSide, compare_scores, gpu_ligands, gpu_pocket, within
+from helpers import OracleSide, branch_jumps, compare_scores, gpu_ligands, gpu_pocket, within
 from oracle import oracle as o
 from paper_2509_12232_gb300 import synth
 
@@ -90,8 +90,9 @@ def test_features_and_scores_match_oracle(dock, env):
     tol = 2.0 ** -7 * np.abs(ref) + 1e-4
     bad = (np.abs(got - ref) > tol) & ok_rows[:, None]
     assert not bad.any(), (np.argwhere(bad)[:5], got[bad][:5], ref[bad][:5])
-    c, near, worst, fails = compare_scores(sc.cpu().numpy(), np.concatenate(scores_ref),
-                                           np.concatenate(smargin))
+    c, near, worst, fails = compare_scores(
+        sc.cpu().numpy(), np.concatenate(scores_ref), np.concatenate(smargin),
+        lambda i: branch_jumps(side, lig_of[i], genos[i, :side.lig(lig_of[i]).n_genes]))
     assert len(fails) == 0
 
 
@@ -235,7 +236,8 @@ def test_surrogate_search_replay(dock, env):
             torch.cuda.synchronize()
             ks = ksc.cpu().numpy()
             ref = side.score(l, kids[kept])
-            c, near, worst, fails = compare_scores(ks, ref["score"], ref["margin"])
+            c, near, worst, fails = compare_scores(ks, ref["score"], ref["margin"],
+                                                   lambda i: branch_jumps(side, l, kids[kept][i]))
             assert len(fails) == 0
             origin, index = o.merge(scores(g - 1), ks, pop)
             kk, prev_g, prev_s = kids[kept], geno(g - 1), scores(g - 1)
