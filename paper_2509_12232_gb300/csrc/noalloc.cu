@@ -82,10 +82,10 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
   if (nl > DOCK_NOALLOC_MAX_LIGANDS)
     return fail(DOCK_EINVAL, "dock_batch_noalloc: %d ligands (at most %d)", nl,
                 DOCK_NOALLOC_MAX_LIGANDS);
-  cudaError_t e = cudaSetDevice(L->device);
-  if (e != cudaSuccess) return fail(DOCK_ECUDA, "dock_batch_noalloc: %s", cudaGetErrorString(e));
   if (L->device < 0 || L->device >= kMaxDevices)
     return fail(DOCK_EINVAL, "dock_batch_noalloc: device %d", L->device);
+  cudaError_t e = cudaSetDevice(L->device);
+  if (e != cudaSuccess) return fail(DOCK_ECUDA, "dock_batch_noalloc: %s", cudaGetErrorString(e));
   // set-up, once per device, with the device current
   void *base = nullptr;
   {

@@ -343,8 +343,16 @@ def dock_batch_noalloc(pocket: Pocket, ligands: Ligands, results, pop: int, gene
                        trace_scores=None, stream=None):
     """The plain search with no device allocation: working buffers live in the
     library's fixed scratch array; `results` is a caller-owned device buffer
-    of n_ligands dock_result records (RESULT_DTYPE.itemsize bytes each).
-    Asynchronous on stream."""
+    of n_ligands dock_result records (RESULT_DTYPE.itemsize bytes each), a
+    CUDA tensor: the kernels write one record per ligand into it and the C
+    side cannot see its size, so it is checked here. Asynchronous on stream."""
+    need = ligands.n_ligands * RESULT_DTYPE.itemsize
+    if not getattr(results, "is_cuda", False):
+        raise DockError(DOCK_EINVAL, "dock_batch_noalloc: results must be a CUDA tensor")
+    have = int(results.numel()) * int(results.element_size())
+    if have < need:
+        raise DockError(DOCK_EINVAL, "dock_batch_noalloc: results holds %d bytes, %d ligands need %d"
+                        % (have, ligands.n_ligands, need))
     sp = dock_search_params(pop, generations, p_cross, p_mut, seed, 0, 0, timeout_ns,
                             _dptr(trace_genotypes), _dptr(trace_scores), DOCK_MODE_PLAIN, 0, 0,
                             None, dock_ls_params(*NO_LS), None)

@@ -74,3 +74,36 @@ def test_noalloc_refuses_searches_larger_than_its_array(setup):
     # the library stays usable
     dock.dock_batch_noalloc(pocket, gl, out, 64, 2, stream=stream)
     torch.cuda.synchronize()
+
+
+def test_noalloc_refuses_a_results_buffer_too_small(setup):
+    """The kernels write one record per ligand into the caller's buffer; the
+    wrapper refuses a buffer that cannot hold them, or one on the host."""
+    dock, pocket, gl, ligs = setup
+    stream = torch.cuda.current_stream()
+    one = torch.empty(dock.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    with pytest.raises(dock.DockError) as e:
+        dock.dock_batch_noalloc(pocket, gl, one, 64, 2, stream=stream)
+    assert e.value.status == dock.DOCK_EINVAL
+    host = torch.empty(ligs.n_ligands * dock.RESULT_DTYPE.itemsize, dtype=torch.uint8)
+    with pytest.raises(dock.DockError) as e:
+        dock.dock_batch_noalloc(pocket, gl, host, 64, 2, stream=stream)
+    assert e.value.status == dock.DOCK_EINVAL
+
+
+def test_noalloc_deadline_reaches_every_record_and_does_not_carry_over(setup):
+    """A deadline that has passed before the first work item stops the search;
+    every record reports DOCK_ETIMEOUT. The status words live in the shared
+    array and are cleared per call, so the next call reports 0."""
+    dock, pocket, gl, ligs = setup
+    stream = torch.cuda.current_stream()
+    n = ligs.n_ligands
+    out = torch.empty(n * dock.RESULT_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    dock.dock_batch_noalloc(pocket, gl, out, 256, 10, timeout_ns=1, stream=stream)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy().view(dock.RESULT_DTYPE)
+    np.testing.assert_array_equal(res["status"], dock.DOCK_ETIMEOUT)
+    dock.dock_batch_noalloc(pocket, gl, out, 64, 2, stream=stream)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy().view(dock.RESULT_DTYPE)
+    np.testing.assert_array_equal(res["status"], 0)
