@@ -32,3 +32,27 @@ def balanced_ranges(costs, world: int):
         bounds.append(min(max(b, bounds[-1]), n))
     bounds.append(n)
     return [(bounds[r], bounds[r + 1]) for r in range(world)]
+
+
+def gather_records(records: np.ndarray, group=None) -> np.ndarray:
+    """The one exchange of a sharded run: every rank's per-ligand records (a
+    structured numpy array, e.g. dock_result rows of its range) gathered in
+    rank order, so the result lists the records in global ligand order when
+    the ranges are balanced_ranges'. Host-side, over torch.distributed (gloo
+    or any backend that moves CPU tensors); returns the gathered array on
+    every rank."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    rec = np.ascontiguousarray(records)
+    raw = torch.from_numpy(rec.view(np.uint8).reshape(-1).copy())
+    sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
+    dist.all_gather(sizes, torch.tensor([raw.numel()], dtype=torch.int64), group=group)
+    m = max(int(s.item()) for s in sizes)
+    pad = torch.zeros(max(m, 1), dtype=torch.uint8)
+    pad[:raw.numel()] = raw
+    got = [torch.zeros(max(m, 1), dtype=torch.uint8) for _ in range(world)]
+    dist.all_gather(got, pad, group=group)
+    parts = [g[:int(s.item())].numpy() for g, s in zip(got, sizes)]
+    return np.concatenate(parts).view(rec.dtype) if parts else rec[:0]

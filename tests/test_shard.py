@@ -1,7 +1,9 @@
 """Multi-process sharding of ligands (gloo, world size 2, CPU): the ranks'
 contiguous ranges cover the batch exactly once and balance the cost; each
-rank's per-ligand results (here: a deterministic stand-in per ligand id) are
-gathered on rank 0 unchanged; the step time is the maximum over ranks."""
+rank docks its range with the FP64 oracle, the per-ligand result records are
+gathered with shard.gather_records and must equal, bit for bit, one
+single-process docking of the whole batch; the step time is the maximum
+over ranks."""
 import os
 import socket
 
@@ -34,42 +36,65 @@ def _free_port():
     return p
 
 
-def _worker(rank, world, port, atom_off, tors_off, out):
+RECORD = np.dtype([("ligand_id", np.uint64), ("best_fp64", np.float64, 8),
+                   ("best_index", np.int32, 8), ("best_genotype", np.float32, (8, 23))])
+SEARCH = dict(pop=32, generations=3, seed=5)
+
+
+def _setup():
+    from oracle import oracle as o
+    pk = synth.make_pocket(300, 6.0, seed=3)
+    ligs = synth.make_ligands(np.random.Generator(np.random.Philox(8)),
+                              np.array([6, 30, 12, 9, 24, 15, 40, 8, 18]),
+                              np.array([1, 5, 2, 0, 4, 3, 6, 0, 2]), id_base=70)
+    P = o.Params(synth.TYPE_PARAMS)
+    pks = o.pocket_from(pk)
+    return o, ligs, P, pks, o.grid_build(pks, P, n_threads=1)
+
+
+def _dock_records(o, ligs, P, pks, grid):
+    r = o.dock_batch(ligs, P, pks, grid, SEARCH["pop"], SEARCH["generations"], seed=SEARCH["seed"],
+                     n_threads=1)
+    out = np.zeros(ligs.n_ligands, RECORD)
+    out["ligand_id"] = ligs.ligand_id
+    out["best_fp64"] = r["best64"]
+    out["best_index"] = r["best_idx"]
+    for l in range(ligs.n_ligands):
+        out["best_genotype"][l] = r["geno"][l][r["best_idx"][l]]
+    return out
+
+
+def _worker(rank, world, port, out):
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    costs = shard.ligand_costs(atom_off, tors_off)
+    o, ligs, P, pks, grid = _setup()
+    costs = shard.ligand_costs(ligs.atom_off, ligs.tors_off)
     a, b = shard.balanced_ranges(costs, world)[rank]
-    mine = torch.arange(a, b, dtype=torch.int64)
-    # per-ligand "result": a deterministic function of the ligand index
-    res = (mine * 2654435761) % 1000003
-    sizes = [torch.zeros(1, dtype=torch.int64) for _ in range(world)]
-    dist.all_gather(sizes, torch.tensor([b - a]))
-    m = int(max(s.item() for s in sizes))
-    pad = torch.full((m,), -1, dtype=torch.int64)
-    pad[:b - a] = res
-    got = [torch.zeros(m, dtype=torch.int64) for _ in range(world)]
-    dist.all_gather(got, pad)
+    mine = _dock_records(o, ligs.subset(np.arange(a, b)), P, pks, grid)
+    allrec = shard.gather_records(mine)
     t = torch.tensor([float(rank + 1)])
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     if rank == 0:
-        allres = torch.cat([g[:int(s.item())] for g, s in zip(got, sizes)])
-        out.put((allres.numpy().tolist(), float(t.item())))
+        out.put((allrec.tobytes(), (a, b), float(t.item())))
     dist.destroy_process_group()
 
 
-def test_two_rank_gloo_sharding():
-    ligs = synth.make_ligands(np.random.default_rng(1), np.full(37, 20) + np.arange(37), np.zeros(37, int))
+def test_two_rank_gloo_sharded_docking_equals_one_process():
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, ligs.atom_off, ligs.tors_off, q))
-             for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    res, tmax = q.get(timeout=120)
+    raw, first, tmax = q.get(timeout=300)
     for p in procs:
         p.join(60)
         assert p.exitcode == 0
-    assert res == [(i * 2654435761) % 1000003 for i in range(37)]
+    got = np.frombuffer(raw, RECORD)
+    o, ligs, P, pks, grid = _setup()
+    ref = _dock_records(o, ligs, P, pks, grid)
+    assert 0 < first[1] < ligs.n_ligands          # both ranks docked something
+    assert got.tobytes() == ref.tobytes()
+    np.testing.assert_array_equal(got["ligand_id"], ligs.ligand_id)
     assert tmax == 2.0
