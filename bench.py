@@ -56,6 +56,11 @@ WORKLOADS = {
            "100,000 synthetic ligands (heavy atoms lognormal, mean 30, sd 10, clipped to 8-100; "
            "Poisson(5) torsions, at most 16) vs a 4,000-atom pocket (16 A cavity, 86^3 x 7 grid "
            "maps), 512 poses x 30 generations, FP64 best-8 rescoring"),
+    "c5": ("ligands/s (plain exact GA docking, large screen in chunks: 2,048 poses x 40 "
+           "generations per ligand)",
+           "1,000,000 synthetic ligands (10-60 heavy atoms, 0-12 torsions) in 20 chunks of 50,000 "
+           "vs a 10,000-atom pocket (20 A cavity, 107^3 x 7 grid maps), 2,048 poses x 40 "
+           "generations, FP64 best-8 rescoring"),
 }
 METRIC_NOGRID = ("ligands/s (plain exact GA docking without grid maps: pairwise inter-energy, "
                  "1,024 poses x 50 generations per ligand)")
@@ -328,6 +333,111 @@ def cpu_baseline(per_core, lga=False):
                       "%d generations each; mean of %d runs after %d dropped, %.2f s per run" % (
                           len(idx), per_core, WORKLOAD, w.pop, w.generations, runs - drop, drop,
                           mean_s)}
+
+
+def _make_chunk(args):
+    from paper_2509_12232_gb300 import synth
+    name, c, size = args
+    return synth.screen_chunk(name, c, size)
+
+
+def run_screen(args, rank, world):
+    """The large screen (c5): every chunk docked through the C ABI from host
+    arrays, chunk k + 1 prepared and uploaded on a side stream while chunk k
+    is searched (screen.screen). The ligands are drawn before the timed
+    region, in parallel processes; the timed region covers the whole screen
+    (upload, search, FP64 rescoring, records to the host)."""
+    import multiprocessing as mp
+    from paper_2509_12232_gb300 import synth
+    size = args.screen_chunk
+    w = synth.WORKLOADS[WORKLOAD]
+    n_total = args.ligands or w.n_ligands
+    n_chunks = -(-n_total // size)
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(min(n_chunks, os.cpu_count() or 1)) as pool:
+        chunks = pool.map(_make_chunk, [(WORKLOAD, c, size) for c in range(n_chunks)])
+    if n_total % size:
+        chunks[-1] = chunks[-1].subset(np.arange(n_total - (n_chunks - 1) * size))
+    gen_s = time.perf_counter() - t0
+    import torch
+    from paper_2509_12232_gb300 import build, dock, screen
+    torch.cuda.set_device(0)
+    build.build()
+    stream = torch.cuda.current_stream()
+    side = torch.cuda.Stream()
+    pk, _, _ = synth.make_workload(WORKLOAD, n_ligands=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pocket = dock.dock_create_pocket(pk.x, pk.y, pk.z, pk.q, pk.type, pk.center, pk.radius,
+                                     pk.spacing, synth.TYPE_PARAMS, stream=stream)
+    torch.cuda.synchronize()
+    grid_ms = 1000 * (time.perf_counter() - t0)
+    # set-up (untimed): launch shape measured on 2,000 ligands of chunk 0,
+    # then kept for every chunk; one profiled search of them for the roofline
+    probe = chunks[0].subset(np.arange(min(2000, chunks[0].n_ligands)))
+    gp = screen._load(pocket, probe, stream, None)
+    tune = dock.dock_autotune(pocket, gp, w.pop, 4, stream=stream)
+    shape = tune["table"][tune["best"]]
+    os.environ["DOCK_THREADS"] = str(shape["threads"])
+    os.environ["DOCK_ATOMS_PER_LANE"] = str(shape["atoms_per_lane"])
+    info = dock.dock_ligands_info(gp)
+    os.environ["DOCK_PROFILE_LAUNCHES"] = "1"
+    j = dock.dock_batch(pocket, gp, w.pop, w.generations, seed=0, use_graph=1, stream=stream)
+    ms_kernels, n_launch = dock.dock_job_kernel_time(j)
+    dock.dock_results(j)
+    j.close()
+    del os.environ["DOCK_PROFILE_LAUNCHES"]
+    gp.close()
+    clocks = Clocks(0)
+    torch.cuda.synchronize()
+    clocks.start()
+    t0 = time.perf_counter()
+    recs, stats = screen.screen(pocket, chunks, w.pop, w.generations, seed=0, stream=stream,
+                                side_stream=side, device=0, use_graph=1)
+    torch.cuda.synchronize()
+    total_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    assert recs.shape[0] == n_total and np.all(recs["status"] == 0)
+    assert np.array_equal(recs["ligand_id"], np.arange(n_total, dtype=np.uint64))
+    peaks, _ = measured_peaks()
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    mufu_peak = n_sm * 16 * sm_mhz * 1e6 / 1e12
+    flops_pose, mufu_pose = work_per_pose(info, probe.n_ligands)
+    per_gen_s = ms_kernels / 1000.0 / max(n_launch, 1)
+    ach = flops_pose * w.pop / per_gen_s / 1e12
+    poses = n_total * w.pop * w.generations
+    line = {"metric": METRIC, "value": round(n_total / total_s, 2), "unit": "ligands/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": round(1000 * total_s, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": DESCR, "ligands": n_total, "chunk": size, "chunks": n_chunks,
+                       "pop": w.pop, "generations": w.generations,
+                       "l2": "inputs larger than L2 (each chunk's genotypes ~10 GB)",
+                       "launch_shape": {"threads": shape["threads"],
+                                        "atoms_per_lane": shape["atoms_per_lane"],
+                                        "picked_by": "dock_autotune on 2,000 ligands of chunk 0"}},
+            "poses_scored_per_s": round(poses / total_s, 1),
+            "timed_region": "whole screen from host ligand arrays: per chunk upload (overlapped "
+                            "with the previous chunk's search), search, FP64 rescoring, records "
+                            "to the host",
+            "chunk_seconds": {"min": round(min(t for _, t in stats), 3),
+                              "max": round(max(t for _, t in stats), 3)},
+            "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2),
+                         "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
+                         "kernel": "search_kernel",
+                         "measured_on": "one profiled search of 2,000 ligands of chunk 0",
+                         "mufu": {"achieved": round(mufu_pose * w.pop / per_gen_s / 1e12, 4),
+                                  "peak": round(mufu_peak, 4), "unit": "Tops/s"},
+                         "generation_ms": round(1000 * per_gen_s, 4)},
+            "grid_build_ms": round(grid_ms, 1), "ligand_generation_s (untimed)": round(gen_s, 1),
+            "gpu_launches": n_chunks * (n_launch + 4),
+            "gpu_launches_note": "per chunk: the search launches of 40 generations (as counted in "
+                                 "the profiled search) plus the set-up and FP64 rescoring kernels",
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_surrogate(args, rank, world):
@@ -665,7 +775,10 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS),
                     help="c2 (default): 1,000 ligands x 1,024 poses x 50 generations; c3: the "
                          "uneven batch, 100,000 ligands x 512 poses x 30 generations "
-                         "(plain, lga and nogrid modes)")
+                         "(plain, lga and nogrid modes); c5: the large screen, 1,000,000 "
+                         "ligands x 2,048 poses x 40 generations in chunks (plain)")
+    ap.add_argument("--screen-chunk", type=int, default=50_000,
+                    help="ligands per dock_batch call of the c5 screen")
     ap.add_argument("--ref-ligands-per-core", type=int, default=2)
     ap.add_argument("--cpu-baseline-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -690,6 +803,8 @@ def main():
         return run_grid(args, rank, world)
     if args.mode == "pairwise":
         return run_pairwise(args, rank, world)
+    if WORKLOAD == "c5":
+        return run_screen(args, rank, world)
 
     import torch
     import torch.distributed as dist

@@ -313,3 +313,22 @@ def make_workload(name: str, n_ligands: int | None = None, seed: int = 0,
     na, nt = ligand_sizes(rng, w.sizes, n)
     ligs = make_ligands(rng, na, nt)
     return pk, ligs, w
+
+
+SCREEN_CHUNK = 50_000
+
+
+def screen_chunk(name: str, c: int, size: int = SCREEN_CHUNK, seed: int = 0) -> LigandSet:
+    """Ligands [c size, (c + 1) size) of a large screen (``c5``: 20 chunks of
+    50,000), drawn from their own Philox stream keyed by (seed + 1000, c) so
+    any chunk can be made alone and in parallel; ligand ids c size + i."""
+    w = WORKLOADS[name]
+    n = max(0, min(size, w.n_ligands - c * size))
+    rng = np.random.Generator(np.random.Philox(np.random.SeedSequence([seed + 1000, c])))
+    na, nt = ligand_sizes(rng, w.sizes, n)
+    return make_ligands(rng, na, nt, id_base=c * size)
+
+
+def screen_chunks(name: str, size: int = SCREEN_CHUNK) -> int:
+    """Number of chunks of the screen `name` at `size` ligands per chunk."""
+    return -(-WORKLOADS[name].n_ligands // size)
