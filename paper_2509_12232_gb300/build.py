@@ -2,7 +2,10 @@
 
 One nvcc per translation unit, in parallel, for sm_103a only; then a shared
 link. Re-running skips translation units whose object is newer than every
-source and header.
+source and header. build(checked=True) makes the bounds-checked variant,
+libdock_checked.so (DOCK_CHECKED: every index the search, local-search and
+pairwise kernels take from their inputs is tested; a failure is recorded in
+the call's status word and reported as DOCK_EDEVICE, without a trap).
 """
 from __future__ import annotations
 
@@ -16,6 +19,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libdock.so")
+CHECKED_LIB = os.path.join(PKG, "libdock_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
@@ -27,17 +31,20 @@ def _headers():
         glob.glob(os.path.join(ROOT, "include", "*.h"))
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    out_dir = OUT + ("_checked" if checked else "")
+    lib_path = CHECKED_LIB if checked else LIB
+    flags = FLAGS + (["-DDOCK_CHECKED"] if checked else [])
+    os.makedirs(out_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = max((os.path.getmtime(h) for h in _headers()), default=0)
     jobs = []
     objs = []
     for s in srcs:
-        o = os.path.join(OUT, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(out_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), hdr_time):
-            jobs.append([NVCC] + ARCH + FLAGS + ["-c", s, "-o", o])
+            jobs.append([NVCC] + ARCH + flags + ["-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -49,11 +56,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
         list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + ".%d.tmp" % os.getpid()
+    if jobs or not os.path.exists(lib_path):
+        tmp = lib_path + ".%d.tmp" % os.getpid()
         run([NVCC] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -518,6 +518,26 @@ void parallel_for(int n, F f) {
 }
 }  // namespace
 
+// The bounds-checked build's report for calls without a status word of their
+// own (scoring, pairwise scoring, standalone local search): waits for the
+// stream and reads the ligand set's check word. A no-op in the normal build.
+static int checked_report(dock_ligands *L, cudaStream_t s, const char *what) {
+#ifdef DOCK_CHECKED
+  int32_t w = 0;
+  CU(cudaMemcpyAsync(&w, L->d_check, sizeof w, cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (w != 0) {
+    CU(cudaMemsetAsync(L->d_check, 0, sizeof w, s));
+    return fail(DOCK_EDEVICE, "%s: bounds check failed at site %d", what, kCheckBase - w);
+  }
+#else
+  (void)L;
+  (void)s;
+  (void)what;
+#endif
+  return DOCK_OK;
+}
+
 extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *b, void *stream,
                                  dock_ligands **out) {
   if (!P || !b || !out) return fail(DOCK_EINVAL, "dock_load_ligands: NULL argument");
@@ -611,6 +631,8 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   CU(up(L->d_pair_rec, prec.get(), sizeof(float) * 4 * np));
   CU(up(L->d_tors, tors.data(), sizeof(TorInfo) * nt));
   CU(up(L->d_moves, moves.data(), (size_t)nm));
+  CU(dalloc(&L->d_check, 1));
+  CU(cudaMemsetAsync(L->d_check, 0, sizeof(int32_t), s));
   CU(launch_intra_const(L->d_info, nl, L->d_atoms_raw, L->d_types, L->d_pair_idx, P->d_params, s));
   CU(cudaStreamSynchronize(s));
   L->total_atoms = n_atoms;
@@ -979,6 +1001,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   A.lig_status = W.lig_status;
   A.deadline = sp->timeout_ns ? W.deadline : nullptr;
   A.pw = pw_view(P);
+  A.bounds = bounds_of(P, L, W.status);
 
   LsArgs LA{};
   if (lamarck) {
@@ -1009,6 +1032,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     LA.pop = pop;
     LA.evals = W.ls_evals;
     LA.status = W.status;
+    LA.bounds = bounds_of(P, L, W.status);
     LA.deadline = A.deadline;
   }
 
@@ -1093,6 +1117,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   KS.coords = nullptr;
   KS.lanes = 8;
   KS.atoms_per_lane = DOCK_MAX_ATOMS / 8;
+  KS.bounds = bounds_of(P, L, W.status);
 
   // One surrogate generation g >= 1: candidates + features, prediction, top
   // `keep`, exact scores of the kept, mu + lambda merge into generation g.
@@ -1253,6 +1278,8 @@ extern "C" int dock_results(dock_job *J, dock_result *out, int32_t cap, uint64_t
   const int n = std::min(cap, J->n_ligands);
   if (n > 0) CU(cudaMemcpy(out, J->L->ws.results, sizeof(dock_result) * n, cudaMemcpyDeviceToHost));
   if (status == DOCK_ETIMEOUT) return fail(DOCK_ETIMEOUT, "dock_results: device deadline exceeded");
+  if (status <= kCheckBase)
+    return fail(DOCK_EDEVICE, "dock_results: bounds check failed at site %d", kCheckBase - status);
   if (status != 0) return fail(DOCK_EDEVICE, "dock_results: device status %d", status);
   return DOCK_OK;
 }
@@ -1334,8 +1361,9 @@ extern "C" int dock_score(dock_pocket *P, dock_ligands *L, const int32_t *pose_l
   A.coords = coords;
   A.lanes = 8;
   A.atoms_per_lane = DOCK_MAX_ATOMS / 8;
+  A.bounds = bounds_of(P, L, L->d_check);
   CU(launch_score(A, s));
-  return DOCK_OK;
+  return checked_report(L, s, "dock_score");
 }
 
 extern "C" int dock_local_search(dock_pocket *P, dock_ligands *L, const dock_ls_params *ls,
@@ -1379,6 +1407,7 @@ extern "C" int dock_local_search(dock_pocket *P, dock_ligands *L, const dock_ls_
   A.scores = scores;
   A.pose_evals = evals;
   A.trace = trace;
+  A.bounds = bounds_of(P, L, L->d_check);
   const int threads = 128, lanes = 8;
   int per_sm = 0, n_sm = 0;
   CU(ls_occupancy(threads, lanes, A.atoms_per_lane, &per_sm));
@@ -1387,7 +1416,7 @@ extern "C" int dock_local_search(dock_pocket *P, dock_ligands *L, const dock_ls_
   const int64_t need = (n_poses + threads / lanes - 1) / (threads / lanes);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * n_sm, need));
   CU(launch_ls(A, blocks, threads, lanes, s));
-  return DOCK_OK;
+  return checked_report(L, s, "dock_local_search");
 }
 
 extern "C" int dock_score_pairwise(dock_pocket *P, dock_ligands *L, const int32_t *pose_ligand,
@@ -1414,8 +1443,9 @@ extern "C" int dock_score_pairwise(dock_pocket *P, dock_ligands *L, const int32_
   A.n_poses = n_poses;
   A.scores = scores;
   A.pw = pw_view(P);
+  A.bounds = bounds_of(P, L, L->d_check);
   CU(launch_score_pairwise(A, (cudaStream_t)stream));
-  return DOCK_OK;
+  return checked_report(L, (cudaStream_t)stream, "dock_score_pairwise");
 }
 
 extern "C" int dock_features(dock_pocket *P, dock_ligands *L, const int32_t *pose_ligand,

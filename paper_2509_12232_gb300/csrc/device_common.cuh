@@ -9,6 +9,23 @@
 
 namespace dk {
 
+// Index checks of the bounds-checked build (DOCK_CHECKED): a failed check
+// records kCheckBase - site in the call's status word (the first failure
+// wins) and returns false; the caller then uses an index known to be in
+// bounds, and the persistent loops stop at their next work item. No trap.
+// The normal build compiles every check to `true`.
+#ifdef DOCK_CHECKED
+__device__ __forceinline__ bool check_ok(bool ok, int32_t *word, int site) {
+  if (!ok && word != nullptr) atomicCAS(word, 0, kCheckBase - site);
+  return ok;
+}
+#define DK_OK(cond, word, site) ::dk::check_ok((cond), (word), (site))
+#define DK_BOUNDS(args) (&(args).bounds)
+#else
+#define DK_OK(cond, word, site) true
+#define DK_BOUNDS(args) nullptr
+#endif
+
 // ---- AutoDock4 free-energy constants (the scoring form the paper's muDock
 // ---- is "functionally equivalent" to, Section V) ----------------------------
 // (double: the FP64 paths use them as they are; FP32 code rounds explicitly)
@@ -412,7 +429,7 @@ struct Lookup {
 };
 
 __device__ __forceinline__ Lookup grid_issue(const GridView &G, int t, float q, float x, float y,
-                                             float z) {
+                                             float z, int32_t *check_word = nullptr) {
   Lookup L;
   // grid coordinates u = x / h - origin / h (one rounding less than (x - o) / h)
   const float ux = fmaf(x, G.inv_h, G.gx), uy = fmaf(y, G.inv_h, G.gy), uz = fmaf(z, G.inv_h, G.gz);
@@ -427,7 +444,9 @@ __device__ __forceinline__ Lookup grid_issue(const GridView &G, int t, float q, 
     const int nc = G.n - 1;
     const int sg = q < 0.0f ? 1 : 0;
     // 32-bit element index: the texture holds at most 2^27 elements
-    const int e = ((((2 * t + sg) * G.n + iz) * nc + iy) * nc + ix) * 2;
+    int e = ((((2 * t + sg) * G.n + iz) * nc + iy) * nc + ix) * 2;
+    if (!DK_OK(e >= 0 && e + G.plane_elems + 1 < G.tex_elems && t < G.n_types, check_word, 9))
+      e = 0;
     const int ez = e + G.plane_elems;
     const float4 a0 = tex1Dfetch<float4>(G.xytex, e), a1 = tex1Dfetch<float4>(G.xytex, e + 1);
     const float4 b0 = tex1Dfetch<float4>(G.xytex, ez), b1 = tex1Dfetch<float4>(G.xytex, ez + 1);

@@ -26,6 +26,21 @@ struct LigInfo {
   uint64_t ligand_id;
 };
 
+// Sizes of the arrays the hot kernels index, and the device word in which a
+// bounds-checked build (compiled with DOCK_CHECKED) records its first failed
+// index check as kCheckBase - site (the host then reports DOCK_EDEVICE). The
+// normal build carries the struct but tests nothing.
+constexpr int32_t kCheckBase = -1000;
+struct Bounds {
+  int32_t *word;           // status word of the call (NULL: checks not recorded)
+  int64_t atoms, pairs;    // atom rows, FP32 pair records of the ligand set
+  int64_t tors, moves;     // torsion records, moved-atom entries
+  int32_t ligands;
+  int32_t tex_elems;       // float4 elements of the map records' texture
+  int32_t prot_atoms;      // protein atoms of the cell list
+  int32_t slot_rows;       // float4 rows of one pose's shared-memory slot
+};
+
 // One rotatable bond: rotate atoms moves[move_off .. move_off + n_move) about
 // the axis parent(b) = a -> b.
 struct TorInfo {
@@ -64,6 +79,7 @@ struct GridView {
   float gx, gy, gz;     // -origin / h: grid coordinate u = x inv_h + g
   int32_t plane_elems;  // texture elements of one z plane of records, 2 (n-1)^2
   int32_t n_types;
+  int32_t tex_elems;    // texture elements of all records, 2 n_types 2 n (n-1)^2
 };
 
 // Protein atoms by cell: cells are kCellX wide in x and kCellYZ in y and z
@@ -86,6 +102,7 @@ struct PwView {
   const float4 *tpair;      // [T][T] {c12, c6, c10, cap} weights folded in
   const float2 *tsv;        // [T] {solpar, vol}
   int32_t n_types;
+  int32_t n_atoms;          // protein atoms in cprot / cext
 };
 
 struct SearchArgs {
@@ -122,6 +139,7 @@ struct SearchArgs {
   int32_t *lig_status;      // [n_ligands]
   const uint64_t *deadline;  // device globaltimer deadline, NULL = none
   PwView pw;                // the protein of the pairwise inter-energy (no-grid search)
+  Bounds bounds;
 };
 
 // Solis-Wets refinement (local_search.cu). Batch mode (units != nullptr):
@@ -172,6 +190,7 @@ struct LsArgs {
   // optional trace rows of 2 + 2 max_its floats: batch [n_ligands * pop],
   // standalone [n_poses]
   float *trace;
+  Bounds bounds;
 };
 // Selection bits and counts of generations [0, gens) (counts zeroed first):
 // bit i of ligand l, generation g is set when individual i is refined.
@@ -199,6 +218,7 @@ struct ScoreArgs {
   float *coords;            // optional
   int32_t lanes;            // lanes per pose
   int32_t atoms_per_lane;
+  Bounds bounds;
 };
 
 // Pairwise scoring of caller-given poses (pairwise.cu): the ScoreArgs inputs
@@ -217,6 +237,7 @@ struct PairwiseArgs {
   int64_t n_poses;
   float *scores;
   PwView pw;
+  Bounds bounds;
 };
 cudaError_t launch_score_pairwise(const PairwiseArgs &a, cudaStream_t s);
 

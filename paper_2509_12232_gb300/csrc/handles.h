@@ -87,6 +87,7 @@ inline GridView grid_view(const dock_pocket *p) {
   g.gz = (float)(-p->oz / p->h);
   g.plane_elems = 2 * (p->n - 1) * (p->n - 1);
   g.n_types = p->n_types;
+  g.tex_elems = 4 * p->n_types * p->n * (p->n - 1) * (p->n - 1);
   return g;
 }
 
@@ -110,6 +111,7 @@ inline PwView pw_view(const dock_pocket *p) {
   w.tpair = p->d_tpair;
   w.tsv = p->d_tsv;
   w.n_types = p->n_types;
+  w.n_atoms = p->n_prot;
   return w;
 }
 
@@ -195,6 +197,7 @@ struct dock_ligands {
   float *d_pair_rec = nullptr;
   TorInfo *d_tors = nullptr;
   uint8_t *d_moves = nullptr;
+  int32_t *d_check = nullptr;  // index-check word of calls without a status word (checked build)
   int64_t total_pairs = 0, total_atoms = 0, total_tors = 0, total_moved = 0, h2d_bytes = 0;
   Workspace ws;
   ~dock_ligands() {
@@ -207,8 +210,25 @@ struct dock_ligands {
     dfree(d_pair_rec);
     dfree(d_tors);
     dfree(d_moves);
+    dfree(d_check);
   }
 };
+
+// Array sizes of a (pocket, ligand set) for the bounds-checked build; word is
+// the status word the call's kernels record a failed check in.
+inline Bounds bounds_of(const dock_pocket *p, const dock_ligands *l, int32_t *word) {
+  Bounds b;
+  b.word = word;
+  b.atoms = l->total_atoms;
+  b.pairs = l->total_pairs;
+  b.tors = l->total_tors;
+  b.moves = l->total_moved;
+  b.ligands = l->n_ligands;
+  b.tex_elems = 4 * p->n_types * p->n * (p->n - 1) * (p->n - 1);
+  b.prot_atoms = p->n_prot;
+  b.slot_rows = 0;
+  return b;
+}
 
 inline uint64_t prob_threshold(float p) {
   double t = (double)p * 4294967296.0;

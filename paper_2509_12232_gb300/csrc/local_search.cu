@@ -194,13 +194,17 @@ __global__ void __launch_bounds__(128, 4) ls_kernel(const LsArgs A) {
           atomicExch(A.status, (int)DOCK_ETIMEOUT);
           u = A.n_units;
         }
+#ifdef DOCK_CHECKED
+        if (u < A.n_units && *(volatile int32_t *)A.status != 0) u = A.n_units;  // a check failed
+#endif
       }
       u = __shfl_sync(0xffffffffu, u, 0);
       if (u >= A.n_units) break;
       lig = A.units[u];
+      if (!DK_OK(lig >= 0 && lig < A.bounds.ligands, A.status, 13)) lig = 0;
       const LigInfo li = A.ligs[lig];
       G = 7 + li.k;
-      V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors);
+      V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors, DK_BOUNDS(A), ss);
       lig_id = li.ligand_id;
       bits = A.sel_bits + (int64_t)lig * A.sel_words;
       count = A.sel_count[lig];
@@ -239,6 +243,7 @@ __global__ void __launch_bounds__(128, 4) ls_kernel(const LsArgs A) {
           break;
         }
         ind = nth_set_bit(bits, A.sel_words, r);
+        if (!DK_OK(ind >= 0 && ind < A.pop, A.status, 14)) ind = 0;
         gp = A.geno + A.geno_off[lig] + ind * G;
         c.f0 = A.score[(int64_t)lig * A.pop + ind];
         c.f = nan_to_inf(c.f0);
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(128, 4) ls_kernel(const LsArgs A) {
         }
         const LigInfo li = A.ligs[lig];
         G = 7 + li.k;
-        V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors);
+        V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors, DK_BOUNDS(A), ss);
         lig_id = li.ligand_id;
         gp = A.genos + ind * DOCK_MAX_GENES;
         c.phase = 0;

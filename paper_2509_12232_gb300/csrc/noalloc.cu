@@ -186,6 +186,7 @@ extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_se
   A.lig_status = lig_status;
   A.deadline = sp->timeout_ns ? deadline : nullptr;
   A.pw = pw_view(P);
+  A.bounds = bounds_of(P, L, status);
   Fp64Args F;
   F.ligs = L->d_info;
   F.atoms = L->d_atoms_raw;

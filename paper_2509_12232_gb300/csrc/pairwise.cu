@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(kPwThreads) score_pairwise_kernel(const Pairwi
   const float *src = A.genos + pose * DOCK_MAX_GENES;
 #pragma unroll
   for (int e = 0; e < DOCK_MAX_GENES; ++e) g[e] = e < 7 + li.k ? src[e] : 0.0f;
-  const LigView V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors);
+  const LigView V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors, DK_BOUNDS(A),
+                             slot_stride(kPwL, kPwApl));
   float4 *sl = s_col + slot * slot_stride(kPwL, kPwApl);
   apply_pose<kPwL>(g, V, A.moves, A.cx, A.cy, A.cz, sl, lane, gmask);
   const float score = score_posed_pw<kPwL>(V, A.pw, sl, lane, gmask, s_tp, s_sv);

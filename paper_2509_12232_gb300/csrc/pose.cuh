@@ -27,11 +27,19 @@ struct LigView {
   const TorInfo *tors;
   int n, k, n_pairs;
   float intra_const;  // energy of the pose-invariant pairs
+#ifdef DOCK_CHECKED
+  int32_t *word;      // status word of the call
+  int64_t moves;      // moved-atom entries of the set
+  int rows;           // float4 rows of the pose slot
+#endif
 };
 
+// b, slot_rows: array sizes for the bounds-checked build (unused otherwise);
+// there a ligand whose rows do not fit its arrays or its slot gets no work.
 __device__ __forceinline__ LigView lig_view(const LigInfo &li, const float4 *atoms,
                                             const uint8_t *types, const float *pair_rec,
-                                            const TorInfo *tors) {
+                                            const TorInfo *tors, const Bounds *b = nullptr,
+                                            int slot_rows = 0) {
   LigView v;
   v.atoms = atoms + li.atom_off;
   v.types = types + li.atom_off;
@@ -41,6 +49,19 @@ __device__ __forceinline__ LigView lig_view(const LigInfo &li, const float4 *ato
   v.k = li.k;
   v.n_pairs = li.n_pairs;
   v.intra_const = li.intra_const;
+#ifdef DOCK_CHECKED
+  v.word = b ? b->word : nullptr;
+  v.moves = b ? b->moves : 0;
+  v.rows = slot_rows;
+  if (b) {
+    const bool ok = DK_OK((int64_t)li.atom_off + li.n <= b->atoms && li.atom_off >= 0, v.word, 1) &&
+                    DK_OK((int64_t)li.pair_off + li.n_pairs <= b->pairs && li.pair_off >= 0,
+                          v.word, 2) &&
+                    DK_OK((int64_t)li.tors_off + li.k <= b->tors && li.tors_off >= 0, v.word, 3) &&
+                    DK_OK(li.n <= slot_rows && li.k <= DOCK_MAX_TORSIONS, v.word, 4);
+    if (!ok) v.n = v.k = v.n_pairs = 0;
+  }
+#endif
   return v;
 }
 
@@ -58,12 +79,27 @@ struct PairWalker {
   const float4 *slot;
   uint32_t last_i = 0xffffffffu;
   float4 ci;
+#ifdef DOCK_CHECKED
+  const LigView *V;
+  int lane;
+  __device__ __forceinline__ PairWalker(const LigView &v, const float4 *s, int ln)
+      : rec(v.pair_rec + ln * 4), slot(s), V(&v), lane(ln) {}
+#else
   __device__ __forceinline__ PairWalker(const LigView &v, const float4 *s, int lane)
       : rec(v.pair_rec + lane * 4), slot(s) {}
+#endif
   // m: the lane's pair counter (pair lane + m L)
   __device__ __forceinline__ float term(int m) {
+#ifdef DOCK_CHECKED
+    const bool in = DK_OK(lane + m * L < V->n_pairs, V->word, 5);
+    const float4 r = ld4(rec + (in ? m * (4 * L) : -lane * 4));
+    uint32_t oij = __float_as_uint(r.x);
+    if (!DK_OK((oij & 0xffffu) < 16u * V->rows && (oij >> 16) < 16u * V->rows, V->word, 6))
+      oij = 0;
+#else
     const float4 r = ld4(rec + m * (4 * L));
     const uint32_t oij = __float_as_uint(r.x);
+#endif
     const uint32_t oi = oij & 0xffffu;
     if (oi != last_i) {
       ci = slot_row(slot, oi);
@@ -108,7 +144,14 @@ __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], con
 #pragma unroll 1
   for (int j = 0; j < V.k; ++j) {
     {
-      const TorInfo T = V.tors[j];
+      TorInfo T = V.tors[j];
+#ifdef DOCK_CHECKED
+      if (!DK_OK(T.a < V.n && T.b < V.n && T.move_off >= 0 && T.n_move >= 0 &&
+                     (int64_t)T.move_off + T.n_move <= V.moves, V.word, 7)) {
+        T.a = T.b = 0;
+        T.n_move = 0;
+      }
+#endif
       const float4 pa = slot[T.a], pb = slot[T.b];
       float ux = pb.x - pa.x, uy = pb.y - pa.y, uz = pb.z - pa.z;
       const float il = rsqrt_ftz(ux * ux + uy * uy + uz * uz);
@@ -124,7 +167,10 @@ __device__ __forceinline__ void apply_pose(const float (&g)[DOCK_MAX_GENES], con
       const float m20 = uz * ux * oc - uy * s, m21 = uz * uy * oc + ux * s, m22 = c + uz * uz * oc;
       const uint8_t *mv = moves + T.move_off;
       for (int m = lane; m < T.n_move; m += L) {
-        const int at = mv[m];
+        int at = mv[m];
+#ifdef DOCK_CHECKED
+        if (!DK_OK(at < V.n, V.word, 8)) at = 0;
+#endif
         const float4 p = slot[at];
         const float vx = p.x - pa.x, vy = p.y - pa.y, vz = p.z - pa.z;
         slot[at] = make_float4(pa.x + m00 * vx + m01 * vy + m02 * vz,
@@ -155,7 +201,11 @@ __device__ __forceinline__ float score_posed(const LigView &V, const GridView &G
   for (int k = 0; k < na; ++k) {
     const int a = lane + k * L;
     const float4 pa = slot[a];
+#ifdef DOCK_CHECKED
+    const Lookup lk = grid_issue(G, V.types[a], __ldg(&V.atoms[a].w), pa.x, pa.y, pa.z, V.word);
+#else
     const Lookup lk = grid_issue(G, V.types[a], __ldg(&V.atoms[a].w), pa.x, pa.y, pa.z);
+#endif
     if (coords_out) {
       coords_out[3 * a] = pa.x;
       coords_out[3 * a + 1] = pa.y;
@@ -211,13 +261,20 @@ __device__ __forceinline__ void pairwise_inter(const LigView &V, const PwView &W
     const float vi = (float)kWSol * svi.y;                               // W_sol V_i
     Kahan ai;
     cutoff_ranges(W.cells, p.x, p.y, p.z, kCutoffSearch2, [&](int j0, int j1) {
+#ifdef DOCK_CHECKED
+      if (!DK_OK(j0 >= 0 && j0 <= j1 && j1 <= W.n_atoms, V.word, 10)) j1 = j0 = 0;
+#endif
       for (int j = j0; j < j1; ++j) {
         const float4 b = __ldg(W.cprot + j);
         const float dx = p.x - b.x, dy = p.y - b.y, dz = p.z - b.z;
         const float r2 = dx * dx + dy * dy + dz * dz;
         if (r2 < kCutoff2) {
           const float4 ex = __ldg(W.cext + j);  // {S_j, V_j, type, 0}
-          const float4 c = tp[ti * T + (int)ex.z];
+          int tj = (int)ex.z;
+#ifdef DOCK_CHECKED
+          if (!DK_OK(tj >= 0 && tj < T && ti < T, V.word, 11)) tj = 0;
+#endif
+          const float4 c = tp[ti * T + tj];
           const float rec[8] = {c.x, c.y, c.z, c.w, qe * b.w, fmaf(si, ex.y, ex.x * vi),
                                 0.0f, 0.0f};
           ai.add(pair_energy(r2, rec));

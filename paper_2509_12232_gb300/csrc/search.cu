@@ -31,6 +31,9 @@ int search_smem_bytes(int threads, int atoms_per_lane) {
 
 __device__ __forceinline__ int fetch_item(const SearchArgs &A) {
   int it = (int)atomicAdd(A.counter, 1u);
+#ifdef DOCK_CHECKED
+  if (it < A.n_items && *(volatile int32_t *)A.status != 0) it = A.n_items;  // a check failed
+#endif
   if (A.deadline != nullptr && it < A.n_items && globaltimer_ns() > *A.deadline) {
     atomicExch(A.status, (int)DOCK_ETIMEOUT);
     it = A.n_items;
@@ -48,6 +51,7 @@ __device__ __forceinline__ void search_item(const SearchArgs &A, const Item &ite
   const int ind = item.first_div * S + slot;
   if (ind >= A.pop) return;
   const unsigned gmask = group_mask<L>();
+  if (!DK_OK(item.lig >= 0 && item.lig < A.bounds.ligands, A.status, 12)) return;
   const LigInfo li = A.ligs[item.lig];
   const int G = 7 + li.k;
   const int64_t goff = A.geno_off[item.lig];
@@ -70,7 +74,8 @@ __device__ __forceinline__ void search_item(const SearchArgs &A, const Item &ite
 #pragma unroll
   for (int e = 0; e < DOCK_MAX_GENES; ++e)
     if (e < G && (e & (L - 1)) == lane) gout[e] = g[e];
-  const LigView V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors);
+  const LigView V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors, DK_BOUNDS(A),
+                             slot_stride(L, A.atoms_per_lane));
   float4 *sl = smem4 + slot * slot_stride(L, A.atoms_per_lane);
   float score;
   if constexpr (PW) {
@@ -190,7 +195,8 @@ __device__ __forceinline__ void score_one(const ScoreArgs &A, float4 *smem4) {
   const float *src = A.genos + pose * DOCK_MAX_GENES;
 #pragma unroll
   for (int e = 0; e < DOCK_MAX_GENES; ++e) g[e] = e < 7 + li.k ? src[e] : 0.0f;
-  const LigView V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors);
+  const LigView V = lig_view(li, A.atoms, A.types, A.pair_rec, A.tors, DK_BOUNDS(A),
+                             slot_stride(L, A.atoms_per_lane));
   float *co = A.coords ? A.coords + pose * (DOCK_MAX_ATOMS * 3) : nullptr;
   float4 *sl = smem4 + slot * slot_stride(L, A.atoms_per_lane);
   const float score = pose_and_score<L>(g, V, A.moves, A.grid, A.cx, A.cy, A.cz, sl, lane,

@@ -13,7 +13,10 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libdock.so")
+# DOCK_CHECKED=1 in the environment loads the bounds-checked build instead
+# (libdock_checked.so, made by build.build(checked=True)).
+LIB_PATH = os.path.join(_PKG, "libdock_checked.so" if os.environ.get("DOCK_CHECKED") == "1"
+                        else "libdock.so")
 
 DOCK_OK, DOCK_EINVAL, DOCK_ENOMEM, DOCK_ECUDA, DOCK_ETIMEOUT, DOCK_EDEVICE, DOCK_ENOTIMPL = \
     0, -1, -2, -3, -4, -5, -6
@@ -118,8 +121,9 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libdock.so is not built: run paper_2509_12232_gb300.build.build() "
-                               "(nvcc, sm_103a); there is no CPU fallback")
+            raise RuntimeError("%s is not built: run paper_2509_12232_gb300.build.build() "
+                               "(nvcc, sm_103a); there is no CPU fallback"
+                               % os.path.basename(LIB_PATH))
         L = C.CDLL(LIB_PATH)
         vp = C.c_void_p
         L.dock_last_error.restype = C.c_char_p
