@@ -584,6 +584,7 @@ extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *
   }
   if (np > INT32_MAX || nm > INT32_MAX) return fail(DOCK_EINVAL, "dock_load_ligands: batch too large");
   L->total_pairs = nvar;
+  L->total_pair_slots = np;
   std::vector<float4> atoms((size_t)n_atoms), raw((size_t)n_atoms);
   std::vector<double> cent((size_t)nl * 3);
   std::vector<uint32_t> pidx((size_t)np);

@@ -198,6 +198,7 @@ struct dock_ligands {
   TorInfo *d_tors = nullptr;
   uint8_t *d_moves = nullptr;
   int32_t *d_check = nullptr;  // index-check word of calls without a status word (checked build)
+  int64_t total_pair_slots = 0;  // pair_idx / pair_rec entries (all included pairs)
   int64_t total_pairs = 0, total_atoms = 0, total_tors = 0, total_moved = 0, h2d_bytes = 0;
   Workspace ws;
   ~dock_ligands() {
@@ -220,7 +221,7 @@ inline Bounds bounds_of(const dock_pocket *p, const dock_ligands *l, int32_t *wo
   Bounds b;
   b.word = word;
   b.atoms = l->total_atoms;
-  b.pairs = l->total_pairs;
+  b.pairs = l->total_pair_slots;
   b.tors = l->total_tors;
   b.moves = l->total_moved;
   b.ligands = l->n_ligands;
