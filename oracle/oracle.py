@@ -17,6 +17,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = [os.path.join(_HERE, "oracle.c"), os.path.join(_HERE, "surrogate.c")]
 _LIB = os.path.join(_HERE, "liboracle.so")
+# the FP32 auto-vectorised CPU baseline (simd_fp32.c) links the oracle's GA
+_SRC32 = os.path.join(_HERE, "simd_fp32.c")
+_LIB32 = os.path.join(_HERE, "libcpu32.so")
 
 EMAX = 1.0e5
 EOUT = 1000.0
@@ -37,7 +40,45 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+def build_cpu32(force: bool = False) -> str:
+    """Compile libcpu32.so: simd_fp32.c at -O3 -ffast-math -fopenmp-simd (the
+    paper's auto-vectorised FP32 style) linked with oracle.c built as for
+    liboracle.so (its GA and topology)."""
+    srcs = [_SRC[0], _SRC32]
+    stale = force or not os.path.exists(_LIB32) or any(
+        os.path.getmtime(s) > os.path.getmtime(_LIB32) for s in srcs)
+    if stale:
+        pid = os.getpid()
+        o1, o2 = _LIB32 + ".%d.oracle.o" % pid, _LIB32 + ".%d.simd.o" % pid
+        tmp = _LIB32 + ".%d.tmp" % pid
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-ffp-contract=off",
+                               "-fno-fast-math", "-pthread", "-c", _SRC[0], "-o", o1])
+        subprocess.check_call(["gcc", "-O3", "-std=gnu11", "-fPIC", "-ffast-math", "-fopenmp-simd",
+                               "-pthread", "-c", _SRC32, "-o", o2])
+        subprocess.check_call(["gcc", "-shared", "-pthread", "-o", tmp, o1, o2, "-lm"])
+        os.replace(tmp, _LIB32)
+        for f in (o1, o2):
+            os.unlink(f)
+    return _LIB32
+
+
 _lib = None
+_lib32 = None
+
+
+def lib32():
+    global _lib32
+    if _lib32 is None:
+        L = C.CDLL(build_cpu32())
+        L.cpu32_score_poses.restype = C.c_int
+        L.cpu32_score_poses.argtypes = [C.POINTER(OrcLigand), C.POINTER(OrcParams), C.POINTER(OrcGrid),
+                                        P_d, P_f, C.c_int, C.c_int64, P_f]
+        L.cpu32_dock_batch.restype = None
+        L.cpu32_dock_batch.argtypes = [C.POINTER(OrcBatch), C.POINTER(OrcParams), C.POINTER(OrcPocket),
+                                       C.POINTER(OrcGrid), C.c_int, C.c_int, C.c_float, C.c_float,
+                                       C.c_uint64, C.c_int, P_f, P_i32, P_f, P_f]
+        _lib32 = L
+    return _lib32
 
 
 def lib():
@@ -598,3 +639,44 @@ def standardize_targets(scores, clip: float):
     t = np.minimum(np.asarray(scores, np.float64), clip)
     mean = t.mean()
     return mean, float(np.sqrt(max((t * t).mean() - mean * mean, 1e-12)))
+
+
+# ---------------------------------------------------------------------------
+# FP32 auto-vectorised CPU baseline (simd_fp32.c): a second CPU reference
+# point for the benchmark, not part of the oracle's parity role
+# ---------------------------------------------------------------------------
+def cpu32_score_poses(lig: Ligand, params: Params, grid: Grid, center, genos) -> np.ndarray:
+    g = _c(genos, np.float32).reshape(-1, lig.n_genes)
+    out = np.zeros(g.shape[0], np.float32)
+    c = _c(center, np.float64)
+    if lib32().cpu32_score_poses(C.byref(lig.s), C.byref(params.s), C.byref(grid.s), _p(c, P_d),
+                                 _p(g, P_f), lig.n_genes, g.shape[0], _p(out, P_f)) < 0:
+        raise ValueError("bad ligand topology")
+    return out
+
+
+def cpu32_dock_batch(ligs, params: Params, pocket: PocketS, grid: Grid, pop: int, generations: int,
+                     p_cross: float = 0.8, p_mut: float = 0.02, seed: int = 0, n_threads: int = 0,
+                     trace: bool = False):
+    """The plain GA search with FP32 auto-vectorised scoring; with trace, the
+    genotypes and scores of every generation of ligand 0."""
+    a = dict(atom_off=_c(ligs.atom_off, np.int32), tors_off=_c(ligs.tors_off, np.int32),
+             x=_c(ligs.x, np.float32), y=_c(ligs.y, np.float32), z=_c(ligs.z, np.float32),
+             q=_c(ligs.q, np.float32), type=_c(ligs.type, np.uint8),
+             parent=_c(ligs.parent, np.int16), tors_b=_c(ligs.tors_b, np.int16),
+             ligand_id=_c(ligs.ligand_id, np.uint64))
+    nl = int(a["atom_off"].shape[0] - 1)
+    b = OrcBatch(nl, _p(a["atom_off"], P_i32), _p(a["tors_off"], P_i32), _p(a["x"], P_f),
+                 _p(a["y"], P_f), _p(a["z"], P_f), _p(a["q"], P_f), _p(a["type"], P_u8),
+                 _p(a["parent"], P_i16), _p(a["tors_b"], P_i16), _p(a["ligand_id"], P_u64))
+    score = np.zeros((nl, pop), np.float32)
+    best = np.zeros(nl, np.int32)
+    G0 = 7 + int(a["tors_off"][1] - a["tors_off"][0]) if nl else 7
+    tg = np.zeros((generations, pop, G0), np.float32) if trace else None
+    ts = np.zeros((generations, pop), np.float32) if trace else None
+    nt = n_threads or (os.cpu_count() or 1)
+    lib32().cpu32_dock_batch(C.byref(b), C.byref(params.s), C.byref(pocket.s), C.byref(grid.s),
+                             pop, generations, p_cross, p_mut, seed, nt, _p(score, P_f),
+                             _p(best, P_i32), _p(tg, P_f) if trace else None,
+                             _p(ts, P_f) if trace else None)
+    return dict(score=score, best=best, trace_geno=tg, trace_score=ts, threads=nt)
