@@ -242,20 +242,9 @@ extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_
   CU(launch_xycell_maps(P->d_maps, P->d_fpm, P->n_types, P->n, P->d_xycell, s));
   {
     const size_t n4 = (size_t)P->n_types * 2 * P->n * (P->n - 1) * (P->n - 1) * 2;
-    int max_w = 0;
-    CU(cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture1DLinearWidth, P->device));
-    if (n4 > (size_t)max_w || n4 > (size_t)INT32_MAX)
-      return fail(DOCK_EINVAL, "dock_create_pocket: %zu grid records exceed the texture limit", n4 / 2);
-    cudaResourceDesc rd;
-    memset(&rd, 0, sizeof rd);
-    rd.resType = cudaResourceTypeLinear;
-    rd.res.linear.devPtr = P->d_xycell;
-    rd.res.linear.desc = cudaCreateChannelDesc<float4>();
-    rd.res.linear.sizeInBytes = n4 * sizeof(float4);
-    cudaTextureDesc td;
-    memset(&td, 0, sizeof td);
-    td.readMode = cudaReadModeElementType;
-    CU(cudaCreateTextureObject(&P->xytex, &rd, &td, nullptr));
+    // the scorers index the records' 16-byte elements with 32-bit integers
+    if (n4 > (size_t)INT32_MAX)
+      return fail(DOCK_EINVAL, "dock_create_pocket: %zu grid records exceed 2^30", n4 / 2);
   }
   // the tables above are freed on return: wait for the kernels that read them
   CU(cudaStreamSynchronize(s));

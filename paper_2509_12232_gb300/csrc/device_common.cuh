@@ -417,10 +417,9 @@ __device__ __forceinline__ float pair_energy16(float r2, float c12, float cb, fl
 
 // Grid lookup of M_t + q E + |q| D split in two halves so other work can run
 // while the loads are in flight: grid_issue computes the cell and fetches the
-// two 32-byte (x, y)-cell records (planes z and z+1) through the texture path
-// (point fetches of float4 elements, no filtering: the interpolation is done
-// here in FP32), which keeps the gathers off the load/store pipe that the
-// coordinate and pair-record traffic uses; grid_finish interpolates. A point
+// two 32-byte (x, y)-cell records (planes z and z+1) with one 256-bit load
+// each, not allocated in L1 (interpolated here in FP32, no texture
+// filtering); grid_finish interpolates. A point
 // outside the grid box (faces count as inside) gives EOUT.
 struct Lookup {
   float c0[8], c1[8];
@@ -443,17 +442,20 @@ __device__ __forceinline__ Lookup grid_issue(const GridView &G, int t, float q, 
     L.fz = uz - (float)iz;
     const int nc = G.n - 1;
     const int sg = q < 0.0f ? 1 : 0;
-    // 32-bit element index: the texture holds at most 2^27 elements
+    // 32-bit element index (dock_create_pocket bounds the record count)
     int e = ((((2 * t + sg) * G.n + iz) * nc + iy) * nc + ix) * 2;
     if (!DK_OK(e >= 0 && e + G.plane_elems + 1 < G.tex_elems && t < G.n_types, check_word, 9))
       e = 0;
     const int ez = e + G.plane_elems;
-    const float4 a0 = tex1Dfetch<float4>(G.xytex, e), a1 = tex1Dfetch<float4>(G.xytex, e + 1);
-    const float4 b0 = tex1Dfetch<float4>(G.xytex, ez), b1 = tex1Dfetch<float4>(G.xytex, ez + 1);
-    L.c0[0] = a0.x; L.c0[1] = a0.y; L.c0[2] = a0.z; L.c0[3] = a0.w;
-    L.c0[4] = a1.x; L.c0[5] = a1.y; L.c0[6] = a1.z; L.c0[7] = a1.w;
-    L.c1[0] = b0.x; L.c1[1] = b0.y; L.c1[2] = b0.z; L.c1[3] = b0.w;
-    L.c1[4] = b1.x; L.c1[5] = b1.y; L.c1[6] = b1.z; L.c1[7] = b1.w;
+    // two 256-bit loads that do not allocate in L1 (the records are read
+    // once per atom; L1 keeps the pair records and coordinates instead)
+    const float *pz0 = G.xycell + (int64_t)e * 4, *pz1 = G.xycell + (int64_t)ez * 4;
+    asm volatile("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(L.c0[0]), "=f"(L.c0[1]), "=f"(L.c0[2]), "=f"(L.c0[3]), "=f"(L.c0[4]),
+                   "=f"(L.c0[5]), "=f"(L.c0[6]), "=f"(L.c0[7]) : "l"(pz0));
+    asm volatile("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(L.c1[0]), "=f"(L.c1[1]), "=f"(L.c1[2]), "=f"(L.c1[3]), "=f"(L.c1[4]),
+                   "=f"(L.c1[5]), "=f"(L.c1[6]), "=f"(L.c1[7]) : "l"(pz1));
   }
   return L;
 }

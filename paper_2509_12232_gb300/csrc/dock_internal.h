@@ -36,7 +36,7 @@ struct Bounds {
   int64_t atoms, pairs;    // atom rows, FP32 pair records of the ligand set
   int64_t tors, moves;     // torsion records, moved-atom entries
   int32_t ligands;
-  int32_t tex_elems;       // float4 elements of the map records' texture
+  int32_t tex_elems;       // 16-byte elements of the map records
   int32_t prot_atoms;      // protein atoms of the cell list
   int32_t slot_rows;       // float4 rows of one pose's shared-memory slot
 };
@@ -68,7 +68,6 @@ struct Item {
 
 struct GridView {
   const float4 *maps;   // [n_types][n][n][n] {M_t, E, D, 0}
-  cudaTextureObject_t xytex;  // the xycell records as a linear float4 texture (2 per record)
   const float *xycell;  // [n_types][2][n][n-1][n-1] (x, y)-cell records, 8 floats, 32-byte
                         // aligned: {M, F} at (x,y), (x+1,y), (x,y+1), (x+1,y+1) with
                         // F = E + D (sign 0, for q >= 0) or E - D (sign 1, q < 0), so
@@ -77,9 +76,9 @@ struct GridView {
   float ox, oy, oz;     // origin
   float inv_h;
   float gx, gy, gz;     // -origin / h: grid coordinate u = x inv_h + g
-  int32_t plane_elems;  // texture elements of one z plane of records, 2 (n-1)^2
+  int32_t plane_elems;  // 16-byte elements of one z plane of records, 2 (n-1)^2
   int32_t n_types;
-  int32_t tex_elems;    // texture elements of all records, 2 n_types 2 n (n-1)^2
+  int32_t tex_elems;    // 16-byte elements of all records, 2 n_types 2 n (n-1)^2
 };
 
 // Protein atoms by cell: cells are kCellX wide in x and kCellYZ in y and z

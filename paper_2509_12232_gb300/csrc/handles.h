@@ -46,7 +46,6 @@ struct dock_pocket {
   int n_prot = 0;
   float4 *d_maps = nullptr;
   float *d_xycell = nullptr;  // (x, y)-cell records of the FP32 scorer
-  cudaTextureObject_t xytex = 0;  // d_xycell as a linear float4 texture
   float2 *d_fpm = nullptr;    // per node {E + D, E - D}
   int n = 0;
   double ox = 0, oy = 0, oz = 0, h = 0;
@@ -59,7 +58,6 @@ struct dock_pocket {
   float cell_lo[3] = {0, 0, 0};
   int cell_dims[3] = {1, 1, 1};
   ~dock_pocket() {
-    if (xytex) cudaDestroyTextureObject(xytex);
     dfree(d_cprot);
     dfree(d_cext);
     dfree(d_tpair);
@@ -76,7 +74,6 @@ inline GridView grid_view(const dock_pocket *p) {
   GridView g;
   g.maps = p->d_maps;
   g.xycell = p->d_xycell;
-  g.xytex = p->xytex;
   g.n = p->n;
   g.ox = (float)p->ox;
   g.oy = (float)p->oy;

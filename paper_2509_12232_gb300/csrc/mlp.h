@@ -43,6 +43,12 @@ __device__ __forceinline__ float gelu_as(float z) {
   return 0.5f * fmaf(fabsf(z), 1.0f - r, z);
 }
 
+// d GELU / dz with the exact erf (the backward pass of every training path).
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) +
+         z * 0.39894228040143268f * __expf(-0.5f * z * z);
+}
+
 struct Epilogue {
   float *c32;               // FP32 output (STORE) or pre-activation cache (BIAS_GELU), or null
   __nv_bfloat16 *c16;       // BF16 output (BIAS_GELU: activation; GELU_BWD: dZ)
@@ -52,15 +58,6 @@ struct Epilogue {
   int64_t split_stride;     // STORE with split K: elements between the splits' partial outputs
 };
 
-// C = A Bt^T: A [M][K] row-major, Bt [N][K] row-major.
-cudaError_t gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb, int M, int N,
-                    int K, int epi, const Epilogue &ep, cudaStream_t s);
-// C (FP32, ldc = N) = A^T B: A stored [K][M], B stored [K][N] (weight
-// gradients). K is split over CTAs when scratch (scratch_elems floats) holds
-// the partial products; the partials are summed in a fixed order.
-cudaError_t gemm_tt_f32(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *B, int ldb, int M,
-                        int N, int K, float *C, float *scratch, int64_t scratch_elems,
-                        cudaStream_t s);
 cudaError_t out_layer(const __nv_bfloat16 *H, const float *w, const float *b, int rows, float *y,
                       cudaStream_t s);
 cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const __nv_bfloat16 *H3,
@@ -70,8 +67,9 @@ cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const
 // (scratch: at least 64 * cols floats).
 cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, float *scratch,
                    cudaStream_t s);
+// Adam step t = *step_dev if step_dev is given (read on the device), else step.
 cudaError_t adam(float *p, float *m, float *v, const float *g, int n, float lr, int step,
-                 cudaStream_t s);
+                 const int *step_dev, cudaStream_t s);
 cudaError_t cast_weights(const float *W, int in, int out, __nv_bfloat16 *w16, __nv_bfloat16 *wt16,
                          cudaStream_t s);
 
@@ -84,6 +82,21 @@ cudaError_t canon_weights(const float *p, __nv_bfloat16 *wc, cudaStream_t s);
 int canon_weight_elems();
 cudaError_t fused_forward(const __nv_bfloat16 *X, int64_t n, const __nv_bfloat16 *wc,
                           const float *params, float *y, int *err, cudaStream_t s);
+
+// Training products on the tensor cores (tcgen05, FP32 accumulator in tensor
+// memory; mlp_tc.cu). C = A Bt^T with A [M][K] and Bt [256][K] BF16,
+// K-major rows (lda, ldb elements, 16-byte aligned), M a multiple of 128, K
+// of 64; the epilogues of gemm_nt (bias + GELU, GELU backward, FP32 store).
+// *err is set if a device wait runs out (the output is then incomplete).
+cudaError_t tc_gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb, int M,
+                       int K, int epi, const Epilogue &ep, int *err, cudaStream_t s);
+// C (FP32 [M][256]) = A^T B for A stored [K][M] and B stored [K][256] (the
+// weight gradients): both transposed to K-major copies (at and bt, M x K and
+// 256 x K BF16), K split over CTAs with FP32 partials in scratch (split x M x
+// 256 floats, split <= scratch_elems / (M 256)) summed in a fixed order.
+cudaError_t tc_gemm_tn_f32(const __nv_bfloat16 *A, int M, const __nv_bfloat16 *B, int K, float *C,
+                           __nv_bfloat16 *at, __nv_bfloat16 *bt, float *scratch,
+                           int64_t scratch_elems, int *err, cudaStream_t s);
 
 }  // namespace mlp
 }  // namespace dk

@@ -364,6 +364,207 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Training products on tcgen05: C[M][256] = A[M][K] Bt[256][K]^T.
+// CTA (blockIdx.x, split blockIdx.y, column half blockIdx.z) computes rows
+// m0 .. m0 + 127 and columns 128 z .. + 127 over its K range in chunks of 64
+// (two halves per row block double the CTAs of a 4,096-row batch): the 256
+// threads move a chunk of A (128 x 64) and of Bt (its 128 rows x 64) from
+// global memory into one of two stages in the K-major core-matrix layout (a
+// warp stores eight rows x 16 bytes of one K block per 128-byte step), one
+// thread issues four MMAs (M 128, N 128, K 16) into the 128-column FP32
+// accumulator and commits them to the stage's mbarrier, and the next
+// chunk's global loads are in flight meanwhile. The epilogue reads the
+// accumulator with tcgen05.ld: warp w takes lanes 32 (w mod 4) .. + 31 and
+// columns 64 (w / 4) .. + 63. Every mbarrier wait is bounded as in the
+// forward kernel; a timeout sets *err and the CTA writes nothing.
+// ---------------------------------------------------------------------------
+constexpr int GK = 64;                     // K per chunk
+constexpr int GA_BYTES = 128 * GK * 2;     // A chunk: 16 KB
+constexpr int GN = 128;                    // columns per CTA
+constexpr int GB_BYTES = GN * GK * 2;      // Bt chunk: 16 KB
+constexpr int G_STAGE = GA_BYTES + GB_BYTES;
+constexpr int G_SMEM = 2 * G_STAGE + 64;
+constexpr int G_THREADS = 256;
+
+template <int EPI>
+__global__ void __launch_bounds__(G_THREADS, 3)
+    tc_gemm_kernel(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb, int k_split,
+                   Epilogue ep, int *err) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * G_STAGE);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * 128;
+  const int64_t k0 = (int64_t)blockIdx.y * k_split;
+  const int n0 = GN * blockIdx.z;
+  Bt += (int64_t)n0 * ldb;
+  const int nc = k_split / GK;
+  const uint32_t bar[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
+  if (tid == 0) {
+    mbar_init(bar[0], 1);
+    mbar_init(bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     smem_u32(tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tmem = *tslot;
+  // a chunk in 16-byte pieces: step v of a warp covers rows 8 (v mod G) + (lane
+  // mod 8) and K block 4 (v / G) + lane / 8 (G = row groups of the operand)
+  uint4 ra[4], rb[4];
+  auto load = [&](int c) {
+    const int64_t kk = k0 + (int64_t)c * GK;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int v = warp + 8 * i, row = 8 * (v & 15) + (lane & 7), kb = 4 * (v >> 4) + (lane >> 3);
+      ra[i] = __ldg(reinterpret_cast<const uint4 *>(A + (m0 + row) * lda + kk + 8 * kb));
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int v = warp + 8 * i, row = 8 * (v & 15) + (lane & 7), kb = 4 * (v >> 4) + (lane >> 3);
+      rb[i] = __ldg(reinterpret_cast<const uint4 *>(Bt + (int64_t)row * ldb + kk + 8 * kb));
+    }
+  };
+  auto store = [&](int st) {
+    unsigned char *sa = sm + st * G_STAGE, *sb = sa + GA_BYTES;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int v = warp + 8 * i, row = 8 * (v & 15) + (lane & 7), kb = 4 * (v >> 4) + (lane >> 3);
+      *reinterpret_cast<uint4 *>(sa + canon_off(row, 8 * kb, GK)) = ra[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int v = warp + 8 * i, row = 8 * (v & 15) + (lane & 7), kb = 4 * (v >> 4) + (lane >> 3);
+      *reinterpret_cast<uint4 *>(sb + canon_off(row, 8 * kb, GK)) = rb[i];
+    }
+  };
+  uint32_t ph[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool ok = nc > 0;
+  if (ok) load(0);
+  for (int c = 0; c < nc && ok; ++c) {
+    const int st = c & 1;
+    if (pending[st]) {  // the products of chunk c - 2 have read this stage
+      ok = __syncthreads_and(mbar_wait(bar[st], ph[st]));
+      if (!ok) break;
+      pending[st] = false;
+      ph[st] ^= 1u;
+    }
+    store(st);
+    fence_proxy_async();
+    __syncthreads();
+    if (c + 1 < nc) load(c + 1);
+    if (tid == 0) {
+      fence_after_sync();
+      const uint32_t sa = smem_u32(sm + st * G_STAGE), sb = sa + GA_BYTES;
+#pragma unroll
+      for (int q = 0; q < GK / 16; ++q)
+        mma_bf16(tmem, sdesc(sa + 256u * q, 128u, GK * 16), sdesc(sb + 256u * q, 128u, GK * 16),
+                 idesc_bf16(128, GN), (c > 0 || q > 0) ? 1u : 0u);
+      mma_commit(bar[st]);
+    }
+    pending[st] = true;
+  }
+  if (ok) {  // the last commit covers every product before it
+    const int st = (nc - 1) & 1;
+    ok = __syncthreads_and(mbar_wait(bar[st], ph[st]));
+    if (ok) {
+      pending[0] = pending[1] = false;
+      ph[st] ^= 1u;
+    }
+  }
+  if (ok) {
+    fence_after_sync();
+    const int quad = warp & 3, half = warp >> 2;
+    const int64_t row = m0 + 32 * quad + lane;
+    const uint32_t t_lane = tmem + ((uint32_t)(32 * quad) << 16);
+#pragma unroll 1
+    for (int cc = 0; cc < 2; ++cc) {
+      const int tcol = 64 * half + 32 * cc, col = n0 + tcol;
+      uint32_t r[32];
+      tmem_ld32(t_lane + (uint32_t)tcol, r);
+      tmem_wait(r);
+      const int64_t o = row * ep.ldc + col;
+      if (EPI == EPI_STORE_F32) {
+        float4 *dst = reinterpret_cast<float4 *>(ep.c32 + (int64_t)blockIdx.y * ep.split_stride + o);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                               __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+      } else if (EPI == EPI_BIAS_GELU) {
+        uint32_t h[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 b = *reinterpret_cast<const float4 *>(ep.bias + col + 4 * j);
+          const float z0 = __uint_as_float(r[4 * j]) + b.x, z1 = __uint_as_float(r[4 * j + 1]) + b.y;
+          const float z2 = __uint_as_float(r[4 * j + 2]) + b.z, z3 = __uint_as_float(r[4 * j + 3]) + b.w;
+          if (ep.c32) reinterpret_cast<float4 *>(ep.c32 + o)[j] = make_float4(z0, z1, z2, z3);
+          h[2 * j] = pack_bf16(gelu_as(z0), gelu_as(z1));
+          h[2 * j + 1] = pack_bf16(gelu_as(z2), gelu_as(z3));
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(ep.c16 + o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dst[j] = make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
+      } else {  // EPI_GELU_BWD: dZ = dH gelu'(Z)
+        uint32_t h[16];
+        const float4 *zin = reinterpret_cast<const float4 *>(ep.zin + o);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float4 z = zin[j];
+          h[2 * j] = pack_bf16(__uint_as_float(r[4 * j]) * gelu_grad(z.x),
+                               __uint_as_float(r[4 * j + 1]) * gelu_grad(z.y));
+          h[2 * j + 1] = pack_bf16(__uint_as_float(r[4 * j + 2]) * gelu_grad(z.z),
+                                   __uint_as_float(r[4 * j + 3]) * gelu_grad(z.w));
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(ep.c16 + o);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dst[j] = make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
+      }
+    }
+  }
+  // ---- teardown: products in flight finish, then the tensor memory is freed
+  for (int st = 0; st < 2; ++st)
+    if (pending[st]) mbar_wait(bar[st], ph[st]);
+  if (!ok && tid == 0 && nc > 0) atomicExch(err, 1);
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
+// out [cols][rows] = in [rows][cols]^T (BF16; 32 x 32 tiles through shared memory).
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *in, int rows, int cols,
+                                      __nv_bfloat16 *out) {
+  __shared__ __nv_bfloat16 t[32][33];
+  const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) t[i][threadIdx.x] = in[(int64_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) out[(int64_t)c * rows + r] = t[threadIdx.x][i];
+  }
+}
+
+// out[c] = sum of the `parts` partials in order 0, 1, ... (fixed order).
+__global__ void sum_parts_kernel(const float *part, int parts, int64_t width, float *out) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= width) return;
+  float s = 0.0f;
+  for (int b = 0; b < parts; ++b) s += part[(int64_t)b * width + c];
+  out[c] = s;
+}
+
 // Layers 1-3 of the packed FP32 parameters (W stored [in][out]) as BF16
 // B operands (N = 256 outputs x K inputs) in the K-major core-matrix layout.
 __global__ void canon_weights_kernel(const float *p, __nv_bfloat16 *wc) {
@@ -412,6 +613,65 @@ cudaError_t fused_forward(const __nv_bfloat16 *X, int64_t n, const __nv_bfloat16
 }
 
 int canon_weight_elems() { return WC_L3 + HIDDEN * HIDDEN; }
+
+template <int EPI>
+static cudaError_t tc_gemm_launch(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt,
+                                  int ldb, int M, int k_split, int splits, const Epilogue &ep,
+                                  int *err, cudaStream_t s) {
+  // the shared-memory attribute once per device (also keeps it out of graph captures)
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    e = cudaFuncSetAttribute(tc_gemm_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             G_SMEM);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  tc_gemm_kernel<EPI><<<dim3(M / 128, splits, HIDDEN / GN), G_THREADS, G_SMEM, s>>>(
+      A, lda, Bt, ldb, k_split, ep, err);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb, int M,
+                       int K, int epi, const Epilogue &ep, int *err, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  if (M % 128 || K % GK || K <= 0 || lda % 8 || ldb % 8) return cudaErrorInvalidValue;
+  switch (epi) {
+    case EPI_STORE_F32: return tc_gemm_launch<EPI_STORE_F32>(A, lda, Bt, ldb, M, K, 1, ep, err, s);
+    case EPI_BIAS_GELU: return tc_gemm_launch<EPI_BIAS_GELU>(A, lda, Bt, ldb, M, K, 1, ep, err, s);
+    case EPI_GELU_BWD: return tc_gemm_launch<EPI_GELU_BWD>(A, lda, Bt, ldb, M, K, 1, ep, err, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t tc_gemm_tn_f32(const __nv_bfloat16 *A, int M, const __nv_bfloat16 *B, int K, float *C,
+                           __nv_bfloat16 *at, __nv_bfloat16 *bt, float *scratch,
+                           int64_t scratch_elems, int *err, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  if (M % 128 || K % GK || K <= 0) return cudaErrorInvalidValue;
+  const dim3 tb(32, 8);
+  transpose_bf16_kernel<<<dim3((M + 31) / 32, (K + 31) / 32), tb, 0, s>>>(A, K, M, at);
+  transpose_bf16_kernel<<<dim3((HIDDEN + 31) / 32, (K + 31) / 32), tb, 0, s>>>(B, K, HIDDEN, bt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // enough K splits to give about 128 CTAs, each a multiple of the chunk
+  int splits = 1;
+  const int tiles = (M / 128) * (HIDDEN / GN);
+  while (splits < 64 && tiles * splits < 128 && K % (GK * splits * 2) == 0 &&
+         (int64_t)splits * 2 * M * HIDDEN <= scratch_elems)
+    splits *= 2;
+  Epilogue ep{};
+  ep.ldc = HIDDEN;
+  ep.c32 = splits > 1 ? scratch : C;
+  ep.split_stride = (int64_t)M * HIDDEN;
+  e = tc_gemm_launch<EPI_STORE_F32>(at, K, bt, K, M, K / splits, splits, ep, err, s);
+  if (e != cudaSuccess || splits == 1) return e;
+  const int64_t w = (int64_t)M * HIDDEN;
+  sum_parts_kernel<<<(unsigned)((w + 255) / 256), 256, 0, s>>>(scratch, splits, w, C);
+  return cudaGetLastError();
+}
 
 }  // namespace mlp
 }  // namespace dk

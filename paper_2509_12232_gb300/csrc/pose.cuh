@@ -50,9 +50,10 @@ __device__ __forceinline__ LigView lig_view(const LigInfo &li, const float4 *ato
   v.n_pairs = li.n_pairs;
   v.intra_const = li.intra_const;
 #ifdef DOCK_CHECKED
+  // without bounds (callers outside the checked kernels) every check passes
   v.word = b ? b->word : nullptr;
-  v.moves = b ? b->moves : 0;
-  v.rows = slot_rows;
+  v.moves = b ? b->moves : INT64_MAX;
+  v.rows = b ? slot_rows : (1 << 20);
   if (b) {
     const bool ok = DK_OK((int64_t)li.atom_off + li.n <= b->atoms && li.atom_off >= 0, v.word, 1) &&
                     DK_OK((int64_t)li.pair_off + li.n_pairs <= b->pairs && li.pair_off >= 0,

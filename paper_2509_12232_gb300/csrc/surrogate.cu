@@ -93,12 +93,14 @@ __device__ __forceinline__ uint64_t train_row(const TrainOrder &o, uint64_t r) {
 // Gathers `rows` rows (r < rows_valid real, the rest zero) into the batch:
 // with use_order, row r is training row pi(r0 + r), else row r.
 __global__ void gather_rows_kernel(const __nv_bfloat16 *X, const float *t, int use_order,
-                                   TrainOrder o, int64_t r0, int64_t n_src, int rows,
+                                   TrainOrder o, int64_t r0, const int64_t *r0_dev, int64_t n_src,
+                                   int rows,
                                    int rows_valid, __nv_bfloat16 *Xb, float *tb, float t_mean,
                                    float t_inv_std, float t_clip) {
   // one warp per row: 128 bf16 = 256 bytes = 32 lanes x 8 bytes
   const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (r >= rows) return;
+  if (r0_dev) r0 = *r0_dev;  // graph-replayed step: the batch start lives on the device
   uint2 v = make_uint2(0, 0);
   float tv = 0.0f;
   if (r < rows_valid) {
@@ -110,6 +112,16 @@ __global__ void gather_rows_kernel(const __nv_bfloat16 *X, const float *t, int u
   }
   reinterpret_cast<uint2 *>(Xb + (int64_t)r * FEATURES)[lane] = v;
   if (lane == 0 && tb) tb[r] = tv;
+}
+
+// The device counters of a graph-replayed training step.
+__global__ void set_counters_kernel(int64_t *r0, int64_t r0_value, int *step, int step_value) {
+  *r0 = r0_value;
+  *step = step_value;
+}
+__global__ void advance_counters_kernel(int64_t *r0, int64_t batch, int *step) {
+  *r0 += batch;
+  *step += 1;
 }
 
 // mean and sum of squares of min(t, clip) (double accumulation, one block)
@@ -153,8 +165,14 @@ struct dock_surrogate {
   __nv_bfloat16 *X = nullptr, *H[3] = {nullptr, nullptr, nullptr}, *dZ[3] = {nullptr, nullptr, nullptr};
   float *Z[3] = {nullptr, nullptr, nullptr}, *y = nullptr, *t = nullptr, *part = nullptr,
         *outg = nullptr;
+  // K-major copies of a weight gradient's operands (activations^T, dZ^T)
+  __nv_bfloat16 *at = nullptr, *bt = nullptr;
   double *stats = nullptr;
   int step = 0;
+  int64_t *d_r0 = nullptr;  // batch start and Adam step of a graph-replayed training step
+  int *d_step = nullptr;
+  cudaStream_t ts = nullptr;  // training runs (and its step graph is captured) on this stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   float t_mean = 0.0f, t_std = 1.0f, t_clip = 1e30f;
   // weights of the fused tensor-core forward pass (refreshed lazily after the
   // FP32 masters change) and its device error flag
@@ -167,6 +185,11 @@ struct dock_surrogate {
     if (wc) cudaFree(wc);
     if (err) cudaFree(err);
     if (wpart) cudaFree(wpart);
+    if (d_r0) cudaFree(d_r0);
+    if (d_step) cudaFree(d_step);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (ts) cudaStreamDestroy(ts);
     for (int l = 0; l < 3; ++l) {
       if (w16[l]) cudaFree(w16[l]);
       if (wt16[l]) cudaFree(wt16[l]);
@@ -175,6 +198,8 @@ struct dock_surrogate {
       if (Z[l]) cudaFree(Z[l]);
     }
     if (X) cudaFree(X);
+    if (at) cudaFree(at);
+    if (bt) cudaFree(bt);
     if (stats) cudaFree(stats);
   }
 };
@@ -188,6 +213,9 @@ static const int64_t kWpartElems = 32 * HIDDEN * HIDDEN;  // 32 K splits of a 25
 static int ensure_workspace(dock_surrogate *S, int rows) {
   if (rows <= S->cap) return DOCK_OK;
   if (S->X) cudaFree(S->X);
+  if (S->at) cudaFree(S->at);
+  if (S->bt) cudaFree(S->bt);
+  S->at = S->bt = nullptr;
   for (int l = 0; l < 3; ++l) {
     if (S->H[l]) cudaFree(S->H[l]);
     if (S->dZ[l]) cudaFree(S->dZ[l]);
@@ -201,6 +229,8 @@ static int ensure_workspace(dock_surrogate *S, int rows) {
   }
   S->cap = 0;
   SCU(cudaMalloc(&S->X, sizeof(__nv_bfloat16) * (size_t)rows * FEATURES));
+  SCU(cudaMalloc(&S->at, sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
+  SCU(cudaMalloc(&S->bt, sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
   for (int l = 0; l < 3; ++l) {
     SCU(cudaMalloc(&S->H[l], sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
     SCU(cudaMalloc(&S->dZ[l], sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
@@ -219,8 +249,9 @@ static int refresh_bf16(dock_surrogate *S, cudaStream_t s) {
   return DOCK_OK;
 }
 
-// Forward pass of `rows` rows already in S->X (rows a multiple of 128).
-// keep = true keeps FP32 pre-activations for the backward pass.
+// Forward pass of `rows` rows already in S->X (rows a multiple of 128), the
+// three hidden layers on the tensor cores (tcgen05). keep = true keeps FP32
+// pre-activations for the backward pass.
 static int forward(dock_surrogate *S, int rows, bool keep, cudaStream_t s) {
   const __nv_bfloat16 *in = S->X;
   for (int l = 0; l < 3; ++l) {
@@ -229,7 +260,8 @@ static int forward(dock_surrogate *S, int rows, bool keep, cudaStream_t s) {
     ep.c16 = S->H[l];
     ep.bias = S->p + kOffB[l];
     ep.ldc = HIDDEN;
-    SCU(mlp::gemm_nt(in, kIn[l], S->wt16[l], kIn[l], rows, HIDDEN, kIn[l], mlp::EPI_BIAS_GELU, ep, s));
+    SCU(mlp::tc_gemm_nt(in, kIn[l], S->wt16[l], kIn[l], rows, kIn[l], mlp::EPI_BIAS_GELU, ep,
+                        S->err, s));
     in = S->H[l];
   }
   SCU(mlp::out_layer(S->H[2], S->p + mlp::OFF_W4, S->p + mlp::OFF_B4, rows, S->y, s));
@@ -245,9 +277,10 @@ static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
                       cudaMemcpyDeviceToDevice, s));
   for (int l = 2; l >= 0; --l) {
     const __nv_bfloat16 *act_in = l ? S->H[l - 1] : S->X;
-    // dW_l = act_in^T dZ_l ; db_l = column sums of dZ_l
-    SCU(mlp::gemm_tt_f32(act_in, kIn[l], S->dZ[l], HIDDEN, kIn[l], HIDDEN, rows, S->g + kOffW[l],
-                         S->wpart, kWpartElems, s));
+    // dW_l = act_in^T dZ_l (tensor cores, K = rows split over CTAs); db_l =
+    // column sums of dZ_l
+    SCU(mlp::tc_gemm_tn_f32(act_in, kIn[l], S->dZ[l], rows, S->g + kOffW[l], S->at, S->bt,
+                            S->wpart, kWpartElems, S->err, s));
     SCU(mlp::colsum(S->dZ[l], rows, HIDDEN, S->g + kOffB[l], S->wpart, s));
     if (l) {
       // dZ_{l-1} = (dZ_l W_l^T) * gelu'(Z_{l-1})
@@ -255,9 +288,22 @@ static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
       ep.c16 = S->dZ[l - 1];
       ep.zin = S->Z[l - 1];
       ep.ldc = HIDDEN;
-      SCU(mlp::gemm_nt(S->dZ[l], HIDDEN, S->w16[l], HIDDEN, rows, HIDDEN, HIDDEN, mlp::EPI_GELU_BWD,
-                       ep, s));
+      SCU(mlp::tc_gemm_nt(S->dZ[l], HIDDEN, S->w16[l], HIDDEN, rows, HIDDEN, mlp::EPI_GELU_BWD,
+                          ep, S->err, s));
     }
+  }
+  return DOCK_OK;
+}
+
+// Waits for the stream; DOCK_EDEVICE (flag cleared) if a tensor-core kernel's
+// bounded device wait ran out since the last check.
+static int check_device_flag(dock_surrogate *S, cudaStream_t s, const char *what) {
+  int flag = 0;
+  SCU(cudaMemcpyAsync(&flag, S->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  SCU(cudaStreamSynchronize(s));
+  if (flag) {
+    SCU(cudaMemsetAsync(S->err, 0, sizeof(int), s));
+    return sfail(DOCK_EDEVICE, "%s: a device wait ran out (results incomplete)", what);
   }
   return DOCK_OK;
 }
@@ -279,6 +325,11 @@ extern "C" int dock_surrogate_create(uint64_t seed, void *stream, dock_surrogate
   SCU(cudaMalloc(&S->wc, sizeof(__nv_bfloat16) * mlp::canon_weight_elems()));
   SCU(cudaMalloc(&S->wpart, sizeof(float) * kWpartElems));
   SCU(cudaMalloc(&S->err, sizeof(int)));
+  SCU(cudaMalloc(&S->d_r0, sizeof(int64_t)));
+  SCU(cudaStreamCreateWithFlags(&S->ts, cudaStreamNonBlocking));
+  SCU(cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
+  SCU(cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming));
+  SCU(cudaMalloc(&S->d_step, sizeof(int)));
   SCU(cudaMemsetAsync(S->err, 0, sizeof(int), s));
   // He-normal weights, zero biases (host draw from the seed, one upload)
   std::vector<float> h(N_PARAMS, 0.0f);
@@ -378,12 +429,13 @@ extern "C" int dock_surrogate_gradients(dock_surrogate *S, const uint16_t *featu
   if (st != DOCK_OK) return st;
   // targets used as given (identity standardisation)
   gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(
-      reinterpret_cast<const __nv_bfloat16 *>(features), targets, 0, TrainOrder{}, 0, n, rows,
-      n, S->X, S->t, 0.0f, 1.0f, 3.0e38f);
+      reinterpret_cast<const __nv_bfloat16 *>(features), targets, 0, TrainOrder{}, 0, nullptr, n,
+      rows, n, S->X, S->t, 0.0f, 1.0f, 3.0e38f);
   SCU(cudaGetLastError());
   if ((st = forward(S, rows, true, s)) != DOCK_OK) return st;
   if ((st = backward(S, rows, n, s)) != DOCK_OK) return st;
   SCU(cudaMemcpyAsync(grad, S->g, sizeof(float) * N_PARAMS, cudaMemcpyDeviceToDevice, s));
+  if ((st = check_device_flag(S, s, "dock_surrogate_gradients")) != DOCK_OK) return st;
   if (loss) {
     SCU(cudaStreamSynchronize(s));
     float ls = 0.0f;
@@ -401,7 +453,12 @@ extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features,
       !(tp->lr > 0.0f))
     return sfail(DOCK_EINVAL, "dock_surrogate_train: bad sizes or learning rate");
   SCU(cudaSetDevice(S->device));
-  cudaStream_t s = (cudaStream_t)stream;
+  // the work runs on the surrogate's own stream, ordered after the caller's
+  // stream and before its later work (a graph can be captured there even
+  // when the caller passes the legacy default stream)
+  cudaStream_t caller = (cudaStream_t)stream, s = S->ts;
+  SCU(cudaEventRecord(S->ev_in, caller));
+  SCU(cudaStreamWaitEvent(s, S->ev_in, 0));
   int st = ensure_workspace(S, tp->batch);
   if (st != DOCK_OK) return st;
   // target standardisation over the training set: min(score, clip), then mean / std
@@ -420,29 +477,89 @@ extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features,
   const __nv_bfloat16 *F = reinterpret_cast<const __nv_bfloat16 *>(features);
   const int B = tp->batch;
   const int64_t steps_per_epoch = (n + B - 1) / B;
+  // one training step: gather, forward, backward, Adam, BF16 weight copies.
+  // dev: the batch start and the Adam step are read from the device counters
+  // (the form captured in a CUDA graph; the graph's last kernel advances them)
+  auto step_body = [&](int64_t r0, int valid, bool dev) -> int {
+    const int rows = (valid + 127) / 128 * 128;
+    gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(
+        F, scores, 1, ord, r0, dev ? S->d_r0 : nullptr, n, rows, valid, S->X, S->t, S->t_mean,
+        1.0f / S->t_std, clip);
+    SCU(cudaGetLastError());
+    int rc;
+    if ((rc = forward(S, rows, true, s)) != DOCK_OK) return rc;
+    if ((rc = backward(S, rows, valid, s)) != DOCK_OK) return rc;
+    SCU(mlp::adam(S->p, S->m, S->v, S->g, N_PARAMS, tp->lr, S->step + 1, dev ? S->d_step : nullptr,
+                  s));
+    if ((rc = refresh_bf16(S, s)) != DOCK_OK) return rc;
+    if (dev) {
+      advance_counters_kernel<<<1, 1, 0, s>>>(S->d_r0, B, S->d_step);
+      SCU(cudaGetLastError());
+    }
+    return DOCK_OK;
+  };
+  // full batches replay one captured graph of the step (captured at the first)
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  auto release = [&]() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+    gexec = nullptr;
+    graph = nullptr;
+  };
   for (int ep = 0; ep < tp->epochs; ++ep) {
     double ep_loss = 0.0;
     for (int64_t b = 0; b < steps_per_epoch; ++b) {
       const int64_t r0 = b * B;
       const int valid = (int)std::min<int64_t>(B, n - r0);
-      const int rows = (valid + 127) / 128 * 128;
-      gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(
-          F, scores, 1, ord, r0, n, rows, valid, S->X, S->t,
-          S->t_mean, 1.0f / S->t_std, clip);
-      SCU(cudaGetLastError());
-      if ((st = forward(S, rows, true, s)) != DOCK_OK) return st;
-      if ((st = backward(S, rows, valid, s)) != DOCK_OK) return st;
-      SCU(mlp::adam(S->p, S->m, S->v, S->g, N_PARAMS, tp->lr, ++S->step, s));
-      if ((st = refresh_bf16(S, s)) != DOCK_OK) return st;
+      if (valid == B) {
+        if (b == 0 || !gexec) {  // counters for this epoch's run of full batches
+          set_counters_kernel<<<1, 1, 0, s>>>(S->d_r0, r0, S->d_step, S->step + 1);
+          SCU(cudaGetLastError());
+        }
+        if (!gexec) {
+          SCU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+          st = step_body(r0, valid, true);
+          cudaError_t ce = cudaStreamEndCapture(s, &graph);
+          if (st != DOCK_OK) {
+            release();
+            return st;
+          }
+          if (ce == cudaSuccess) ce = cudaGraphInstantiate(&gexec, graph, 0);
+          if (ce != cudaSuccess) {
+            release();
+            return sfail(DOCK_ECUDA, "dock_surrogate_train: step graph: %s", cudaGetErrorString(ce));
+          }
+        }
+        cudaError_t le = cudaGraphLaunch(gexec, s);
+        if (le != cudaSuccess) {
+          release();
+          return sfail(DOCK_ECUDA, "dock_surrogate_train: %s", cudaGetErrorString(le));
+        }
+        ++S->step;
+      } else {
+        if ((st = step_body(r0, valid, false)) != DOCK_OK) {
+          release();
+          return st;
+        }
+        ++S->step;
+      }
       if (loss_per_epoch && (b == steps_per_epoch - 1 || (b & 63) == 0)) {
         float ls = 0.0f;
-        SCU(cudaMemcpyAsync(&ls, S->outg + HIDDEN + 1, sizeof(float), cudaMemcpyDeviceToHost, s));
-        SCU(cudaStreamSynchronize(s));
+        cudaError_t ce = cudaMemcpyAsync(&ls, S->outg + HIDDEN + 1, sizeof(float),
+                                         cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) {
+          release();
+          return sfail(DOCK_ECUDA, "dock_surrogate_train: %s", cudaGetErrorString(ce));
+        }
         ep_loss = ls / valid;
       }
     }
     if (loss_per_epoch) loss_per_epoch[ep] = (float)ep_loss;
   }
-  SCU(cudaStreamSynchronize(s));
-  return DOCK_OK;
+  release();
+  SCU(cudaEventRecord(S->ev_out, s));
+  SCU(cudaStreamWaitEvent(caller, S->ev_out, 0));
+  return check_device_flag(S, s, "dock_surrogate_train");
 }
