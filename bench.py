@@ -202,6 +202,20 @@ class Clocks:
                 "samples": len(rows)}
 
 
+def alu_peaks(dock, stream, n_sm, sm_mhz):
+    """(FP32 TFLOP/s, MUFU Tops/s, description): measured on this GPU by
+    dock_measure_peaks (independent FMA / ex2 chains on every SM), with the
+    unit-count figures (lanes x clock) beside them for reference."""
+    f, m = dock.dock_measure_peaks(stream)
+    spec_f = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    spec_m = n_sm * 16 * sm_mhz * 1e6 / 1e12
+    return f, m, {"peak_source": "measured: dock_measure_peaks (FFMA and ex2 chains on every SM)",
+                  "unit_count_peaks": {"fp32_tflops": round(spec_f, 2),
+                                       "mufu_tops": round(spec_m, 4),
+                                       "from": "%d SMs x 128 FP32 / 16 MUFU lanes x %.0f MHz"
+                                               % (n_sm, sm_mhz)}}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -402,8 +416,7 @@ def run_screen(args, rank, world):
     peaks, _ = measured_peaks()
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
-    mufu_peak = n_sm * 16 * sm_mhz * 1e6 / 1e12
+    fp32_peak, mufu_peak, peak_src = alu_peaks(dock, stream, n_sm, sm_mhz)
     flops_pose, mufu_pose = work_per_pose(info, probe.n_ligands)
     per_gen_s = ms_kernels / 1000.0 / max(n_launch, 1)
     ach = flops_pose * w.pop / per_gen_s / 1e12
@@ -426,10 +439,12 @@ def run_screen(args, rank, world):
                               "max": round(max(t for _, t in stats), 3)},
             "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2),
                          "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
-                         "kernel": "search_kernel",
+                         "kernel": "search_kernel", **peak_src,
                          "measured_on": "one profiled search of 2,000 ligands of chunk 0",
                          "mufu": {"achieved": round(mufu_pose * w.pop / per_gen_s / 1e12, 4),
-                                  "peak": round(mufu_peak, 4), "unit": "Tops/s"},
+                                  "peak": round(mufu_peak, 4), "unit": "Tops/s",
+                                  "frac": round(mufu_pose * w.pop / per_gen_s / 1e12 / mufu_peak,
+                                                4)},
                          "generation_ms": round(1000 * per_gen_s, 4)},
             "grid_build_ms": round(grid_ms, 1), "ligand_generation_s (untimed)": round(gen_s, 1),
             "gpu_launches": n_chunks * (n_launch + 4),
@@ -732,8 +747,7 @@ def run_pairwise(args, rank, world):
     peaks, peak_kind = measured_peaks()
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
-    mufu_peak = n_sm * 16 * sm_mhz * 1e6 / 1e12
+    fp32_peak, mufu_peak, peak_src = alu_peaks(dock, stream, n_sm, sm_mhz)
     ach = flops / (ms_step / 1000.0) / 1e12
     achm = mufu / (ms_step / 1000.0) / 1e12
     # end to end from host genotypes: upload, score, download
@@ -757,8 +771,7 @@ def run_pairwise(args, rank, world):
                        "protein_pairs_within_cutoff_per_pose": round(inter_per_pose, 1)},
             "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2),
                          "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4), "traffic": None,
-                         "kernel": "score_pairwise_kernel",
-                         "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
+                         "kernel": "score_pairwise_kernel", **peak_src,
                          "mufu": {"achieved": round(achm, 4), "peak": round(mufu_peak, 4),
                                   "unit": "Tops/s", "frac": round(achm / mufu_peak, 4)}},
             "e2e": {"value": round(n / e2e_s, 1), "unit": "poses/s",
@@ -984,8 +997,7 @@ def main():
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12           # TFLOP/s
-    mufu_peak = n_sm * 16 * sm_mhz * 1e6 / 1e12                 # Tops/s
+    fp32_peak, mufu_peak, peak_src = alu_peaks(dock, stream, n_sm, sm_mhz)  # TFLOP/s, Tops/s
     flops_pose, mufu_pose = work_per_pose(info, ligs.n_ligands)
     per_gen_s = ms_kernels / 1000.0 / max(n_launch, 1)
     # poses scored per generation per ligand: pop (GA), plus in the Lamarckian
@@ -1002,7 +1014,7 @@ def main():
             "traffic": None if (lga or nogrid or WORKLOAD != "c2") else read_traffic(),
             "kernel": ("search_kernel + ls_kernel" if lga else
                        "search_kernel<L, pairwise>" if nogrid else "search_kernel"),
-            "peak_source": "FP32 lanes x 2 x max SM clock (%s sm_max_mhz)" % peak_kind,
+            **peak_src,
             "mufu": {"achieved": round(ach_mufu, 4), "peak": round(mufu_peak, 4), "unit": "Tops/s",
                      "frac": round(ach_mufu / mufu_peak, 4)},
             "issue": None if (lga or nogrid or WORKLOAD != "c2") else read_issue(per_gen_s, n_sm,

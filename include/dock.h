@@ -476,6 +476,16 @@ int dock_autotune(dock_pocket *pocket, dock_ligands *ligands, const dock_search_
  * (0 when the job was not profiled). */
 int dock_job_kernel_time(const dock_job *job, double *ms_total, int32_t *launches);
 
+/* Measurement aid (the paper has no counterpart): the device's FP32
+ * fused-multiply-add rate (*fp32_tflops, TFLOP/s, FMA = 2 flops) and its
+ * special-function rate (*mufu_tops, ex2 per second in units of 1e12), each
+ * measured by a kernel of independent dependency chains on every SM, timed
+ * with events on stream (best of three after a warm-up run); the rooflines
+ * of the scoring kernels divide by these instead of unit counts times the
+ * clock. Allocates and frees 4 bytes; waits for stream. Errors: DOCK_EINVAL
+ * (NULL output), DOCK_ENOMEM, DOCK_ECUDA. */
+int dock_measure_peaks(double *fp32_tflops, double *mufu_tops, void *stream);
+
 const char *dock_last_error(void);
 
 /* Library build string (architecture, version). */

@@ -162,6 +162,7 @@ def lib():
         L.dock_surrogate_gradients.argtypes = [vp, vp, vp, C.c_int32, vp, C.POINTER(C.c_float), vp]
         L.dock_surrogate_train.argtypes = [vp, vp, vp, C.c_int64, C.POINTER(dock_train_params), vp,
                                            vp]
+        L.dock_measure_peaks.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         for name in ("dock_create_pocket", "dock_pocket_grid", "dock_load_ligands", "dock_batch",
                      "dock_results", "dock_job_population", "dock_job_kernel_time", "dock_score",
                      "dock_score_pairwise",
@@ -169,7 +170,7 @@ def lib():
                      "dock_features_population", "dock_surrogate_create",
                      "dock_surrogate_set_params", "dock_surrogate_get_params",
                      "dock_surrogate_predict", "dock_surrogate_gradients",
-                     "dock_surrogate_train", "dock_autotune"):
+                     "dock_surrogate_train", "dock_autotune", "dock_measure_peaks"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -494,6 +495,13 @@ def dock_surrogate_train(s: Surrogate, features, scores, epochs=2, batch=4096, l
     check(lib().dock_surrogate_train(s.handle, _dptr(features), _dptr(scores), n, C.byref(tp),
                                      losses.ctypes.data_as(C.c_void_p), _stream(stream)))
     return losses
+
+
+def dock_measure_peaks(stream=None):
+    """(FP32 FMA TFLOP/s, MUFU ex2 Tops/s) measured on the current device."""
+    f, m = C.c_double(), C.c_double()
+    check(lib().dock_measure_peaks(C.byref(f), C.byref(m), _stream(stream)))
+    return f.value, m.value
 
 
 def dock_autotune(pocket: Pocket, ligands: Ligands, pop: int, generations: int, seed=0,
