@@ -14,7 +14,7 @@ namespace mlp {
 
 namespace {
 
-__device__ __forceinline__ float gelu_d(float z) { return gelu_grad(z); }
+__device__ __forceinline__ float gelu_d(float z) { return gelu_t_grad(z); }
 
 // y[m] = b + sum_j H[m][j] w[j] (the 256 -> 1 output layer; one warp per row).
 __global__ void out_layer_kernel(const __nv_bfloat16 *H, const float *w, const float *b, int rows,

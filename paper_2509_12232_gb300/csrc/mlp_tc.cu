@@ -1,5 +1,5 @@
 // Fused forward pass of the surrogate MLP (128 -> 256 -> 256 -> 256 -> 1,
-// erf-GELU after the hidden layers) on the 5th-generation tensor cores.
+// GELU after the hidden layers) on the 5th-generation tensor cores.
 //
 // One persistent CTA per SM (8 warps) takes tiles of 128 feature rows:
 //   - the tile is stored in shared memory in the K-major "core matrix" layout
@@ -167,27 +167,16 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
                : "memory");
 }
 
-// gelu_as (mlp.h) on two activations with packed two-wide FP32 arithmetic (the same
-// operations in the same order, one instruction for both lanes of a pair).
+// gelu_t (mlp.h) on two activations: packed two-wide FP32 arithmetic (the same
+// operations in the same order, one instruction for both) around two tanh
+// on the special-function unit.
 __device__ __forceinline__ float2 gelu2(float2 z) {
-  const float2 az = make_float2(fabsf(z.x), fabsf(z.y));
-  const float2 x = __fmul2_rn(az, make_float2(0.70710678118654752f, 0.70710678118654752f));
-  float2 p = __ffma2_rn(make_float2(4.30638e-5f, 4.30638e-5f), x,
-                        make_float2(2.765672e-4f, 2.765672e-4f));
-  p = __ffma2_rn(p, x, make_float2(1.520143e-4f, 1.520143e-4f));
-  p = __ffma2_rn(p, x, make_float2(9.2705272e-3f, 9.2705272e-3f));
-  p = __ffma2_rn(p, x, make_float2(4.22820123e-2f, 4.22820123e-2f));
-  p = __ffma2_rn(p, x, make_float2(7.05230784e-2f, 7.05230784e-2f));
-  p = __ffma2_rn(p, x, make_float2(1.0f, 1.0f));
-  float2 r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(p.x));
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(p.y));
-  r = __fmul2_rn(r, r);
-  r = __fmul2_rn(r, r);
-  r = __fmul2_rn(r, r);
-  r = __fmul2_rn(r, r);  // p^-16
-  const float2 t = __ffma2_rn(r, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
-  return __fmul2_rn(make_float2(0.5f, 0.5f), __ffma2_rn(az, t, z));
+  const float2 z2 = __fmul2_rn(z, z);
+  const float2 t = __ffma2_rn(make_float2(kGeluC1, kGeluC1), z2, make_float2(kGeluC0, kGeluC0));
+  const float2 u = __fmul2_rn(z, t);
+  const float2 th = make_float2(tanh_sfu(u.x), tanh_sfu(u.y));
+  const float2 h = __fmul2_rn(make_float2(0.5f, 0.5f), z);
+  return __ffma2_rn(h, th, h);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -506,8 +495,9 @@ __global__ void __launch_bounds__(G_THREADS, 3)
           const float z0 = __uint_as_float(r[4 * j]) + b.x, z1 = __uint_as_float(r[4 * j + 1]) + b.y;
           const float z2 = __uint_as_float(r[4 * j + 2]) + b.z, z3 = __uint_as_float(r[4 * j + 3]) + b.w;
           if (ep.c32) reinterpret_cast<float4 *>(ep.c32 + o)[j] = make_float4(z0, z1, z2, z3);
-          h[2 * j] = pack_bf16(gelu_as(z0), gelu_as(z1));
-          h[2 * j + 1] = pack_bf16(gelu_as(z2), gelu_as(z3));
+          const float2 g01 = gelu2(make_float2(z0, z1)), g23 = gelu2(make_float2(z2, z3));
+          h[2 * j] = pack_bf16(g01.x, g01.y);
+          h[2 * j + 1] = pack_bf16(g23.x, g23.y);
         }
         uint4 *dst = reinterpret_cast<uint4 *>(ep.c16 + o);
 #pragma unroll
@@ -518,10 +508,10 @@ __global__ void __launch_bounds__(G_THREADS, 3)
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const float4 z = zin[j];
-          h[2 * j] = pack_bf16(__uint_as_float(r[4 * j]) * gelu_grad(z.x),
-                               __uint_as_float(r[4 * j + 1]) * gelu_grad(z.y));
-          h[2 * j + 1] = pack_bf16(__uint_as_float(r[4 * j + 2]) * gelu_grad(z.z),
-                                   __uint_as_float(r[4 * j + 3]) * gelu_grad(z.w));
+          h[2 * j] = pack_bf16(__uint_as_float(r[4 * j]) * gelu_t_grad(z.x),
+                               __uint_as_float(r[4 * j + 1]) * gelu_t_grad(z.y));
+          h[2 * j + 1] = pack_bf16(__uint_as_float(r[4 * j + 2]) * gelu_t_grad(z.z),
+                                   __uint_as_float(r[4 * j + 3]) * gelu_t_grad(z.w));
         }
         uint4 *dst = reinterpret_cast<uint4 *>(ep.c16 + o);
 #pragma unroll
