@@ -79,8 +79,10 @@ __global__ void reduce_parts_kernel(const float *part, int blocks, int width, fl
 // (1-b2) g^2; p -= lr * mhat / (sqrt(vhat) + eps), mhat = m / (1 - b1^t),
 // vhat = v / (1 - b2^t); t from step_dev when given (a graph-replayed step),
 // else step.
+// With copies (training): the updated W1..W3 are also written as their BF16
+// copies w16 [in][out] and wt16 [out][in] (what cast_weights_kernel makes).
 __global__ void adam_kernel(float *p, float *m, float *v, const float *g, int n, float lr, float b1,
-                            float b2, float eps, int step, const int *step_dev) {
+                            float b2, float eps, int step, const int *step_dev, WeightCopies wc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float t = (float)(step_dev ? *step_dev : step);
@@ -90,7 +92,21 @@ __global__ void adam_kernel(float *p, float *m, float *v, const float *g, int n,
   const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
   m[i] = mi;
   v[i] = vi;
-  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  p[i] = pi;
+  if (wc.w16[0] == nullptr) return;
+  int l = -1, e = 0, in = 0;
+  if (i >= OFF_W1 && i < OFF_W1 + FEATURES * HIDDEN) {
+    l = 0; e = i - OFF_W1; in = FEATURES;
+  } else if (i >= OFF_W2 && i < OFF_W2 + HIDDEN * HIDDEN) {
+    l = 1; e = i - OFF_W2; in = HIDDEN;
+  } else if (i >= OFF_W3 && i < OFF_W3 + HIDDEN * HIDDEN) {
+    l = 2; e = i - OFF_W3; in = HIDDEN;
+  }
+  if (l < 0) return;
+  const __nv_bfloat16 b = __float2bfloat16_rn(pi);
+  wc.w16[l][e] = b;
+  wc.wt16[l][(int64_t)(e % HIDDEN) * in + e / HIDDEN] = b;
 }
 
 // BF16 copies of a weight matrix W [in][out]: w16 (same layout) and wt16 [out][in].
@@ -131,9 +147,9 @@ cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, float
 }
 
 cudaError_t adam(float *p, float *m, float *v, const float *g, int n, float lr, int step,
-                 const int *step_dev, cudaStream_t s) {
+                 const int *step_dev, const WeightCopies *copies, cudaStream_t s) {
   adam_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, m, v, g, n, lr, 0.9f, 0.999f, 1e-8f, step,
-                                              step_dev);
+                                              step_dev, copies ? *copies : WeightCopies{});
   return cudaGetLastError();
 }
 

@@ -71,9 +71,15 @@ cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const
 // (scratch: at least 64 * cols floats).
 cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, float *scratch,
                    cudaStream_t s);
-// Adam step t = *step_dev if step_dev is given (read on the device), else step.
+// BF16 copies of W1..W3 that the training products read: w16[l] [in][out], wt16[l] [out][in].
+struct WeightCopies {
+  __nv_bfloat16 *w16[3] = {nullptr, nullptr, nullptr};
+  __nv_bfloat16 *wt16[3] = {nullptr, nullptr, nullptr};
+};
+// Adam step t = *step_dev if step_dev is given (read on the device), else step;
+// with copies, the updated W1..W3 are also written to them (one kernel).
 cudaError_t adam(float *p, float *m, float *v, const float *g, int n, float lr, int step,
-                 const int *step_dev, cudaStream_t s);
+                 const int *step_dev, const WeightCopies *copies, cudaStream_t s);
 cudaError_t cast_weights(const float *W, int in, int out, __nv_bfloat16 *w16, __nv_bfloat16 *wt16,
                          cudaStream_t s);
 

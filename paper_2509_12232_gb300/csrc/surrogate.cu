@@ -489,9 +489,15 @@ extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features,
     int rc;
     if ((rc = forward(S, rows, true, s)) != DOCK_OK) return rc;
     if ((rc = backward(S, rows, valid, s)) != DOCK_OK) return rc;
+    // Adam writes the BF16 copies the next step's products read
+    mlp::WeightCopies wcp;
+    for (int l = 0; l < 3; ++l) {
+      wcp.w16[l] = S->w16[l];
+      wcp.wt16[l] = S->wt16[l];
+    }
     SCU(mlp::adam(S->p, S->m, S->v, S->g, N_PARAMS, tp->lr, S->step + 1, dev ? S->d_step : nullptr,
-                  s));
-    if ((rc = refresh_bf16(S, s)) != DOCK_OK) return rc;
+                  &wcp, s));
+    S->wc_valid = false;  // the prediction's tensor-core layout is rebuilt when next needed
     if (dev) {
       advance_counters_kernel<<<1, 1, 0, s>>>(S->d_r0, B, S->d_step);
       SCU(cudaGetLastError());
