@@ -1,28 +1,36 @@
 // Fused forward pass of the surrogate MLP (128 -> 256 -> 256 -> 256 -> 1,
 // GELU after the hidden layers) on the 5th-generation tensor cores.
 //
-// One persistent CTA per SM (8 warps) takes tiles of 128 feature rows:
-//   - the tile is stored in shared memory in the K-major "core matrix" layout
-//     the tensor core reads without swizzling (8 rows x 16 bytes per 128-byte
-//     block, blocks ordered by row group then by K);
-//   - each layer's BF16 weights, kept in global memory in that same layout,
-//     arrive by bulk asynchronous copies that complete on an mbarrier (the
-//     next layer's copy runs during the current layer's epilogue);
-//   - one thread issues tcgen05.mma (M = 128, N = 256, K = 16 per instruction)
-//     into a 256-column FP32 accumulator in tensor memory and commits it to an
+// One persistent CTA per SM takes tiles of 128 feature rows, two at a time in
+// two slots, so that one slot's products run while the other slot's
+// epilogue runs (the epilogue is as long as the products):
+//   - a slot's A operand (features, then each hidden layer) is a 64 KB tile
+//     in shared memory in the K-major "core matrix" layout the tensor core
+//     reads without swizzling (8 rows x 16 bytes per 128-byte block, blocks
+//     ordered by row group then by K); its accumulator is one half (256
+//     columns) of the CTA's tensor memory;
+//   - the BF16 weights are kept in global memory as chunks of 32 K columns
+//     (16 KB, the same layout with K = 32); a copy warp streams them, in the
+//     order the products use them, through a ring of five shared-memory
+//     stages (bulk asynchronous copies completing on the stage's "full"
+//     mbarrier; the products that read a stage commit to its "empty" one);
+//   - an MMA warp issues, per slot and layer, tcgen05.mma (M = 128, N = 256,
+//     K = 16 per instruction) into the slot's accumulator once the slot's A
+//     operand is ready, and commits the layer to the slot's accumulator
 //     mbarrier;
-//   - the 16 warps drain the accumulator, warp w reading lanes 32 (w mod 4) ..
-//     + 31 (the lane quarter its position in the warp group may access) and
-//     columns 64 (w / 4) .. + 63 with tcgen05.ld; they add the bias, apply
-//     GELU, round to BF16 and store the activations in the same layout as the
-//     next layer's A operand; after the third layer each thread forms a
-//     quarter of its row's output (a dot product with the FP32 w4) and the
-//     quarters are added. Four warps per scheduler keep the epilogue, the
-//     kernel's longest phase, issuing while some wait on their loads.
-// Every mbarrier wait is bounded (one second of globaltimer); a timeout sets
-// *err, skips the rest of the CTA's tiles (the caller fills the output with
-// NaN beforehand) and releases the tensor memory after waiting, again
-// bounded, for the copies and products in flight.
+//   - 16 epilogue warps drain a finished accumulator, warp w reading lanes
+//     32 (w mod 4) .. + 31 (the lane quarter its position in the warp group
+//     may access) and columns 64 (w / 4) .. + 63 with tcgen05.ld: bias, GELU,
+//     rounding to BF16 and stores into the slot's A operand for the next
+//     layer; after the third layer each thread forms a quarter of its row's
+//     output (a dot product with the FP32 w4), parts 1-3 hand theirs to part 0
+//     through shared memory, and the slot receives its next tile's features
+//     (read from global memory during that epilogue). Each step signals the
+//     MMA warp through the slot's "A ready" mbarrier.
+// Every mbarrier wait is bounded (one second of globaltimer) and also ends
+// when another role has given up; a timeout sets *err, the roles leave their
+// loops (the caller fills the output with NaN beforehand), and the tensor
+// memory is released after the copies and products in flight are waited for.
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -33,17 +41,37 @@ namespace mlp {
 
 namespace {
 
-constexpr int TM = 128;        // rows per tile (MMA M)
-constexpr int kThreads = 512;  // warp w: accumulator lanes 32 (w mod 4) .., columns 64 (w / 4) ..
-constexpr int kParts = kThreads / 128;  // column quarters of a row
-constexpr int XH_BYTES = TM * HIDDEN * 2;       // feature tile (32 KB) or hidden tile (64 KB)
-constexpr int W_BYTES = HIDDEN * HIDDEN * 2;    // one layer's weights (at most 128 KB)
-constexpr int SMEM_BYTES = XH_BYTES + W_BYTES + 64 + (kParts - 1) * TM * 4 + 4 * HIDDEN * 4;
-// + output partial sums of quarters 1-3, biases b1..b3 and w4
-constexpr int WC_L2 = HIDDEN * FEATURES;        // element offsets of layers 2, 3 in the weights
+constexpr int TM = 128;                       // rows per tile (MMA M)
+constexpr int kEpiWarps = 16;                 // warp w: lanes 32 (w mod 4).., columns 64 (w / 4)..
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kMmaWarp = kEpiWarps, kCopyWarp = kEpiWarps + 1;
+constexpr int kThreads = kEpiThreads + 64;    // + the MMA warp and the weight-copy warp
+constexpr int kParts = kEpiWarps / 4;         // column quarters of a row
+constexpr int ACT_BYTES = TM * HIDDEN * 2;    // one slot's A operand (64 KB)
+constexpr int KC = 32;                        // K columns of one weight chunk
+constexpr int WCH_ELEMS = HIDDEN * KC;        // BF16 values of a chunk (16 KB)
+constexpr int WCH_BYTES = 2 * WCH_ELEMS;
+constexpr int kStages = 5;                    // weight chunks in shared memory
+// mbarriers: weight stages full / empty, slot accumulators complete, slot A
+// operands ready, output partials full / empty, products drained at the end
+constexpr int B_WFULL = 0, B_WEMPTY = kStages, B_ACC = 2 * kStages, B_ACT = B_ACC + 2,
+              B_YFULL = B_ACT + 2, B_YEMPTY = B_YFULL + 2, B_FIN = B_YEMPTY + 2,
+              N_BARS = B_FIN + 1;
+constexpr int OFF_WST = 2 * ACT_BYTES;
+constexpr int OFF_BAR = OFF_WST + kStages * WCH_BYTES;
+constexpr int OFF_YP = OFF_BAR + 256;         // barriers, TMEM address, abort flag
+constexpr int OFF_PAR = OFF_YP + 2 * (kParts - 1) * TM * 4;  // output partials of parts 1-3
+constexpr int SMEM_BYTES = OFF_PAR + 4 * HIDDEN * 4;         // + biases b1..b3 and w4
+static_assert(8 * N_BARS + 8 <= 256, "barrier block");
+static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
+constexpr int WC_L2 = HIDDEN * FEATURES;      // weight values of layer 1 (and of 1 + 2: WC_L3)
 constexpr int WC_L3 = WC_L2 + HIDDEN * HIDDEN;
-constexpr int kCopyChunk = 16384;               // bytes per bulk copy
-constexpr uint64_t kWaitNs = 1000000000ull;     // bound of every mbarrier wait
+constexpr uint64_t kWaitNs = 1000000000ull;   // bound of every mbarrier wait
+
+// First chunk of layer `layer` (0-2) in the chunked weight array.
+__host__ __device__ constexpr int wchunk0(int layer) {
+  return layer == 0 ? 0 : (layer == 1 ? FEATURES / KC : (FEATURES + HIDDEN) / KC);
+}
 
 // Byte offset of element (r, k) of an R x K BF16 operand in the K-major
 // core-matrix layout: 128-byte blocks of 8 rows x 8 elements, block (r / 8,
@@ -86,6 +114,27 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t ph) {
     if (done) return true;
     if (gtimer() - t0 > kWaitNs) return false;
   }
+}
+
+// mbar_wait that also gives up once *abort is set (another role of the CTA
+// has given up).
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t ph, const volatile int *abort) {
+  const uint64_t t0 = gtimer();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(ph)
+        : "memory");
+    if (done) return true;
+    if (*abort || gtimer() - t0 > kWaitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
@@ -184,26 +233,37 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+// 96 registers: each of the SM's four schedulers has a quarter of the
+// register file, and 18 warps put five warps on two of them.
+__global__ void __maxnreg__(96)
     fused_forward_kernel(const __nv_bfloat16 *X, int64_t n, const __nv_bfloat16 *wc,
                          const float *params, float *y, int *err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  unsigned char *xh = sm;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + XH_BYTES + W_BYTES);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
-  float *ypart = reinterpret_cast<float *>(sm + XH_BYTES + W_BYTES + 64);
-  float *s_par = ypart + (kParts - 1) * TM;  // b1, b2, b3, w4 (256 each)
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + OFF_BAR);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_BAR + 8 * N_BARS);
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + OFF_BAR + 8 * N_BARS + 4);
+  float *ypart = reinterpret_cast<float *>(sm + OFF_YP);   // [slot][part - 1][row]
+  float *s_par = reinterpret_cast<float *>(sm + OFF_PAR);  // b1, b2, b3, w4 (256 each)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, part = warp >> 2;  // accumulator lanes 32 quad.., columns 64 part..
-  const uint32_t bar_w = smem_u32(&bars[0]), bar_m = smem_u32(&bars[1]);
-  const uint32_t s_xh = smem_u32(xh), s_w = smem_u32(sm + XH_BYTES);
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
+  const uint32_t s_act = smem_u32(sm), s_wst = smem_u32(sm + OFF_WST);
   if (tid == 0) {
-    mbar_init(bar_w, 1);
-    mbar_init(bar_m, 1);
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(bar(B_WFULL + i), 1);
+      mbar_init(bar(B_WEMPTY + i), 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(bar(B_ACC + s), 1);
+      mbar_init(bar(B_ACT + s), kEpiWarps);
+      mbar_init(bar(B_YFULL + s), kEpiWarps - kEpiWarps / kParts);  // warps of parts 1-3
+      mbar_init(bar(B_YEMPTY + s), kEpiWarps / kParts);             // warps of part 0
+    }
+    mbar_init(bar(B_FIN), 1);
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                      smem_u32(tslot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -215,142 +275,222 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tslot;
-  const uint32_t t_lane = tmem + ((uint32_t)(32 * quad) << 16);
-  const float b4 = params[OFF_B4];
-  const int64_t n_tiles = (n + TM - 1) / TM;
-  uint32_t ph_w = 0, ph_m = 0;
-  bool ok = true, w_pending = false, m_pending = false;
-
-  auto load_w = [&](int layer) {
-    const uint32_t bytes = (layer == 0 ? FEATURES : HIDDEN) * HIDDEN * 2;
-    const unsigned char *src = reinterpret_cast<const unsigned char *>(
-        wc + (layer == 0 ? 0 : (layer == 1 ? WC_L2 : WC_L3)));
-    if (tid == 0) {
-      mbar_expect_tx(bar_w, bytes);
-      for (uint32_t off = 0; off < bytes; off += kCopyChunk)
-        bulk_g2s(s_w + off, src + off, kCopyChunk, bar_w);
-    }
-    w_pending = true;
+  const int64_t n_tiles = (n + TM - 1) / TM, G = gridDim.x;
+  // this CTA's tiles blockIdx.x + i G, i < n_local; tile i goes to slot i mod 2
+  const int n_local = blockIdx.x < n_tiles ? (int)((n_tiles - 1 - blockIdx.x) / G + 1) : 0;
+  bool ok = true;
+  auto fail = [&]() {
+    ok = false;
+    *abort_flag = 1;
   };
 
-  // feature tile t: a warp moves 8 rows x 4 chunks of 16 bytes per step (full
-  // 32-byte sectors) into registers, stored later in the K-major core-matrix
-  // layout (K = 128); the next tile's rows are read during the last epilogue
-  constexpr int kXSteps = 64 / (kThreads / 32);
-  uint4 xr[kXSteps];
-  auto load_x = [&](int64_t t) {
-#pragma unroll
-    for (int i = 0; i < kXSteps; ++i) {
-      const int v = warp + (kThreads / 32) * i;
-      const int row = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
-      const int64_t gr = t * TM + row;
-      xr[i] = gr < n ? __ldg(reinterpret_cast<const uint4 *>(X + gr * FEATURES) + chunk)
-                     : make_uint4(0, 0, 0, 0);
-    }
-  };
-  if (blockIdx.x < n_tiles) {
-    load_w(0);
-    load_x(blockIdx.x);
-  }
-  for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
-#pragma unroll
-    for (int i = 0; i < kXSteps; ++i) {
-      const int v = warp + (kThreads / 32) * i;
-      const int row = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
-      *reinterpret_cast<uint4 *>(xh + canon_off(row, 8 * chunk, FEATURES)) = xr[i];
-    }
-    fence_proxy_async();
-    __syncthreads();
-    const int row = 32 * quad + lane;                  // this thread's row (accumulator lane)
-    float yrow = part ? 0.0f : b4;
-    for (int layer = 0; layer < 3 && ok; ++layer) {
-      const int K = layer == 0 ? FEATURES : HIDDEN;
-      // this layer's weights are in shared memory (the outcome of every wait
-      // is agreed by the whole CTA, so all threads leave together)
-      ok = __syncthreads_and(mbar_wait(bar_w, ph_w));
-      if (!ok) break;
-      w_pending = false;
-      ph_w ^= 1u;
-      if (tid == 0) {
-        fence_after_sync();
-        const uint32_t sbo = (uint32_t)K * 16;  // next 8-row group: K / 8 blocks of 128 bytes
-        for (int s = 0; s < K / 16; ++s)
-          mma_bf16(tmem, sdesc(s_xh + 256u * s, 128u, sbo), sdesc(s_w + 256u * s, 128u, sbo),
-                   idesc_bf16(TM, HIDDEN), s > 0);
-        mma_commit(bar_m);
-      }
-      m_pending = true;
-      ok = __syncthreads_and(mbar_wait(bar_m, ph_m));  // accumulator complete; A, B buffers free
-      if (!ok) break;
-      m_pending = false;
-      ph_m ^= 1u;
-      fence_after_sync();
-      // the next weights (and after the last layer the next tile's features)
-      // stream in during this epilogue
-      if (layer < 2) {
-        load_w(layer + 1);
-      } else if (t + gridDim.x < n_tiles) {
-        load_w(0);
-        load_x(t + gridDim.x);
-      }
-      // ---- epilogue: bias + GELU -> BF16 (next A operand) or the output --
-      const float *bias = s_par + HIDDEN * layer;
-      const float *w4 = s_par + 3 * HIDDEN;
-      // two chunks of 32 columns; the read of the second is in flight while
-      // the first is processed
-      uint32_t ra[32], rb[32];
-      auto chunk = [&](int cc, const uint32_t (&r)[32]) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 bl = *reinterpret_cast<const float4 *>(bias + 32 * cc + 8 * q);
-          const float4 bh = *reinterpret_cast<const float4 *>(bias + 32 * cc + 8 * q + 4);
-          const float bq[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
-          uint32_t w[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float2 a = gelu2(__fadd2_rn(make_float2(__uint_as_float(r[8 * q + 2 * e]),
-                                                          __uint_as_float(r[8 * q + 2 * e + 1])),
-                                              make_float2(bq[2 * e], bq[2 * e + 1])));
-            w[e] = pack_bf16(a.x, a.y);
-          }
-          if (layer < 2) {
-            *reinterpret_cast<uint4 *>(xh + canon_off(row, 32 * cc + 8 * q, HIDDEN)) =
-                make_uint4(w[0], w[1], w[2], w[3]);
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int c = 32 * cc + 8 * q + 2 * e;
-              const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[e]);
-              yrow = fmaf(__low2float(h), w4[c], yrow);
-              yrow = fmaf(__high2float(h), w4[c + 1], yrow);
+  if (warp == kCopyWarp) {
+    // ---- weight chunks in the order the products use them -----------------
+    if (lane == 0) {
+      int g = 0;  // chunks issued
+      for (int i0 = 0; i0 < n_local && ok; i0 += 2)
+        for (int layer = 0; layer < 3 && ok; ++layer)
+          for (int s = 0; s < 2 && ok && i0 + s < n_local; ++s) {
+            const int nch = (layer ? HIDDEN : FEATURES) / KC;
+            for (int c = 0; c < nch; ++c, ++g) {
+              const int st = g % kStages;
+              if (g >= kStages &&
+                  !mbar_wait_ab(bar(B_WEMPTY + st), (uint32_t)((g / kStages) - 1) & 1u, abort_flag)) {
+                fail();
+                break;
+              }
+              mbar_expect_tx(bar(B_WFULL + st), WCH_BYTES);
+              bulk_g2s(s_wst + st * WCH_BYTES, wc + (int64_t)(wchunk0(layer) + c) * WCH_ELEMS,
+                       WCH_BYTES, bar(B_WFULL + st));
             }
           }
-        }
-      };
-      const int c0 = 2 * part;
-      tmem_ld32(t_lane + 32u * c0, ra);
-      tmem_wait(ra);
-      tmem_ld32(t_lane + 32u * (c0 + 1), rb);
-      chunk(c0, ra);
-      tmem_wait(rb);
-      chunk(c0 + 1, rb);
-      if (layer < 2) fence_proxy_async();
-      else if (part) ypart[(part - 1) * TM + row] = yrow;
-      fence_before_sync();
-      __syncthreads();
+      // the last copy into each stage lands before the CTA ends
+      for (int k = 1; k <= kStages && k <= g; ++k)
+        mbar_wait(bar(B_WFULL + (g - k) % kStages), (uint32_t)((g - k) / kStages) & 1u);
     }
-    if (ok && !part && t * TM + row < n)
-      y[t * TM + row] = yrow + (ypart[row] + (ypart[TM + row] + ypart[2 * TM + row]));
+  } else if (warp == kMmaWarp) {
+    // ---- products: per slot and layer, once the slot's A operand is ready --
+    if (lane == 0) {
+      int g = 0;  // chunks consumed
+      uint32_t ph_act[2] = {0u, 0u};
+      bool issued = false;
+      for (int i0 = 0; i0 < n_local && ok; i0 += 2)
+        for (int layer = 0; layer < 3 && ok; ++layer)
+          for (int s = 0; s < 2 && ok && i0 + s < n_local; ++s) {
+            if (!mbar_wait_ab(bar(B_ACT + s), ph_act[s], abort_flag)) {
+              fail();
+              break;
+            }
+            ph_act[s] ^= 1u;
+            fence_after_sync();
+            const int K = layer ? HIDDEN : FEATURES;
+            const uint32_t a0 = s_act + s * ACT_BYTES, sbo_a = (uint32_t)K * 16;
+            const uint32_t d = tmem + 256u * s;
+            for (int c = 0; c < K / KC; ++c, ++g) {
+              const int st = g % kStages;
+              if (!mbar_wait_ab(bar(B_WFULL + st), (uint32_t)(g / kStages) & 1u, abort_flag)) {
+                fail();
+                break;
+              }
+              fence_after_sync();
+#pragma unroll
+              for (int j = 0; j < KC / 16; ++j)
+                mma_bf16(d, sdesc(a0 + 256u * (c * (KC / 16) + j), 128u, sbo_a),
+                         sdesc(s_wst + st * WCH_BYTES + 256u * j, 128u, (KC / 8) * 128u),
+                         idesc_bf16(TM, HIDDEN), (c | j) != 0);
+              mma_commit(bar(B_WEMPTY + st));
+              issued = true;
+            }
+            if (ok) mma_commit(bar(B_ACC + s));
+          }
+      // the products in flight finish before the tensor memory is released
+      if (issued) {
+        mma_commit(bar(B_FIN));
+        mbar_wait(bar(B_FIN), 0u);
+      }
+    }
+  } else {
+    // ---- epilogue warps -----------------------------------------------------
+    const int quad = warp & 3, part = warp >> 2;  // accumulator lanes 32 quad.., columns 64 part..
+    const int row = 32 * quad + lane;             // this thread's row (accumulator lane)
+    const uint32_t t_lane = tmem + ((uint32_t)(32 * quad) << 16);
+    const float b4 = params[OFF_B4];
+    uint32_t ph_acc[2] = {0u, 0u};
+    int y_use[2] = {0, 0};
+    // feature tile: a warp moves 8 rows x 4 chunks of 16 bytes per step (full
+    // 32-byte sectors) into registers, stored later in the K-major
+    // core-matrix layout (K = 128)
+    constexpr int kXSteps = 64 / kEpiWarps;
+    uint4 xr[kXSteps];
+    auto load_x = [&](int64_t t) {
+#pragma unroll
+      for (int i = 0; i < kXSteps; ++i) {
+        const int v = warp + kEpiWarps * i;
+        const int r = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
+        const int64_t gr = t * TM + r;
+        xr[i] = gr < n ? __ldg(reinterpret_cast<const uint4 *>(X + gr * FEATURES) + chunk)
+                       : make_uint4(0, 0, 0, 0);
+      }
+    };
+    auto store_x = [&](int s) {
+      unsigned char *a = sm + s * ACT_BYTES;
+#pragma unroll
+      for (int i = 0; i < kXSteps; ++i) {
+        const int v = warp + kEpiWarps * i;
+        const int r = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
+        *reinterpret_cast<uint4 *>(a + canon_off(r, 8 * chunk, FEATURES)) = xr[i];
+      }
+    };
+    // A operand ready (features or a hidden layer written, accumulator read)
+    auto signal_act = [&](int s) {
+      fence_proxy_async();
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar(B_ACT + s));
+    };
+    for (int s = 0; s < 2 && s < n_local; ++s) {
+      load_x(blockIdx.x + s * G);
+      store_x(s);
+      signal_act(s);
+    }
+    for (int i0 = 0; i0 < n_local && ok; i0 += 2)
+      for (int layer = 0; layer < 3 && ok; ++layer)
+        for (int s = 0; s < 2 && ok && i0 + s < n_local; ++s) {
+          const int i = i0 + s;
+          const int64_t t = blockIdx.x + (int64_t)i * G;
+          if (!__all_sync(0xffffffffu, mbar_wait_ab(bar(B_ACC + s), ph_acc[s], abort_flag))) {
+            fail();
+            break;
+          }
+          ph_acc[s] ^= 1u;
+          fence_after_sync();
+          const bool next = layer == 2 && i + 2 < n_local;
+          if (next) load_x(t + 2 * G);  // in flight during this epilogue
+          // ---- bias + GELU -> BF16 (next A operand) or the output ------------
+          unsigned char *act = sm + s * ACT_BYTES;
+          const float *bias = s_par + HIDDEN * layer;
+          const float *w4 = s_par + 3 * HIDDEN;
+          float yrow = part ? 0.0f : b4;
+          // two chunks of 32 columns; the read of the second is in flight
+          // while the first is processed
+          uint32_t ra[32], rb[32];
+          auto chunk = [&](int cc, const uint32_t (&r)[32]) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float4 bl = *reinterpret_cast<const float4 *>(bias + 32 * cc + 8 * q);
+              const float4 bh = *reinterpret_cast<const float4 *>(bias + 32 * cc + 8 * q + 4);
+              const float bq[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
+              uint32_t w[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float2 a = gelu2(__fadd2_rn(make_float2(__uint_as_float(r[8 * q + 2 * e]),
+                                                              __uint_as_float(r[8 * q + 2 * e + 1])),
+                                                  make_float2(bq[2 * e], bq[2 * e + 1])));
+                w[e] = pack_bf16(a.x, a.y);
+              }
+              if (layer < 2) {
+                *reinterpret_cast<uint4 *>(act + canon_off(row, 32 * cc + 8 * q, HIDDEN)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+              } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                  const int c = 32 * cc + 8 * q + 2 * e;
+                  const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[e]);
+                  yrow = fmaf(__low2float(h), w4[c], yrow);
+                  yrow = fmaf(__high2float(h), w4[c + 1], yrow);
+                }
+              }
+            }
+          };
+          const int c0 = 2 * part;
+          const uint32_t ta = t_lane + 256u * s;
+          tmem_ld32(ta + 32u * c0, ra);
+          tmem_wait(ra);
+          tmem_ld32(ta + 32u * (c0 + 1), rb);
+          chunk(c0, ra);
+          tmem_wait(rb);
+          chunk(c0 + 1, rb);
+          if (layer < 2) {
+            signal_act(s);
+            continue;
+          }
+          // ---- output: parts 1-3 hand their partial dot products to part 0 ---
+          float *yp = ypart + s * (kParts - 1) * TM;
+          const int u = y_use[s]++;
+          if (part) {
+            if (u > 0 &&
+                !__all_sync(0xffffffffu, mbar_wait_ab(bar(B_YEMPTY + s), (uint32_t)(u - 1) & 1u,
+                                                      abort_flag))) {
+              fail();
+              break;
+            }
+            yp[(part - 1) * TM + row] = yrow;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(B_YFULL + s));
+          } else {
+            if (!__all_sync(0xffffffffu,
+                            mbar_wait_ab(bar(B_YFULL + s), (uint32_t)u & 1u, abort_flag))) {
+              fail();
+              break;
+            }
+            if (t * TM + row < n)
+              y[t * TM + row] = yrow + (yp[row] + (yp[TM + row] + yp[2 * TM + row]));
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar(B_YEMPTY + s));
+          }
+          if (next) {
+            store_x(s);
+            signal_act(s);
+          }
+        }
   }
-  // ---- teardown: let copies and products in flight finish, free TMEM ------
-  if (w_pending) mbar_wait(bar_w, ph_w);
-  if (m_pending) mbar_wait(bar_m, ph_m);
+  // ---- teardown: copies and products in flight have finished; free TMEM ---
   if (!ok && lane == 0) atomicExch(err, 1);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -556,7 +696,9 @@ __global__ void sum_parts_kernel(const float *part, int parts, int64_t width, fl
 }
 
 // Layers 1-3 of the packed FP32 parameters (W stored [in][out]) as BF16
-// B operands (N = 256 outputs x K inputs) in the K-major core-matrix layout.
+// B operands (N = 256 outputs x K inputs) in chunks of KC input columns, each
+// chunk in the K-major core-matrix layout with K = KC; layer l's chunks
+// start at chunk wchunk0(l).
 __global__ void canon_weights_kernel(const float *p, __nv_bfloat16 *wc) {
   const int total = WC_L3 + HIDDEN * HIDDEN;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -574,8 +716,8 @@ __global__ void canon_weights_kernel(const float *p, __nv_bfloat16 *wc) {
     const int K = layer == 0 ? FEATURES : HIDDEN;
     const int nn = e / K, k = e % K;  // output nn, input k
     const int off_w = layer == 0 ? OFF_W1 : (layer == 1 ? OFF_W2 : OFF_W3);
-    const int base = layer == 0 ? 0 : (layer == 1 ? WC_L2 : WC_L3);
-    wc[base + canon_off(nn, k, K) / 2] = __float2bfloat16_rn(p[off_w + k * HIDDEN + nn]);
+    wc[(wchunk0(layer) + k / KC) * WCH_ELEMS + canon_off(nn, k % KC, KC) / 2] =
+        __float2bfloat16_rn(p[off_w + k * HIDDEN + nn]);
   }
 }
 
