@@ -31,6 +31,7 @@
 // when another role has given up; a timeout sets *err, the roles leave their
 // loops (the caller fills the output with NaN beforehand), and the tensor
 // memory is released after the copies and products in flight are waited for.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -42,25 +43,35 @@ namespace mlp {
 namespace {
 
 constexpr int TM = 128;                       // rows per tile (MMA M)
-constexpr int kEpiWarps = 16;                 // warp w: lanes 32 (w mod 4).., columns 64 (w / 4)..
+#ifndef DOCK_MLP_EPI_WARPS
+#define DOCK_MLP_EPI_WARPS 16
+#endif
+constexpr int kEpiWarps = DOCK_MLP_EPI_WARPS; // a multiple of 4
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kMmaWarp = kEpiWarps, kCopyWarp = kEpiWarps + 1;
 constexpr int kThreads = kEpiThreads + 64;    // + the MMA warp and the weight-copy warp
-constexpr int kParts = kEpiWarps / 4;         // column quarters of a row
+constexpr int kParts = kEpiWarps / 4;         // column parts of a row: warp w takes lanes
+                                              // 32 (w mod 4).. and part w / 4 of the columns
+constexpr int kPartChunks = HIDDEN / 32 / kParts;  // 32-column accumulator reads per part
+// Registers per thread: each of the SM's four schedulers holds a quarter of
+// the register file, and the warps are spread over them round robin.
+constexpr int kMaxRegs = (16384 / (32 * ((kEpiWarps + 2 + 3) / 4))) / 8 * 8;
 constexpr int ACT_BYTES = TM * HIDDEN * 2;    // one slot's A operand (64 KB)
 constexpr int KC = 32;                        // K columns of one weight chunk
 constexpr int WCH_ELEMS = HIDDEN * KC;        // BF16 values of a chunk (16 KB)
 constexpr int WCH_BYTES = 2 * WCH_ELEMS;
 constexpr int kStages = 5;                    // weight chunks in shared memory
 // mbarriers: weight stages full / empty, slot accumulators complete, slot A
-// operands ready, output partials full / empty, products drained at the end
+// operands ready, slot features landed, slot A operand free (its last
+// product done), output partials full / empty, products drained at the end
 constexpr int B_WFULL = 0, B_WEMPTY = kStages, B_ACC = 2 * kStages, B_ACT = B_ACC + 2,
-              B_YFULL = B_ACT + 2, B_YEMPTY = B_YFULL + 2, B_FIN = B_YEMPTY + 2,
-              N_BARS = B_FIN + 1;
+              B_XF = B_ACT + 2, B_AFREE = B_XF + 2, B_YFULL = B_AFREE + 2,
+              B_YEMPTY = B_YFULL + 2, B_FIN = B_YEMPTY + 2, N_BARS = B_FIN + 1;
+constexpr int X_BYTES = TM * FEATURES * 2;    // one feature tile (32 KB)
 constexpr int OFF_WST = 2 * ACT_BYTES;
 constexpr int OFF_BAR = OFF_WST + kStages * WCH_BYTES;
 constexpr int OFF_YP = OFF_BAR + 256;         // barriers, TMEM address, abort flag
-constexpr int OFF_PAR = OFF_YP + 2 * (kParts - 1) * TM * 4;  // output partials of parts 1-3
+constexpr int OFF_PAR = OFF_YP + 2 * (kParts - 1) * TM * 4;  // output partials of parts >= 1
 constexpr int SMEM_BYTES = OFF_PAR + 4 * HIDDEN * 4;         // + biases b1..b3 and w4
 static_assert(8 * N_BARS + 8 <= 256, "barrier block");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
@@ -119,8 +130,8 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t ph) {
 // mbar_wait that also gives up once *abort is set (another role of the CTA
 // has given up).
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t ph, const volatile int *abort) {
-  const uint64_t t0 = gtimer();
-  for (;;) {
+  uint64_t t0 = 0;
+  for (uint32_t k = 0;; ++k) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -129,7 +140,10 @@ __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t ph, const vo
         : "r"(bar), "r"(ph)
         : "memory");
     if (done) return true;
-    if (*abort || gtimer() - t0 > kWaitNs) return false;
+    if ((k & 15) == 0) {  // the clock and the flag every 16 polls
+      if (k == 0) t0 = gtimer();
+      else if (*abort || gtimer() - t0 > kWaitNs) return false;
+    }
   }
 }
 
@@ -143,6 +157,16 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
           "r"(dst),
       "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Tiled 2-D tensor copy of box (x, y) of the tensor map into shared memory.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, "
+      "%3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
 
@@ -233,11 +257,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<const uint32_t *>(&h);
 }
 
-// 96 registers: each of the SM's four schedulers has a quarter of the
-// register file, and 18 warps put five warps on two of them.
-__global__ void __maxnreg__(96)
-    fused_forward_kernel(const __nv_bfloat16 *X, int64_t n, const __nv_bfloat16 *wc,
-                         const float *params, float *y, int *err) {
+__global__ void __maxnreg__(kMaxRegs)
+    fused_forward_kernel(const __grid_constant__ CUtensorMap tmx, int64_t n,
+                         const __nv_bfloat16 *wc, const float *params, float *y, int *err) {
   extern __shared__ __align__(1024) unsigned char sm[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + OFF_BAR);
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_BAR + 8 * N_BARS);
@@ -255,8 +277,10 @@ __global__ void __maxnreg__(96)
     for (int s = 0; s < 2; ++s) {
       mbar_init(bar(B_ACC + s), 1);
       mbar_init(bar(B_ACT + s), kEpiWarps);
-      mbar_init(bar(B_YFULL + s), kEpiWarps - kEpiWarps / kParts);  // warps of parts 1-3
-      mbar_init(bar(B_YEMPTY + s), kEpiWarps / kParts);             // warps of part 0
+      mbar_init(bar(B_XF + s), 1);
+      mbar_init(bar(B_AFREE + s), 1);
+      mbar_init(bar(B_YFULL + s), kEpiWarps - 4);  // warps of parts >= 1
+      mbar_init(bar(B_YEMPTY + s), 4);             // warps of part 0
     }
     mbar_init(bar(B_FIN), 1);
     *abort_flag = 0;
@@ -285,12 +309,32 @@ __global__ void __maxnreg__(96)
   };
 
   if (warp == kCopyWarp) {
-    // ---- weight chunks in the order the products use them -----------------
+    // ---- features and weight chunks in the order the products use them ----
     if (lane == 0) {
-      int g = 0;  // chunks issued
+      int g = 0;                       // weight chunks issued
+      int x_issued[2] = {0, 0};        // feature tiles issued per slot
+      uint32_t ph_free[2] = {0u, 0u};
       for (int i0 = 0; i0 < n_local && ok; i0 += 2)
         for (int layer = 0; layer < 3 && ok; ++layer)
           for (int s = 0; s < 2 && ok && i0 + s < n_local; ++s) {
+            if (layer == 0) {
+              // the tile's features into the slot once its previous tile's
+              // last product is done: one 2 KB box (8 K values x 128 rows)
+              // per K block, which is the core-matrix layout with the K
+              // blocks 2 KB apart
+              if (i0 > 0) {
+                if (!mbar_wait_ab(bar(B_AFREE + s), ph_free[s], abort_flag)) {
+                  fail();
+                  break;
+                }
+                ph_free[s] ^= 1u;
+              }
+              const int row0 = (int)((blockIdx.x + (int64_t)(i0 + s) * G) * TM);
+              mbar_expect_tx(bar(B_XF + s), X_BYTES);
+              for (int c = 0; c < FEATURES / 8; ++c)
+                tma_load_2d(s_act + s * ACT_BYTES + c * (TM * 16), &tmx, 8 * c, row0, bar(B_XF + s));
+              ++x_issued[s];
+            }
             const int nch = (layer ? HIDDEN : FEATURES) / KC;
             for (int c = 0; c < nch; ++c, ++g) {
               const int st = g % kStages;
@@ -304,27 +348,44 @@ __global__ void __maxnreg__(96)
                        WCH_BYTES, bar(B_WFULL + st));
             }
           }
-      // the last copy into each stage lands before the CTA ends
+      // the last copies into each stage and slot land before the CTA ends
       for (int k = 1; k <= kStages && k <= g; ++k)
         mbar_wait(bar(B_WFULL + (g - k) % kStages), (uint32_t)((g - k) / kStages) & 1u);
+      for (int s = 0; s < 2; ++s)
+        if (x_issued[s] > 0) mbar_wait(bar(B_XF + s), (uint32_t)(x_issued[s] - 1) & 1u);
     }
   } else if (warp == kMmaWarp) {
     // ---- products: per slot and layer, once the slot's A operand is ready --
     if (lane == 0) {
       int g = 0;  // chunks consumed
-      uint32_t ph_act[2] = {0u, 0u};
+      uint32_t ph_act[2] = {0u, 0u}, ph_x[2] = {0u, 0u};
       bool issued = false;
       for (int i0 = 0; i0 < n_local && ok; i0 += 2)
         for (int layer = 0; layer < 3 && ok; ++layer)
           for (int s = 0; s < 2 && ok && i0 + s < n_local; ++s) {
-            if (!mbar_wait_ab(bar(B_ACT + s), ph_act[s], abort_flag)) {
-              fail();
-              break;
+            // layer 0: the features have landed (and, after the slot's first
+            // tile, the epilogue has read the accumulator); layers 1-2: the
+            // epilogue has written this layer's A operand
+            if (layer == 0) {
+              if (!mbar_wait_ab(bar(B_XF + s), ph_x[s], abort_flag)) {
+                fail();
+                break;
+              }
+              ph_x[s] ^= 1u;
             }
-            ph_act[s] ^= 1u;
+            if (layer > 0 || i0 > 0) {
+              if (!mbar_wait_ab(bar(B_ACT + s), ph_act[s], abort_flag)) {
+                fail();
+                break;
+              }
+              ph_act[s] ^= 1u;
+            }
             fence_after_sync();
             const int K = layer ? HIDDEN : FEATURES;
-            const uint32_t a0 = s_act + s * ACT_BYTES, sbo_a = (uint32_t)K * 16;
+            // A operand: features with K blocks 2 KB apart and row groups 128 B
+            // apart; hidden layers with K blocks 128 B and row groups K * 16 B
+            const uint32_t a0 = s_act + s * ACT_BYTES;
+            const uint32_t lbo_a = layer ? 128u : TM * 16u, sbo_a = layer ? (uint32_t)K * 16 : 128u;
             const uint32_t d = tmem + 256u * s;
             for (int c = 0; c < K / KC; ++c, ++g) {
               const int st = g % kStages;
@@ -335,13 +396,16 @@ __global__ void __maxnreg__(96)
               fence_after_sync();
 #pragma unroll
               for (int j = 0; j < KC / 16; ++j)
-                mma_bf16(d, sdesc(a0 + 256u * (c * (KC / 16) + j), 128u, sbo_a),
+                mma_bf16(d, sdesc(a0 + 2u * lbo_a * (c * (KC / 16) + j), lbo_a, sbo_a),
                          sdesc(s_wst + st * WCH_BYTES + 256u * j, 128u, (KC / 8) * 128u),
                          idesc_bf16(TM, HIDDEN), (c | j) != 0);
               mma_commit(bar(B_WEMPTY + st));
               issued = true;
             }
-            if (ok) mma_commit(bar(B_ACC + s));
+            if (ok) {
+              if (layer == 2) mma_commit(bar(B_AFREE + s));  // the slot may take new features
+              mma_commit(bar(B_ACC + s));
+            }
           }
       // the products in flight finish before the tensor memory is released
       if (issued) {
@@ -351,48 +415,19 @@ __global__ void __maxnreg__(96)
     }
   } else {
     // ---- epilogue warps -----------------------------------------------------
-    const int quad = warp & 3, part = warp >> 2;  // accumulator lanes 32 quad.., columns 64 part..
+    const int quad = warp & 3, part = warp >> 2;  // lanes 32 quad.., column part `part`
     const int row = 32 * quad + lane;             // this thread's row (accumulator lane)
     const uint32_t t_lane = tmem + ((uint32_t)(32 * quad) << 16);
     const float b4 = params[OFF_B4];
     uint32_t ph_acc[2] = {0u, 0u};
     int y_use[2] = {0, 0};
-    // feature tile: a warp moves 8 rows x 4 chunks of 16 bytes per step (full
-    // 32-byte sectors) into registers, stored later in the K-major
-    // core-matrix layout (K = 128)
-    constexpr int kXSteps = 64 / kEpiWarps;
-    uint4 xr[kXSteps];
-    auto load_x = [&](int64_t t) {
-#pragma unroll
-      for (int i = 0; i < kXSteps; ++i) {
-        const int v = warp + kEpiWarps * i;
-        const int r = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
-        const int64_t gr = t * TM + r;
-        xr[i] = gr < n ? __ldg(reinterpret_cast<const uint4 *>(X + gr * FEATURES) + chunk)
-                       : make_uint4(0, 0, 0, 0);
-      }
-    };
-    auto store_x = [&](int s) {
-      unsigned char *a = sm + s * ACT_BYTES;
-#pragma unroll
-      for (int i = 0; i < kXSteps; ++i) {
-        const int v = warp + kEpiWarps * i;
-        const int r = 8 * (v & 15) + (lane & 7), chunk = 4 * (v >> 4) + (lane >> 3);
-        *reinterpret_cast<uint4 *>(a + canon_off(r, 8 * chunk, FEATURES)) = xr[i];
-      }
-    };
-    // A operand ready (features or a hidden layer written, accumulator read)
+    // A operand ready (a hidden layer written, the accumulator read)
     auto signal_act = [&](int s) {
       fence_proxy_async();
       fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_ACT + s));
     };
-    for (int s = 0; s < 2 && s < n_local; ++s) {
-      load_x(blockIdx.x + s * G);
-      store_x(s);
-      signal_act(s);
-    }
     for (int i0 = 0; i0 < n_local && ok; i0 += 2)
       for (int layer = 0; layer < 3 && ok; ++layer)
         for (int s = 0; s < 2 && ok && i0 + s < n_local; ++s) {
@@ -405,7 +440,6 @@ __global__ void __maxnreg__(96)
           ph_acc[s] ^= 1u;
           fence_after_sync();
           const bool next = layer == 2 && i + 2 < n_local;
-          if (next) load_x(t + 2 * G);  // in flight during this epilogue
           // ---- bias + GELU -> BF16 (next A operand) or the output ------------
           unsigned char *act = sm + s * ACT_BYTES;
           const float *bias = s_par + HIDDEN * layer;
@@ -442,19 +476,26 @@ __global__ void __maxnreg__(96)
               }
             }
           };
-          const int c0 = 2 * part;
+          const int c0 = kPartChunks * part;
           const uint32_t ta = t_lane + 256u * s;
           tmem_ld32(ta + 32u * c0, ra);
           tmem_wait(ra);
-          tmem_ld32(ta + 32u * (c0 + 1), rb);
-          chunk(c0, ra);
-          tmem_wait(rb);
-          chunk(c0 + 1, rb);
+#pragma unroll
+          for (int k = 0; k < kPartChunks; k += 2) {
+            if (k + 1 < kPartChunks) tmem_ld32(ta + 32u * (c0 + k + 1), rb);
+            chunk(c0 + k, ra);
+            if (k + 1 < kPartChunks) {
+              tmem_wait(rb);
+              if (k + 2 < kPartChunks) tmem_ld32(ta + 32u * (c0 + k + 2), ra);
+              chunk(c0 + k + 1, rb);
+              if (k + 2 < kPartChunks) tmem_wait(ra);
+            }
+          }
           if (layer < 2) {
             signal_act(s);
             continue;
           }
-          // ---- output: parts 1-3 hand their partial dot products to part 0 ---
+          // ---- output: parts >= 1 hand their partial dot products to part 0 -
           float *yp = ypart + s * (kParts - 1) * TM;
           const int u = y_use[s]++;
           if (part) {
@@ -473,15 +514,14 @@ __global__ void __maxnreg__(96)
               fail();
               break;
             }
-            if (t * TM + row < n)
-              y[t * TM + row] = yrow + (yp[row] + (yp[TM + row] + yp[2 * TM + row]));
+            float rest = yp[(kParts - 2) * TM + row];
+#pragma unroll
+            for (int q = kParts - 3; q >= 0; --q) rest = yp[q * TM + row] + rest;
+            if (t * TM + row < n) y[t * TM + row] = yrow + rest;
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(B_YEMPTY + s));
           }
-          if (next) {
-            store_x(s);
-            signal_act(s);
-          }
+          if (next) signal_act(s);  // the accumulator may take the next tile
         }
   }
   // ---- teardown: copies and products in flight have finished; free TMEM ---
@@ -728,9 +768,43 @@ cudaError_t canon_weights(const float *p, __nv_bfloat16 *wc, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled from the driver, found once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
 cudaError_t fused_forward(const __nv_bfloat16 *X, int64_t n, const __nv_bfloat16 *wc,
                           const float *params, float *y, int *err, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
+  // 32-bit row coordinates in the tensor copies; 16-byte aligned rows
+  if (n > (int64_t)INT32_MAX - TM || (reinterpret_cast<uintptr_t>(X) & 15u) != 0)
+    return cudaErrorInvalidValue;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  // X [n][128] BF16 as a 2-D tensor; a box is 8 features x 128 rows (2 KB),
+  // rows past n read as zero
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)FEATURES, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)FEATURES * 2};
+  const cuuint32_t box[2] = {8u, (cuuint32_t)TM};
+  const cuuint32_t estr[2] = {1u, 1u};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(X), dims, strides,
+          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   int dev = 0, n_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
@@ -740,7 +814,7 @@ cudaError_t fused_forward(const __nv_bfloat16 *X, int64_t n, const __nv_bfloat16
   if (e != cudaSuccess) return e;
   const int64_t tiles = (n + TM - 1) / TM;
   const int grid = (int)(tiles < n_sm ? tiles : n_sm);
-  fused_forward_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(X, n, wc, params, y, err);
+  fused_forward_kernel<<<grid, kThreads, SMEM_BYTES, s>>>(map, n, wc, params, y, err);
   return cudaGetLastError();
 }
 
