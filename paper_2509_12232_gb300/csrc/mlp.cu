@@ -67,12 +67,16 @@ __global__ void colsum_part_kernel(const __nv_bfloat16 *X, int rows, int cols, i
   }
 }
 
-__global__ void reduce_parts_kernel(const float *part, int blocks, int width, float *out) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+// out[c] = sum over b of part[b][c], one warp per column: lane l adds parts
+// l, l + 32, ... in order, then a fixed shuffle tree (the same sum every run).
+__global__ void reduce_cols_kernel(const float *part, int blocks, int width, float *out) {
+  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (c >= width) return;
   float s = 0.0f;
-  for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * width + c];
-  out[c] = s;
+  for (int b = lane; b < blocks; b += 32) s += part[(int64_t)b * width + c];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) out[c] = s;
 }
 
 // Adam on FP32 masters (Kingma & Ba 2015): m = b1 m + (1-b1) g; v = b2 v +
@@ -132,17 +136,17 @@ cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const
                           const float *Z3, const float *w4, __nv_bfloat16 *dZ3, float *part,
                           int blocks, float *out /* [HIDDEN + 2] */, cudaStream_t s) {
   out_layer_bwd_kernel<<<blocks, HIDDEN, 0, s>>>(y, t, n, rows, H3, Z3, w4, dZ3, part);
-  reduce_parts_kernel<<<(HIDDEN + 2 + 127) / 128, 128, 0, s>>>(part, blocks, HIDDEN + 2, out);
+  reduce_cols_kernel<<<(HIDDEN + 2 + 7) / 8, 256, 0, s>>>(part, blocks, HIDDEN + 2, out);
   return cudaGetLastError();
 }
 
 cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, float *scratch,
                    cudaStream_t s) {
   if (rows <= 0) return cudaMemsetAsync(out, 0, sizeof(float) * cols, s);
-  const int chunks = rows < 64 ? rows : 64;
+  const int chunks = rows < kColsumChunks ? rows : kColsumChunks;
   const int chunk_rows = (rows + chunks - 1) / chunks;
   colsum_part_kernel<<<chunks, 256, 0, s>>>(X, rows, cols, chunk_rows, scratch);
-  reduce_parts_kernel<<<(cols + 255) / 256, 256, 0, s>>>(scratch, chunks, cols, out);
+  reduce_cols_kernel<<<(cols + 7) / 8, 256, 0, s>>>(scratch, chunks, cols, out);
   return cudaGetLastError();
 }
 

@@ -67,8 +67,9 @@ cudaError_t out_layer(const __nv_bfloat16 *H, const float *w, const float *b, in
 cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const __nv_bfloat16 *H3,
                           const float *Z3, const float *w4, __nv_bfloat16 *dZ3, float *part,
                           int blocks, float *out, cudaStream_t s);
-// out[c] = sum over rows of X[r][c]: row chunks in parallel, then a fixed-order sum
-// (scratch: at least 64 * cols floats).
+// out[c] = sum over rows of X[r][c]: kColsumChunks row chunks in parallel, then a
+// fixed-order sum (scratch: at least kColsumChunks * cols floats).
+constexpr int kColsumChunks = 128;
 cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, float *scratch,
                    cudaStream_t s);
 // BF16 copies of W1..W3 that the training products read: w16[l] [in][out], wt16[l] [out][in].

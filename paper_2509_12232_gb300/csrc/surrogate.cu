@@ -173,6 +173,11 @@ struct dock_surrogate {
   int *d_step = nullptr;
   cudaStream_t ts = nullptr;  // training runs (and its step graph is captured) on this stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // the backward pass's weight gradients (ts_w) and bias gradients (ts_c) run
+  // beside its chain of input gradients, forked and joined by events
+  cudaStream_t ts_w = nullptr, ts_c = nullptr;
+  cudaEvent_t ev_dz[3] = {nullptr, nullptr, nullptr}, ev_w = nullptr, ev_c = nullptr;
+  float *cpart = nullptr;  // column-sum partials of the bias gradients
   float t_mean = 0.0f, t_std = 1.0f, t_clip = 1e30f;
   // weights of the fused tensor-core forward pass (refreshed lazily after the
   // FP32 masters change) and its device error flag
@@ -189,7 +194,11 @@ struct dock_surrogate {
     if (d_step) cudaFree(d_step);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
+    for (cudaEvent_t e : {ev_dz[0], ev_dz[1], ev_dz[2], ev_w, ev_c}) if (e) cudaEventDestroy(e);
     if (ts) cudaStreamDestroy(ts);
+    if (ts_w) cudaStreamDestroy(ts_w);
+    if (ts_c) cudaStreamDestroy(ts_c);
+    if (cpart) cudaFree(cpart);
     for (int l = 0; l < 3; ++l) {
       if (w16[l]) cudaFree(w16[l]);
       if (wt16[l]) cudaFree(wt16[l]);
@@ -207,7 +216,7 @@ struct dock_surrogate {
 static const int kIn[3] = {FEATURES, HIDDEN, HIDDEN};
 static const int kOffW[3] = {mlp::OFF_W1, mlp::OFF_W2, mlp::OFF_W3};
 static const int kOffB[3] = {mlp::OFF_B1, mlp::OFF_B2, mlp::OFF_B3};
-static const int kBwdBlocks = 128;
+static const int kBwdBlocks = 512;
 static const int64_t kWpartElems = 32 * HIDDEN * HIDDEN;  // 32 K splits of a 256 x 256 gradient
 
 static int ensure_workspace(dock_surrogate *S, int rows) {
@@ -269,19 +278,25 @@ static int forward(dock_surrogate *S, int rows, bool keep, cudaStream_t s) {
 }
 
 // Gradients of loss = mean over the first n rows of (y - t)^2 into S->g
-// (rows >= n padded: contribute nothing). Needs forward(keep = true).
+// (rows >= n padded: contribute nothing). Needs forward(keep = true). The
+// chain dZ_2 -> dZ_1 -> dZ_0 runs on s; each layer's weight gradient (on
+// ts_w) and bias gradient (on ts_c) start once its dZ is written, and s waits
+// for both before it returns (also inside a captured step graph).
 static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
   SCU(mlp::out_layer_bwd(S->y, S->t, n, rows, S->H[2], S->Z[2], S->p + mlp::OFF_W4, S->dZ[2],
                          S->part, kBwdBlocks, S->outg, s));
   SCU(cudaMemcpyAsync(S->g + mlp::OFF_W4, S->outg, sizeof(float) * (HIDDEN + 1),
                       cudaMemcpyDeviceToDevice, s));
   for (int l = 2; l >= 0; --l) {
+    SCU(cudaEventRecord(S->ev_dz[l], s));
+    SCU(cudaStreamWaitEvent(S->ts_w, S->ev_dz[l], 0));
+    SCU(cudaStreamWaitEvent(S->ts_c, S->ev_dz[l], 0));
     const __nv_bfloat16 *act_in = l ? S->H[l - 1] : S->X;
-    // dW_l = act_in^T dZ_l (tensor cores, K = rows split over CTAs); db_l =
-    // column sums of dZ_l
+    // dW_l = act_in^T dZ_l (tensor cores, K = rows split over CTAs)
     SCU(mlp::tc_gemm_tn_f32(act_in, kIn[l], S->dZ[l], rows, S->g + kOffW[l], S->at, S->bt,
-                            S->wpart, kWpartElems, S->err, s));
-    SCU(mlp::colsum(S->dZ[l], rows, HIDDEN, S->g + kOffB[l], S->wpart, s));
+                            S->wpart, kWpartElems, S->err, S->ts_w));
+    // db_l = column sums of dZ_l
+    SCU(mlp::colsum(S->dZ[l], rows, HIDDEN, S->g + kOffB[l], S->cpart, S->ts_c));
     if (l) {
       // dZ_{l-1} = (dZ_l W_l^T) * gelu'(Z_{l-1})
       mlp::Epilogue ep{};
@@ -292,6 +307,10 @@ static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
                           ep, S->err, s));
     }
   }
+  SCU(cudaEventRecord(S->ev_w, S->ts_w));
+  SCU(cudaEventRecord(S->ev_c, S->ts_c));
+  SCU(cudaStreamWaitEvent(s, S->ev_w, 0));
+  SCU(cudaStreamWaitEvent(s, S->ev_c, 0));
   return DOCK_OK;
 }
 
@@ -327,6 +346,11 @@ extern "C" int dock_surrogate_create(uint64_t seed, void *stream, dock_surrogate
   SCU(cudaMalloc(&S->err, sizeof(int)));
   SCU(cudaMalloc(&S->d_r0, sizeof(int64_t)));
   SCU(cudaStreamCreateWithFlags(&S->ts, cudaStreamNonBlocking));
+  SCU(cudaStreamCreateWithFlags(&S->ts_w, cudaStreamNonBlocking));
+  SCU(cudaStreamCreateWithFlags(&S->ts_c, cudaStreamNonBlocking));
+  for (cudaEvent_t *e : {&S->ev_dz[0], &S->ev_dz[1], &S->ev_dz[2], &S->ev_w, &S->ev_c})
+    SCU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  SCU(cudaMalloc(&S->cpart, sizeof(float) * mlp::kColsumChunks * HIDDEN));
   SCU(cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
   SCU(cudaEventCreateWithFlags(&S->ev_out, cudaEventDisableTiming));
   SCU(cudaMalloc(&S->d_step, sizeof(int)));

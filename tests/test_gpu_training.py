@@ -119,4 +119,12 @@ def test_two_batch_epoch_uses_the_order_in_batches(dock, data):
         o.adam_step(p, m, v, grad.cpu().numpy().astype(np.float64), step, lr=LR)
         at = p.astype(np.float32)
     err = np.abs(W2.astype(np.float64) - p)
-    assert np.all(err <= 1e-7 + 1e-6 * np.abs(p)), float(err.max())
+    # Step 2's BF16 weight copies are rounded from FP32 masters that differ by
+    # an FP32 ulp between the two runs (FP32 Adam in training, FP64 Adam here),
+    # so a copy near a BF16 rounding boundary can round the other way and move
+    # that step's gradients by a BF16 step: a few masters then differ by a
+    # small fraction of the learning rate. Taking the batches in another order
+    # moves them by about the learning rate (1e-3).
+    tight = err <= 1e-7 + 1e-6 * np.abs(p)
+    assert tight.mean() >= 0.999, (float(tight.mean()), float(err.max()))
+    assert np.all(err <= 2e-6 + 1e-5 * np.abs(p)), float(err.max())
