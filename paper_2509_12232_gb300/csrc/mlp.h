@@ -60,6 +60,8 @@ struct Epilogue {
   const float *zin;         // GELU_BWD: pre-activations
   int ldc;
   int64_t split_stride;     // STORE with split K: elements between the splits' partial outputs
+  __nv_bfloat16 *c16t;      // BIAS_GELU / GELU_BWD, or null: c16 transposed, [col][row]
+  int64_t ldt;              // row stride of c16t (elements)
 };
 
 cudaError_t out_layer(const __nv_bfloat16 *H, const float *w, const float *b, int rows, float *y,
@@ -108,6 +110,12 @@ cudaError_t tc_gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt,
 cudaError_t tc_gemm_tn_f32(const __nv_bfloat16 *A, int M, const __nv_bfloat16 *B, int K, float *C,
                            __nv_bfloat16 *at, __nv_bfloat16 *bt, float *scratch,
                            int64_t scratch_elems, int *err, cudaStream_t s);
+// The same from operands already K-major: at [M][K] (A^T) and bt [256][K] (B^T).
+cudaError_t tc_gemm_tt_f32(const __nv_bfloat16 *at, const __nv_bfloat16 *bt, int M, int K, float *C,
+                           float *scratch, int64_t scratch_elems, int *err, cudaStream_t s);
+// out[c][r] = in[r][c] for in [rows][cols] BF16.
+cudaError_t transpose_bf16(const __nv_bfloat16 *in, int rows, int cols, __nv_bfloat16 *out,
+                           cudaStream_t s);
 
 }  // namespace mlp
 }  // namespace dk

@@ -548,6 +548,19 @@ __global__ void __maxnreg__(kMaxRegs)
 // columns 64 (w / 4) .. + 63. Every mbarrier wait is bounded as in the
 // forward kernel; a timeout sets *err and the CTA writes nothing.
 // ---------------------------------------------------------------------------
+// The transposed copy c16t[c][r] (row stride ldt) of a thread's 32 BF16
+// values h (row r, columns col..col+31): the lanes of a warp hold 32
+// consecutive rows, so each column is one 64-byte store per warp.
+__device__ __forceinline__ void store_transposed(const Epilogue &ep, const uint32_t (&h)[16],
+                                                 int64_t row, int col) {
+  if (ep.c16t == nullptr) return;
+  unsigned short *t = reinterpret_cast<unsigned short *>(ep.c16t);
+#pragma unroll
+  for (int k = 0; k < 32; ++k)
+    t[(int64_t)(col + k) * ep.ldt + row] =
+        (unsigned short)((k & 1) ? (h[k >> 1] >> 16) : (h[k >> 1] & 0xffffu));
+}
+
 constexpr int GK = 64;                     // K per chunk
 constexpr int GA_BYTES = 128 * GK * 2;     // A chunk: 16 KB
 constexpr int GN = 128;                    // columns per CTA
@@ -682,6 +695,7 @@ __global__ void __launch_bounds__(G_THREADS, 3)
         uint4 *dst = reinterpret_cast<uint4 *>(ep.c16 + o);
 #pragma unroll
         for (int j = 0; j < 4; ++j) dst[j] = make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
+        store_transposed(ep, h, row, col);
       } else {  // EPI_GELU_BWD: dZ = dH gelu'(Z)
         uint32_t h[16];
         const float4 *zin = reinterpret_cast<const float4 *>(ep.zin + o);
@@ -696,6 +710,7 @@ __global__ void __launch_bounds__(G_THREADS, 3)
         uint4 *dst = reinterpret_cast<uint4 *>(ep.c16 + o);
 #pragma unroll
         for (int j = 0; j < 4; ++j) dst[j] = make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
+        store_transposed(ep, h, row, col);
       }
     }
   }
@@ -852,16 +867,18 @@ cudaError_t tc_gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt,
   return cudaErrorInvalidValue;
 }
 
-cudaError_t tc_gemm_tn_f32(const __nv_bfloat16 *A, int M, const __nv_bfloat16 *B, int K, float *C,
-                           __nv_bfloat16 *at, __nv_bfloat16 *bt, float *scratch,
-                           int64_t scratch_elems, int *err, cudaStream_t s) {
+cudaError_t transpose_bf16(const __nv_bfloat16 *in, int rows, int cols, __nv_bfloat16 *out,
+                           cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  transpose_bf16_kernel<<<dim3((cols + 31) / 32, (rows + 31) / 32), dim3(32, 8), 0, s>>>(in, rows,
+                                                                                       cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_tt_f32(const __nv_bfloat16 *at, const __nv_bfloat16 *bt, int M, int K, float *C,
+                           float *scratch, int64_t scratch_elems, int *err, cudaStream_t s) {
   if (M <= 0) return cudaSuccess;
   if (M % 128 || K % GK || K <= 0) return cudaErrorInvalidValue;
-  const dim3 tb(32, 8);
-  transpose_bf16_kernel<<<dim3((M + 31) / 32, (K + 31) / 32), tb, 0, s>>>(A, K, M, at);
-  transpose_bf16_kernel<<<dim3((HIDDEN + 31) / 32, (K + 31) / 32), tb, 0, s>>>(B, K, HIDDEN, bt);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   // enough K splits to give about 128 CTAs, each a multiple of the chunk
   int splits = 1;
   const int tiles = (M / 128) * (HIDDEN / GN);
@@ -872,11 +889,22 @@ cudaError_t tc_gemm_tn_f32(const __nv_bfloat16 *A, int M, const __nv_bfloat16 *B
   ep.ldc = HIDDEN;
   ep.c32 = splits > 1 ? scratch : C;
   ep.split_stride = (int64_t)M * HIDDEN;
-  e = tc_gemm_launch<EPI_STORE_F32>(at, K, bt, K, M, K / splits, splits, ep, err, s);
+  cudaError_t e = tc_gemm_launch<EPI_STORE_F32>(at, K, bt, K, M, K / splits, splits, ep, err, s);
   if (e != cudaSuccess || splits == 1) return e;
   const int64_t w = (int64_t)M * HIDDEN;
   sum_parts_kernel<<<(unsigned)((w + 255) / 256), 256, 0, s>>>(scratch, splits, w, C);
   return cudaGetLastError();
+}
+
+cudaError_t tc_gemm_tn_f32(const __nv_bfloat16 *A, int M, const __nv_bfloat16 *B, int K, float *C,
+                           __nv_bfloat16 *at, __nv_bfloat16 *bt, float *scratch,
+                           int64_t scratch_elems, int *err, cudaStream_t s) {
+  if (M <= 0) return cudaSuccess;
+  if (M % 128 || K % GK || K <= 0) return cudaErrorInvalidValue;
+  cudaError_t e = transpose_bf16(A, K, M, at, s);
+  if (e == cudaSuccess) e = transpose_bf16(B, K, HIDDEN, bt, s);
+  if (e != cudaSuccess) return e;
+  return tc_gemm_tt_f32(at, bt, M, K, C, scratch, scratch_elems, err, s);
 }
 
 }  // namespace mlp

@@ -165,8 +165,11 @@ struct dock_surrogate {
   __nv_bfloat16 *X = nullptr, *H[3] = {nullptr, nullptr, nullptr}, *dZ[3] = {nullptr, nullptr, nullptr};
   float *Z[3] = {nullptr, nullptr, nullptr}, *y = nullptr, *t = nullptr, *part = nullptr,
         *outg = nullptr;
-  // K-major copies of a weight gradient's operands (activations^T, dZ^T)
+  // K-major copies of a weight gradient's operands (activations^T, dZ^T):
+  // H_0^T, H_1^T and dZ_0^T, dZ_1^T written by the epilogues that make them,
+  // X^T and dZ_2^T by transposes (into at, bt)
   __nv_bfloat16 *at = nullptr, *bt = nullptr;
+  __nv_bfloat16 *Ht[2] = {nullptr, nullptr}, *dZt[2] = {nullptr, nullptr};
   double *stats = nullptr;
   int step = 0;
   int64_t *d_r0 = nullptr;  // batch start and Adam step of a graph-replayed training step
@@ -209,6 +212,10 @@ struct dock_surrogate {
     if (X) cudaFree(X);
     if (at) cudaFree(at);
     if (bt) cudaFree(bt);
+    for (int l = 0; l < 2; ++l) {
+      if (Ht[l]) cudaFree(Ht[l]);
+      if (dZt[l]) cudaFree(dZt[l]);
+    }
     if (stats) cudaFree(stats);
   }
 };
@@ -225,6 +232,11 @@ static int ensure_workspace(dock_surrogate *S, int rows) {
   if (S->at) cudaFree(S->at);
   if (S->bt) cudaFree(S->bt);
   S->at = S->bt = nullptr;
+  for (int l = 0; l < 2; ++l) {
+    if (S->Ht[l]) cudaFree(S->Ht[l]);
+    if (S->dZt[l]) cudaFree(S->dZt[l]);
+    S->Ht[l] = S->dZt[l] = nullptr;
+  }
   for (int l = 0; l < 3; ++l) {
     if (S->H[l]) cudaFree(S->H[l]);
     if (S->dZ[l]) cudaFree(S->dZ[l]);
@@ -240,6 +252,10 @@ static int ensure_workspace(dock_surrogate *S, int rows) {
   SCU(cudaMalloc(&S->X, sizeof(__nv_bfloat16) * (size_t)rows * FEATURES));
   SCU(cudaMalloc(&S->at, sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
   SCU(cudaMalloc(&S->bt, sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
+  for (int l = 0; l < 2; ++l) {
+    SCU(cudaMalloc(&S->Ht[l], sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
+    SCU(cudaMalloc(&S->dZt[l], sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
+  }
   for (int l = 0; l < 3; ++l) {
     SCU(cudaMalloc(&S->H[l], sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
     SCU(cudaMalloc(&S->dZ[l], sizeof(__nv_bfloat16) * (size_t)rows * HIDDEN));
@@ -267,6 +283,8 @@ static int forward(dock_surrogate *S, int rows, bool keep, cudaStream_t s) {
     mlp::Epilogue ep{};
     ep.c32 = keep ? S->Z[l] : nullptr;
     ep.c16 = S->H[l];
+    ep.c16t = keep && l < 2 ? S->Ht[l] : nullptr;  // the next layer's weight gradient reads H_l^T
+    ep.ldt = rows;
     ep.bias = S->p + kOffB[l];
     ep.ldc = HIDDEN;
     SCU(mlp::tc_gemm_nt(in, kIn[l], S->wt16[l], kIn[l], rows, kIn[l], mlp::EPI_BIAS_GELU, ep,
@@ -291,16 +309,22 @@ static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
     SCU(cudaEventRecord(S->ev_dz[l], s));
     SCU(cudaStreamWaitEvent(S->ts_w, S->ev_dz[l], 0));
     SCU(cudaStreamWaitEvent(S->ts_c, S->ev_dz[l], 0));
-    const __nv_bfloat16 *act_in = l ? S->H[l - 1] : S->X;
-    // dW_l = act_in^T dZ_l (tensor cores, K = rows split over CTAs)
-    SCU(mlp::tc_gemm_tn_f32(act_in, kIn[l], S->dZ[l], rows, S->g + kOffW[l], S->at, S->bt,
-                            S->wpart, kWpartElems, S->err, S->ts_w));
+    // dW_l = act_in^T dZ_l (tensor cores, K = rows split over CTAs) from
+    // K-major copies: H_{l-1}^T and dZ_l^T from the epilogues, X^T and dZ_2^T
+    // transposed here
+    const __nv_bfloat16 *at = l ? S->Ht[l - 1] : S->at, *bt = l < 2 ? S->dZt[l] : S->bt;
+    if (l == 0) SCU(mlp::transpose_bf16(S->X, rows, FEATURES, S->at, S->ts_w));
+    if (l == 2) SCU(mlp::transpose_bf16(S->dZ[2], rows, HIDDEN, S->bt, S->ts_w));
+    SCU(mlp::tc_gemm_tt_f32(at, bt, kIn[l], rows, S->g + kOffW[l], S->wpart, kWpartElems, S->err,
+                            S->ts_w));
     // db_l = column sums of dZ_l
     SCU(mlp::colsum(S->dZ[l], rows, HIDDEN, S->g + kOffB[l], S->cpart, S->ts_c));
     if (l) {
       // dZ_{l-1} = (dZ_l W_l^T) * gelu'(Z_{l-1})
       mlp::Epilogue ep{};
       ep.c16 = S->dZ[l - 1];
+      ep.c16t = S->dZt[l - 1];
+      ep.ldt = rows;
       ep.zin = S->Z[l - 1];
       ep.ldc = HIDDEN;
       SCU(mlp::tc_gemm_nt(S->dZ[l], HIDDEN, S->w16[l], HIDDEN, rows, HIDDEN, mlp::EPI_GELU_BWD,
