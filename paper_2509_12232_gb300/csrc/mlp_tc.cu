@@ -535,17 +535,17 @@ __global__ void __maxnreg__(kMaxRegs)
 
 // ---------------------------------------------------------------------------
 // Training products on tcgen05: C[M][256] = A[M][K] Bt[256][K]^T.
-// CTA (blockIdx.x, split blockIdx.y, column half blockIdx.z) computes rows
-// m0 .. m0 + 127 and columns 128 z .. + 127 over its K range in chunks of 64
-// (two halves per row block double the CTAs of a 4,096-row batch): the 256
-// threads move a chunk of A (128 x 64) and of Bt (its 128 rows x 64) from
+// CTA (blockIdx.x, split blockIdx.y, column quarter blockIdx.z) computes rows
+// m0 .. m0 + 127 and columns 64 z .. + 63 over its K range in chunks of 64
+// (four quarters per row block give a 4,096-row batch 128 CTAs): the 256
+// threads move a chunk of A (128 x 64) and of Bt (its 64 rows x 64) from
 // global memory into one of two stages in the K-major core-matrix layout (a
 // warp stores eight rows x 16 bytes of one K block per 128-byte step), one
-// thread issues four MMAs (M 128, N 128, K 16) into the 128-column FP32
+// thread issues four MMAs (M 128, N 64, K 16) into the 64-column FP32
 // accumulator and commits them to the stage's mbarrier, and the next
 // chunk's global loads are in flight meanwhile. The epilogue reads the
 // accumulator with tcgen05.ld: warp w takes lanes 32 (w mod 4) .. + 31 and
-// columns 64 (w / 4) .. + 63. Every mbarrier wait is bounded as in the
+// columns 32 (w / 4) .. + 31. Every mbarrier wait is bounded as in the
 // forward kernel; a timeout sets *err and the CTA writes nothing.
 // ---------------------------------------------------------------------------
 // The transposed copy c16t[c][r] (row stride ldt) of a thread's 32 BF16
@@ -563,14 +563,15 @@ __device__ __forceinline__ void store_transposed(const Epilogue &ep, const uint3
 
 constexpr int GK = 64;                     // K per chunk
 constexpr int GA_BYTES = 128 * GK * 2;     // A chunk: 16 KB
-constexpr int GN = 128;                    // columns per CTA
-constexpr int GB_BYTES = GN * GK * 2;      // Bt chunk: 16 KB
+constexpr int GN = 64;                     // columns per CTA (4 CTAs across 256 columns)
+constexpr int GB_BYTES = GN * GK * 2;      // Bt chunk: 8 KB
+constexpr int GB_STEPS = GN / 32;          // 16-byte pieces of the Bt chunk per thread
 constexpr int G_STAGE = GA_BYTES + GB_BYTES;
 constexpr int G_SMEM = 2 * G_STAGE + 64;
 constexpr int G_THREADS = 256;
 
 template <int EPI>
-__global__ void __launch_bounds__(G_THREADS, 3)
+__global__ void __launch_bounds__(G_THREADS, 4)
     tc_gemm_kernel(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb, int k_split,
                    Epilogue ep, int *err) {
   extern __shared__ __align__(1024) unsigned char sm[];
@@ -589,8 +590,8 @@ __global__ void __launch_bounds__(G_THREADS, 3)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
-                     smem_u32(tslot))
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)), "n"(GN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -600,7 +601,7 @@ __global__ void __launch_bounds__(G_THREADS, 3)
   const uint32_t tmem = *tslot;
   // a chunk in 16-byte pieces: step v of a warp covers rows 8 (v mod G) + (lane
   // mod 8) and K block 4 (v / G) + lane / 8 (G = row groups of the operand)
-  uint4 ra[4], rb[4];
+  uint4 ra[4], rb[GB_STEPS];
   auto load = [&](int c) {
     const int64_t kk = k0 + (int64_t)c * GK;
 #pragma unroll
@@ -609,8 +610,9 @@ __global__ void __launch_bounds__(G_THREADS, 3)
       ra[i] = __ldg(reinterpret_cast<const uint4 *>(A + (m0 + row) * lda + kk + 8 * kb));
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int v = warp + 8 * i, row = 8 * (v & 15) + (lane & 7), kb = 4 * (v >> 4) + (lane >> 3);
+    for (int i = 0; i < GB_STEPS; ++i) {
+      const int v = warp + 8 * i, row = 8 * (v % (GN / 8)) + (lane & 7),
+                kb = 4 * (v / (GN / 8)) + (lane >> 3);
       rb[i] = __ldg(reinterpret_cast<const uint4 *>(Bt + (int64_t)row * ldb + kk + 8 * kb));
     }
   };
@@ -622,8 +624,9 @@ __global__ void __launch_bounds__(G_THREADS, 3)
       *reinterpret_cast<uint4 *>(sa + canon_off(row, 8 * kb, GK)) = ra[i];
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int v = warp + 8 * i, row = 8 * (v & 15) + (lane & 7), kb = 4 * (v >> 4) + (lane >> 3);
+    for (int i = 0; i < GB_STEPS; ++i) {
+      const int v = warp + 8 * i, row = 8 * (v % (GN / 8)) + (lane & 7),
+                kb = 4 * (v / (GN / 8)) + (lane >> 3);
       *reinterpret_cast<uint4 *>(sb + canon_off(row, 8 * kb, GK)) = rb[i];
     }
   };
@@ -668,8 +671,8 @@ __global__ void __launch_bounds__(G_THREADS, 3)
     const int64_t row = m0 + 32 * quad + lane;
     const uint32_t t_lane = tmem + ((uint32_t)(32 * quad) << 16);
 #pragma unroll 1
-    for (int cc = 0; cc < 2; ++cc) {
-      const int tcol = 64 * half + 32 * cc, col = n0 + tcol;
+    for (int cc = 0; cc < GN / 64; ++cc) {
+      const int tcol = (GN / 2) * half + 32 * cc, col = n0 + tcol;
       uint32_t r[32];
       tmem_ld32(t_lane + (uint32_t)tcol, r);
       tmem_wait(r);
@@ -722,7 +725,8 @@ __global__ void __launch_bounds__(G_THREADS, 3)
   __syncthreads();
   fence_after_sync();
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(GN)
+                 : "memory");
 }
 
 // out [cols][rows] = in [rows][cols]^T (BF16; 32 x 32 tiles through shared memory).
