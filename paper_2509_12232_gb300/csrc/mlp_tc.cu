@@ -9,9 +9,9 @@
 //     reads without swizzling (8 rows x 16 bytes per 128-byte block, blocks
 //     ordered by row group then by K); its accumulator is one half (256
 //     columns) of the CTA's tensor memory;
-//   - the BF16 weights are kept in global memory as chunks of 32 K columns
-//     (16 KB, the same layout with K = 32); a copy warp streams them, in the
-//     order the products use them, through a ring of five shared-memory
+//   - the BF16 weights are kept in global memory as chunks of 64 K columns
+//     (32 KB, the same layout with K = 64); a copy warp streams them, in the
+//     order the products use them, through a ring of two shared-memory
 //     stages (bulk asynchronous copies completing on the stage's "full"
 //     mbarrier; the products that read a stage commit to its "empty" one);
 //   - an MMA warp issues, per slot and layer, tcgen05.mma (M = 128, N = 256,
@@ -57,10 +57,10 @@ constexpr int kPartChunks = HIDDEN / 32 / kParts;  // 32-column accumulator read
 // the register file, and the warps are spread over them round robin.
 constexpr int kMaxRegs = (16384 / (32 * ((kEpiWarps + 2 + 3) / 4))) / 8 * 8;
 constexpr int ACT_BYTES = TM * HIDDEN * 2;    // one slot's A operand (64 KB)
-constexpr int KC = 32;                        // K columns of one weight chunk
-constexpr int WCH_ELEMS = HIDDEN * KC;        // BF16 values of a chunk (16 KB)
+constexpr int KC = 64;                        // K columns of one weight chunk
+constexpr int WCH_ELEMS = HIDDEN * KC;        // BF16 values of a chunk (32 KB)
 constexpr int WCH_BYTES = 2 * WCH_ELEMS;
-constexpr int kStages = 5;                    // weight chunks in shared memory
+constexpr int kStages = 2;                    // weight chunks in shared memory
 // mbarriers: weight stages full / empty, slot accumulators complete, slot A
 // operands ready, slot features landed, slot A operand free (its last
 // product done), output partials full / empty, products drained at the end
@@ -70,10 +70,11 @@ constexpr int B_WFULL = 0, B_WEMPTY = kStages, B_ACC = 2 * kStages, B_ACT = B_AC
 constexpr int X_BYTES = TM * FEATURES * 2;    // one feature tile (32 KB)
 constexpr int OFF_WST = 2 * ACT_BYTES;
 constexpr int OFF_BAR = OFF_WST + kStages * WCH_BYTES;
-constexpr int OFF_YP = OFF_BAR + 256;         // barriers, TMEM address, abort flag
+constexpr int kBarBytes = (8 * N_BARS + 8 + 127) / 128 * 128;
+constexpr int OFF_YP = OFF_BAR + kBarBytes;         // barriers, TMEM address, abort flag
 constexpr int OFF_PAR = OFF_YP + 2 * (kParts - 1) * TM * 4;  // output partials of parts >= 1
 constexpr int SMEM_BYTES = OFF_PAR + 4 * HIDDEN * 4;         // + biases b1..b3 and w4
-static_assert(8 * N_BARS + 8 <= 256, "barrier block");
+static_assert(8 * N_BARS + 8 <= kBarBytes, "barrier block");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 constexpr int WC_L2 = HIDDEN * FEATURES;      // weight values of layer 1 (and of 1 + 2: WC_L3)
 constexpr int WC_L3 = WC_L2 + HIDDEN * HIDDEN;
