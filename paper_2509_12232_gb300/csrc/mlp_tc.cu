@@ -23,10 +23,12 @@
 //     may access) and columns 64 (w / 4) .. + 63 with tcgen05.ld: bias, GELU,
 //     rounding to BF16 and stores into the slot's A operand for the next
 //     layer; after the third layer each thread forms a quarter of its row's
-//     output (a dot product with the FP32 w4), parts 1-3 hand theirs to part 0
-//     through shared memory, and the slot receives its next tile's features
-//     (read from global memory during that epilogue). Each step signals the
-//     MMA warp through the slot's "A ready" mbarrier.
+//     output (a dot product with the FP32 w4) and parts 1-3 hand theirs to
+//     part 0 through shared memory. Each step signals the MMA warp through
+//     the slot's "A ready" mbarrier; the copy warp fetches the slot's next
+//     features (2-D tensor copies) once the slot's last product is done. The hidden activations
+//     are kept doubled and W2, W3 and w4 halved (exact powers of two: the
+//     same roundings and products, one multiply fewer per activation).
 // Every mbarrier wait is bounded (one second of globaltimer) and also ends
 // when another role has given up; a timeout sets *err, the roles leave their
 // loops (the caller fills the output with NaN beforehand), and the tensor
@@ -253,6 +255,19 @@ __device__ __forceinline__ float2 gelu2(float2 z) {
   return __ffma2_rn(h, th, h);
 }
 
+// Twice gelu2, z (1 + tanh(u)) in one fused multiply-add: the same value
+// scaled by 2 exactly (one multiply fewer). The fused forward pass keeps its
+// hidden activations scaled by 2 and the weights that read them (W2, W3, w4)
+// scaled by 1/2, powers of two that leave every BF16 rounding and every
+// product unchanged.
+__device__ __forceinline__ float2 gelu2_twice(float2 z) {
+  const float2 z2 = __fmul2_rn(z, z);
+  const float2 t = __ffma2_rn(make_float2(kGeluC1, kGeluC1), z2, make_float2(kGeluC0, kGeluC0));
+  const float2 u = __fmul2_rn(z, t);
+  const float2 th = make_float2(tanh_sfu(u.x), tanh_sfu(u.y));
+  return __ffma2_rn(z, th, z);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<const uint32_t *>(&h);
@@ -266,7 +281,7 @@ __global__ void __maxnreg__(kMaxRegs)
   uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + OFF_BAR + 8 * N_BARS);
   volatile int *abort_flag = reinterpret_cast<volatile int *>(sm + OFF_BAR + 8 * N_BARS + 4);
   float *ypart = reinterpret_cast<float *>(sm + OFF_YP);   // [slot][part - 1][row]
-  float *s_par = reinterpret_cast<float *>(sm + OFF_PAR);  // b1, b2, b3, w4 (256 each)
+  float *s_par = reinterpret_cast<float *>(sm + OFF_PAR);  // b1, b2, b3, w4 / 2 (256 each)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   auto bar = [&](int i) { return smem_u32(&bars[i]); };
   const uint32_t s_act = smem_u32(sm), s_wst = smem_u32(sm + OFF_WST);
@@ -295,7 +310,7 @@ __global__ void __maxnreg__(kMaxRegs)
   }
   for (int i = tid; i < 3 * HIDDEN; i += kThreads)
     s_par[i] = params[(i >> 8) == 0 ? OFF_B1 + i : ((i >> 8) == 1 ? OFF_B2 + i - 256 : OFF_B3 + i - 512)];
-  for (int i = tid; i < HIDDEN; i += kThreads) s_par[3 * HIDDEN + i] = params[OFF_W4 + i];
+  for (int i = tid; i < HIDDEN; i += kThreads) s_par[3 * HIDDEN + i] = 0.5f * params[OFF_W4 + i];
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -458,7 +473,7 @@ __global__ void __maxnreg__(kMaxRegs)
               uint32_t w[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                const float2 a = gelu2(__fadd2_rn(make_float2(__uint_as_float(r[8 * q + 2 * e]),
+                const float2 a = gelu2_twice(__fadd2_rn(make_float2(__uint_as_float(r[8 * q + 2 * e]),
                                                               __uint_as_float(r[8 * q + 2 * e + 1])),
                                                   make_float2(bq[2 * e], bq[2 * e + 1])));
                 w[e] = pack_bf16(a.x, a.y);
@@ -776,8 +791,10 @@ __global__ void canon_weights_kernel(const float *p, __nv_bfloat16 *wc) {
     const int K = layer == 0 ? FEATURES : HIDDEN;
     const int nn = e / K, k = e % K;  // output nn, input k
     const int off_w = layer == 0 ? OFF_W1 : (layer == 1 ? OFF_W2 : OFF_W3);
+    // W2, W3 halved: they read activations kept doubled (gelu2_twice)
+    const float w = p[off_w + k * HIDDEN + nn];
     wc[(wchunk0(layer) + k / KC) * WCH_ELEMS + canon_off(nn, k % KC, KC) / 2] =
-        __float2bfloat16_rn(p[off_w + k * HIDDEN + nn]);
+        __float2bfloat16_rn(layer == 0 ? w : 0.5f * w);
   }
 }
 
