@@ -20,9 +20,11 @@
 //     mbarrier;
 //   - 16 epilogue warps drain a finished accumulator, warp w reading lanes
 //     32 (w mod 4) .. + 31 (the lane quarter its position in the warp group
-//     may access) and columns 64 (w / 4) .. + 63 with tcgen05.ld: bias, GELU,
+//     may access) and columns 64 (w / 4) .. + 63 with tcgen05.ld: GELU,
 //     rounding to BF16 and stores into the slot's A operand for the next
-//     layer; after the third layer each thread forms a quarter of its row's
+//     layer, then they set those columns to the next layer's bias with
+//     tcgen05.st, so that the products accumulate onto it; after the third
+//     layer each thread forms a quarter of its row's
 //     output (a dot product with the FP32 w4) and parts 1-3 hand theirs to
 //     part 0 through shared memory. Each step signals the MMA warp through
 //     the slot's "A ready" mbarrier; the copy warp fetches the slot's next
@@ -243,6 +245,24 @@ __device__ __forceinline__ void tmem_wait(uint32_t (&r)[32]) {
                : "memory");
 }
 
+// Write 32 consecutive accumulator columns of this thread's lane.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31, %32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]),
+      "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]),
+      "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 // gelu_t (mlp.h) on two activations: packed two-wide FP32 arithmetic (the same
 // operations in the same order, one instruction for both) around two tanh
 // on the special-function unit.
@@ -379,9 +399,9 @@ __global__ void __maxnreg__(kMaxRegs)
       for (int i0 = 0; i0 < n_local && ok; i0 += 2)
         for (int layer = 0; layer < 3 && ok; ++layer)
           for (int s = 0; s < 2 && ok && i0 + s < n_local; ++s) {
-            // layer 0: the features have landed (and, after the slot's first
-            // tile, the epilogue has read the accumulator); layers 1-2: the
-            // epilogue has written this layer's A operand
+            // layer 0: the features have landed; every layer: the epilogue
+            // has read the accumulator, set it to this layer's bias and (layers
+            // 1-2) written this layer's A operand
             if (layer == 0) {
               if (!mbar_wait_ab(bar(B_XF + s), ph_x[s], abort_flag)) {
                 fail();
@@ -389,13 +409,11 @@ __global__ void __maxnreg__(kMaxRegs)
               }
               ph_x[s] ^= 1u;
             }
-            if (layer > 0 || i0 > 0) {
-              if (!mbar_wait_ab(bar(B_ACT + s), ph_act[s], abort_flag)) {
-                fail();
-                break;
-              }
-              ph_act[s] ^= 1u;
+            if (!mbar_wait_ab(bar(B_ACT + s), ph_act[s], abort_flag)) {
+              fail();
+              break;
             }
+            ph_act[s] ^= 1u;
             fence_after_sync();
             const int K = layer ? HIDDEN : FEATURES;
             // A operand: features with K blocks 2 KB apart and row groups 128 B
@@ -414,7 +432,7 @@ __global__ void __maxnreg__(kMaxRegs)
               for (int j = 0; j < KC / 16; ++j)
                 mma_bf16(d, sdesc(a0 + 2u * lbo_a * (c * (KC / 16) + j), lbo_a, sbo_a),
                          sdesc(s_wst + st * WCH_BYTES + 256u * j, 128u, (KC / 8) * 128u),
-                         idesc_bf16(TM, HIDDEN), (c | j) != 0);
+                         idesc_bf16(TM, HIDDEN), 1u);  // onto the bias
               mma_commit(bar(B_WEMPTY + st));
               issued = true;
             }
@@ -437,13 +455,39 @@ __global__ void __maxnreg__(kMaxRegs)
     const float b4 = params[OFF_B4];
     uint32_t ph_acc[2] = {0u, 0u};
     int y_use[2] = {0, 0};
-    // A operand ready (a hidden layer written, the accumulator read)
+    const int c0 = kPartChunks * part;
+    // this thread's accumulator columns of slot s set to the bias of layer
+    // `layer` (the products then accumulate onto it)
+    auto preload_bias = [&](int s, int layer) {
+      const float *b = s_par + HIDDEN * layer;
+      const uint32_t ta = t_lane + 256u * s;
+#pragma unroll
+      for (int k = 0; k < kPartChunks; ++k) {
+        uint32_t r[32];
+#pragma unroll
+        for (int j = 0; j < 32; j += 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(b + 32 * (c0 + k) + j);
+          r[j] = __float_as_uint(v.x);
+          r[j + 1] = __float_as_uint(v.y);
+          r[j + 2] = __float_as_uint(v.z);
+          r[j + 3] = __float_as_uint(v.w);
+        }
+        tmem_st32(ta + 32u * (c0 + k), r);
+      }
+      tmem_wait_st();
+    };
+    // A operand ready (a hidden layer written, the accumulator read and set
+    // to the next bias)
     auto signal_act = [&](int s) {
       fence_proxy_async();
       fence_before_sync();
       __syncwarp();
       if (lane == 0) mbar_arrive(bar(B_ACT + s));
     };
+    for (int s = 0; s < 2 && s < n_local; ++s) {
+      preload_bias(s, 0);
+      signal_act(s);
+    }
     for (int i0 = 0; i0 < n_local && ok; i0 += 2)
       for (int layer = 0; layer < 3 && ok; ++layer)
         for (int s = 0; s < 2 && ok && i0 + s < n_local; ++s) {
@@ -456,9 +500,9 @@ __global__ void __maxnreg__(kMaxRegs)
           ph_acc[s] ^= 1u;
           fence_after_sync();
           const bool next = layer == 2 && i + 2 < n_local;
-          // ---- bias + GELU -> BF16 (next A operand) or the output ------------
+          // ---- GELU (the bias is in the accumulator) -> BF16 (next A operand)
+          // ---- or the output ----------------------------------------------
           unsigned char *act = sm + s * ACT_BYTES;
-          const float *bias = s_par + HIDDEN * layer;
           const float *w4 = s_par + 3 * HIDDEN;
           float yrow = part ? 0.0f : b4;
           // two chunks of 32 columns; the read of the second is in flight
@@ -467,15 +511,11 @@ __global__ void __maxnreg__(kMaxRegs)
           auto chunk = [&](int cc, const uint32_t (&r)[32]) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-              const float4 bl = *reinterpret_cast<const float4 *>(bias + 32 * cc + 8 * q);
-              const float4 bh = *reinterpret_cast<const float4 *>(bias + 32 * cc + 8 * q + 4);
-              const float bq[8] = {bl.x, bl.y, bl.z, bl.w, bh.x, bh.y, bh.z, bh.w};
               uint32_t w[4];
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                const float2 a = gelu2_twice(__fadd2_rn(make_float2(__uint_as_float(r[8 * q + 2 * e]),
-                                                              __uint_as_float(r[8 * q + 2 * e + 1])),
-                                                  make_float2(bq[2 * e], bq[2 * e + 1])));
+                const float2 a = gelu2_twice(make_float2(__uint_as_float(r[8 * q + 2 * e]),
+                                                         __uint_as_float(r[8 * q + 2 * e + 1])));
                 w[e] = pack_bf16(a.x, a.y);
               }
               if (layer < 2) {
@@ -492,7 +532,6 @@ __global__ void __maxnreg__(kMaxRegs)
               }
             }
           };
-          const int c0 = kPartChunks * part;
           const uint32_t ta = t_lane + 256u * s;
           tmem_ld32(ta + 32u * c0, ra);
           tmem_wait(ra);
@@ -508,6 +547,7 @@ __global__ void __maxnreg__(kMaxRegs)
             }
           }
           if (layer < 2) {
+            preload_bias(s, layer + 1);
             signal_act(s);
             continue;
           }
@@ -537,7 +577,10 @@ __global__ void __maxnreg__(kMaxRegs)
             __syncwarp();
             if (lane == 0) mbar_arrive(bar(B_YEMPTY + s));
           }
-          if (next) signal_act(s);  // the accumulator may take the next tile
+          if (next) {  // the accumulator may take the next tile
+            preload_bias(s, 0);
+            signal_act(s);
+          }
         }
   }
   // ---- teardown: copies and products in flight have finished; free TMEM ---
