@@ -596,15 +596,14 @@ __global__ void __maxnreg__(kMaxRegs)
 // Training products on tcgen05: C[M][256] = A[M][K] Bt[256][K]^T.
 // CTA (blockIdx.x, split blockIdx.y, column quarter blockIdx.z) computes rows
 // m0 .. m0 + 127 and columns 64 z .. + 63 over its K range in chunks of 64
-// (four quarters per row block give a 4,096-row batch 128 CTAs): the 256
-// threads move a chunk of A (128 x 64) and of Bt (its 64 rows x 64) from
-// global memory into one of two stages in the K-major core-matrix layout (a
-// warp stores eight rows x 16 bytes of one K block per 128-byte step), one
-// thread issues four MMAs (M 128, N 64, K 16) into the 64-column FP32
-// accumulator and commits them to the stage's mbarrier, and the next
-// chunk's global loads are in flight meanwhile. The epilogue reads the
-// accumulator with tcgen05.ld: warp w takes lanes 32 (w mod 4) .. + 31 and
-// columns 32 (w / 4) .. + 31. Every mbarrier wait is bounded as in the
+// (four quarters per row block give a 4,096-row batch 128 CTAs): one thread
+// streams the chunks of A (128 x 64) and Bt (its 64 rows x 64) by 2-D tensor
+// copies into a ring of four stages and issues four MMAs (M 128, N 64, K 16)
+// per chunk into the 64-column FP32 accumulator, committing each chunk to its
+// stage's "empty" mbarrier, after which the stage takes the chunk four ahead.
+// The epilogue reads the accumulator with tcgen05.ld: warp w takes lanes
+// 32 (w mod 4) .. + 31 and columns 32 (w / 4) .. + 31. Every mbarrier wait
+// is bounded as in the
 // forward kernel; a timeout sets *err and the CTA writes nothing.
 // ---------------------------------------------------------------------------
 // The transposed copy c16t[c][r] (row stride ldt) of a thread's 32 BF16
@@ -624,28 +623,29 @@ constexpr int GK = 64;                     // K per chunk
 constexpr int GA_BYTES = 128 * GK * 2;     // A chunk: 16 KB
 constexpr int GN = 64;                     // columns per CTA (4 CTAs across 256 columns)
 constexpr int GB_BYTES = GN * GK * 2;      // Bt chunk: 8 KB
-constexpr int GB_STEPS = GN / 32;          // 16-byte pieces of the Bt chunk per thread
 constexpr int G_STAGE = GA_BYTES + GB_BYTES;
-constexpr int G_SMEM = 2 * G_STAGE + 64;
+constexpr int G_STAGES = 4;                // chunks in flight
+constexpr int G_SMEM = G_STAGES * G_STAGE + 128;
 constexpr int G_THREADS = 256;
 
 template <int EPI>
-__global__ void __launch_bounds__(G_THREADS, 4)
-    tc_gemm_kernel(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb, int k_split,
-                   Epilogue ep, int *err) {
+__global__ void __launch_bounds__(G_THREADS, 2)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tma, const __grid_constant__ CUtensorMap tmb,
+                   int k_split, Epilogue ep, int *err) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + 2 * G_STAGE);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+  // mbarriers: stage full [G_STAGES], stage empty [G_STAGES], products done
+  uint64_t *bars = reinterpret_cast<uint64_t *>(sm + G_STAGES * G_STAGE);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2 * G_STAGES + 1);
+  int *s_ok = reinterpret_cast<int *>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t m0 = (int64_t)blockIdx.x * 128;
-  const int64_t k0 = (int64_t)blockIdx.y * k_split;
+  const int k0 = blockIdx.y * k_split;
   const int n0 = GN * blockIdx.z;
-  Bt += (int64_t)n0 * ldb;
   const int nc = k_split / GK;
-  const uint32_t bar[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
+  auto bar = [&](int i) { return smem_u32(&bars[i]); };
+  const int B_FULL = 0, B_EMPTY = G_STAGES, B_DONE = 2 * G_STAGES;
   if (tid == 0) {
-    mbar_init(bar[0], 1);
-    mbar_init(bar[1], 1);
+    for (int i = 0; i < 2 * G_STAGES + 1; ++i) mbar_init(bar(i), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -658,72 +658,62 @@ __global__ void __launch_bounds__(G_THREADS, 4)
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tslot;
-  // a chunk in 16-byte pieces: step v of a warp covers rows 8 (v mod G) + (lane
-  // mod 8) and K block 4 (v / G) + lane / 8 (G = row groups of the operand)
-  uint4 ra[4], rb[GB_STEPS];
-  auto load = [&](int c) {
-    const int64_t kk = k0 + (int64_t)c * GK;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int v = warp + 8 * i, row = 8 * (v & 15) + (lane & 7), kb = 4 * (v >> 4) + (lane >> 3);
-      ra[i] = __ldg(reinterpret_cast<const uint4 *>(A + (m0 + row) * lda + kk + 8 * kb));
-    }
-#pragma unroll
-    for (int i = 0; i < GB_STEPS; ++i) {
-      const int v = warp + 8 * i, row = 8 * (v % (GN / 8)) + (lane & 7),
-                kb = 4 * (v / (GN / 8)) + (lane >> 3);
-      rb[i] = __ldg(reinterpret_cast<const uint4 *>(Bt + (int64_t)row * ldb + kk + 8 * kb));
-    }
-  };
-  auto store = [&](int st) {
-    unsigned char *sa = sm + st * G_STAGE, *sb = sa + GA_BYTES;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int v = warp + 8 * i, row = 8 * (v & 15) + (lane & 7), kb = 4 * (v >> 4) + (lane >> 3);
-      *reinterpret_cast<uint4 *>(sa + canon_off(row, 8 * kb, GK)) = ra[i];
-    }
-#pragma unroll
-    for (int i = 0; i < GB_STEPS; ++i) {
-      const int v = warp + 8 * i, row = 8 * (v % (GN / 8)) + (lane & 7),
-                kb = 4 * (v / (GN / 8)) + (lane >> 3);
-      *reinterpret_cast<uint4 *>(sb + canon_off(row, 8 * kb, GK)) = rb[i];
-    }
-  };
-  uint32_t ph[2] = {0u, 0u};
-  bool pending[2] = {false, false};
   bool ok = nc > 0;
-  if (ok) load(0);
-  for (int c = 0; c < nc && ok; ++c) {
-    const int st = c & 1;
-    if (pending[st]) {  // the products of chunk c - 2 have read this stage
-      ok = __syncthreads_and(mbar_wait(bar[st], ph[st]));
-      if (!ok) break;
-      pending[st] = false;
-      ph[st] ^= 1u;
-    }
-    store(st);
-    fence_proxy_async();
-    __syncthreads();
-    if (c + 1 < nc) load(c + 1);
-    if (tid == 0) {
+  if (tid == 0) {
+    // One thread streams the chunks (tensor copies: a box of 8 K values x the
+    // operand's rows per K block, which lands as the core-matrix layout with
+    // K blocks 2 KB (A) or 1 KB (Bt) apart and row groups 128 B apart) and
+    // issues the products; a stage is refilled once its products are done.
+    auto load = [&](int c) {
+      const int st = c % G_STAGES;
+      const uint32_t sa = smem_u32(sm + st * G_STAGE), sb = sa + GA_BYTES;
+      const int kk = k0 + c * GK;
+      mbar_expect_tx(bar(B_FULL + st), G_STAGE);
+#pragma unroll
+      for (int kb = 0; kb < GK / 8; ++kb) {
+        tma_load_2d(sa + kb * (128 * 16), &tma, kk + 8 * kb, (int)m0, bar(B_FULL + st));
+        tma_load_2d(sb + kb * (GN * 16), &tmb, kk + 8 * kb, n0, bar(B_FULL + st));
+      }
+    };
+    int loaded = 0, used = 0;
+    for (; ok && loaded < nc && loaded < G_STAGES; ++loaded) load(loaded);
+    for (int c = 0; c < nc && ok; ++c) {
+      const int st = c % G_STAGES;
+      if (!mbar_wait(bar(B_FULL + st), (uint32_t)(c / G_STAGES) & 1u)) {
+        ok = false;
+        break;
+      }
+      used = c + 1;
       fence_after_sync();
       const uint32_t sa = smem_u32(sm + st * G_STAGE), sb = sa + GA_BYTES;
 #pragma unroll
       for (int q = 0; q < GK / 16; ++q)
-        mma_bf16(tmem, sdesc(sa + 256u * q, 128u, GK * 16), sdesc(sb + 256u * q, 128u, GK * 16),
-                 idesc_bf16(128, GN), (c > 0 || q > 0) ? 1u : 0u);
-      mma_commit(bar[st]);
+        mma_bf16(tmem, sdesc(sa + 2u * (128 * 16) * q, 128u * 16, 128u),
+                 sdesc(sb + 2u * (GN * 16) * q, GN * 16u, 128u), idesc_bf16(128, GN),
+                 (c > 0 || q > 0) ? 1u : 0u);
+      mma_commit(bar(B_EMPTY + st));
+      // refill the stage of chunk c - 1 once its products are done
+      if (c >= 1 && loaded < nc) {
+        const int pc = c - 1;
+        if (!mbar_wait(bar(B_EMPTY + pc % G_STAGES), (uint32_t)(pc / G_STAGES) & 1u)) {
+          ok = false;
+          break;
+        }
+        load(loaded++);
+      }
     }
-    pending[st] = true;
-  }
-  if (ok) {  // the last commit covers every product before it
-    const int st = (nc - 1) & 1;
-    ok = __syncthreads_and(mbar_wait(bar[st], ph[st]));
-    if (ok) {
-      pending[0] = pending[1] = false;
-      ph[st] ^= 1u;
+    // the products issued so far, then the copies not consumed, finish
+    if (used > 0) mma_commit(bar(B_DONE));
+    if (!ok) {
+      if (used > 0) mbar_wait(bar(B_DONE), 0u);
+      for (int c = used; c < loaded; ++c)
+        mbar_wait(bar(B_FULL + c % G_STAGES), (uint32_t)(c / G_STAGES) & 1u);
     }
+    *s_ok = ok ? 1 : 0;
   }
+  __syncthreads();
+  ok = *s_ok != 0;
+  if (ok) ok = __syncthreads_and(mbar_wait(bar(B_DONE), 0u));
   if (ok) {
     fence_after_sync();
     const int quad = warp & 3, half = warp >> 2;
@@ -776,9 +766,7 @@ __global__ void __launch_bounds__(G_THREADS, 4)
       }
     }
   }
-  // ---- teardown: products in flight finish, then the tensor memory is freed
-  for (int st = 0; st < 2; ++st)
-    if (pending[st]) mbar_wait(bar[st], ph[st]);
+  // ---- teardown (the producing thread has waited for its work in flight) ---
   if (!ok && tid == 0 && nc > 0) atomicExch(err, 1);
   fence_before_sync();
   __syncthreads();
@@ -915,8 +903,26 @@ static cudaError_t tc_gemm_launch(const __nv_bfloat16 *A, int lda, const __nv_bf
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
+  // A [M][K] and Bt [256][K] (row strides lda, ldb) as 2-D tensors; a box is
+  // 8 K values x 128 (A) or 64 (Bt) rows
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(A) & 15u) || (reinterpret_cast<uintptr_t>(Bt) & 15u))
+    return cudaErrorInvalidValue;
+  const cuuint64_t K = (cuuint64_t)k_split * splits;
+  CUtensorMap ma, mb;
+  const cuuint64_t da[2] = {K, (cuuint64_t)M}, db[2] = {K, (cuuint64_t)HIDDEN};
+  const cuuint64_t sa[1] = {(cuuint64_t)lda * 2}, sb[1] = {(cuuint64_t)ldb * 2};
+  const cuuint32_t ba[2] = {8u, 128u}, bb[2] = {8u, (cuuint32_t)GN}, es[2] = {1u, 1u};
+  if (enc(&ma, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(A), da, sa, ba, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&mb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16 *>(Bt), db, sb, bb, es,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   tc_gemm_kernel<EPI><<<dim3(M / 128, splits, HIDDEN / GN), G_THREADS, G_SMEM, s>>>(
-      A, lda, Bt, ldb, k_split, ep, err);
+      ma, mb, k_split, ep, err);
   return cudaGetLastError();
 }
 
