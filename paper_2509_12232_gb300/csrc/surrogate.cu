@@ -176,10 +176,12 @@ struct dock_surrogate {
   int *d_step = nullptr;
   cudaStream_t ts = nullptr;  // training runs (and its step graph is captured) on this stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  // the backward pass's weight gradients (ts_w) and bias gradients (ts_c) run
+  // the backward pass's weight gradients (ts_w[l], one stream per layer, each
+  // with its own split-K scratch) and bias gradients (ts_c) run
   // beside its chain of input gradients, forked and joined by events
-  cudaStream_t ts_w = nullptr, ts_c = nullptr;
-  cudaEvent_t ev_dz[3] = {nullptr, nullptr, nullptr}, ev_w = nullptr, ev_c = nullptr;
+  cudaStream_t ts_w[3] = {nullptr, nullptr, nullptr}, ts_c = nullptr;
+  cudaEvent_t ev_dz[3] = {nullptr, nullptr, nullptr}, ev_w[3] = {nullptr, nullptr, nullptr},
+              ev_c = nullptr;
   float *cpart = nullptr;  // column-sum partials of the bias gradients
   float t_mean = 0.0f, t_std = 1.0f, t_clip = 1e30f;
   // weights of the fused tensor-core forward pass (refreshed lazily after the
@@ -187,7 +189,7 @@ struct dock_surrogate {
   __nv_bfloat16 *wc = nullptr;
   bool wc_valid = false;
   int *err = nullptr;
-  float *wpart = nullptr;  // split-K partial weight gradients, column-sum partials
+  float *wpart = nullptr;  // split-K partial weight gradients, one region per layer
   ~dock_surrogate() {
     for (float *q : {p, m, v, g, y, t, part, outg}) if (q) cudaFree(q);
     if (wc) cudaFree(wc);
@@ -197,9 +199,10 @@ struct dock_surrogate {
     if (d_step) cudaFree(d_step);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
-    for (cudaEvent_t e : {ev_dz[0], ev_dz[1], ev_dz[2], ev_w, ev_c}) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : {ev_dz[0], ev_dz[1], ev_dz[2], ev_w[0], ev_w[1], ev_w[2], ev_c})
+      if (e) cudaEventDestroy(e);
     if (ts) cudaStreamDestroy(ts);
-    if (ts_w) cudaStreamDestroy(ts_w);
+    for (cudaStream_t q : {ts_w[0], ts_w[1], ts_w[2]}) if (q) cudaStreamDestroy(q);
     if (ts_c) cudaStreamDestroy(ts_c);
     if (cpart) cudaFree(cpart);
     for (int l = 0; l < 3; ++l) {
@@ -224,7 +227,9 @@ static const int kIn[3] = {FEATURES, HIDDEN, HIDDEN};
 static const int kOffW[3] = {mlp::OFF_W1, mlp::OFF_W2, mlp::OFF_W3};
 static const int kOffB[3] = {mlp::OFF_B1, mlp::OFF_B2, mlp::OFF_B3};
 static const int kBwdBlocks = 512;
-static const int64_t kWpartElems = 32 * HIDDEN * HIDDEN;  // 32 K splits of a 256 x 256 gradient
+// split-K partials of one layer's weight gradient: 16 splits of 256 x 256 or
+// 32 of 128 x 256 (128 CTAs per product); one region per layer
+static const int64_t kWpartElems = 16 * HIDDEN * HIDDEN;
 
 static int ensure_workspace(dock_surrogate *S, int rows) {
   if (rows <= S->cap) return DOCK_OK;
@@ -298,7 +303,7 @@ static int forward(dock_surrogate *S, int rows, bool keep, cudaStream_t s) {
 // Gradients of loss = mean over the first n rows of (y - t)^2 into S->g
 // (rows >= n padded: contribute nothing). Needs forward(keep = true). The
 // chain dZ_2 -> dZ_1 -> dZ_0 runs on s; each layer's weight gradient (on
-// ts_w) and bias gradient (on ts_c) start once its dZ is written, and s waits
+// ts_w[l]) and bias gradient (on ts_c) start once its dZ is written, and s waits
 // for both before it returns (also inside a captured step graph).
 static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
   SCU(mlp::out_layer_bwd(S->y, S->t, n, rows, S->H[2], S->Z[2], S->p + mlp::OFF_W4, S->dZ[2],
@@ -307,16 +312,16 @@ static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
                       cudaMemcpyDeviceToDevice, s));
   for (int l = 2; l >= 0; --l) {
     SCU(cudaEventRecord(S->ev_dz[l], s));
-    SCU(cudaStreamWaitEvent(S->ts_w, S->ev_dz[l], 0));
+    SCU(cudaStreamWaitEvent(S->ts_w[l], S->ev_dz[l], 0));
     SCU(cudaStreamWaitEvent(S->ts_c, S->ev_dz[l], 0));
     // dW_l = act_in^T dZ_l (tensor cores, K = rows split over CTAs) from
     // K-major copies: H_{l-1}^T and dZ_l^T from the epilogues, X^T and dZ_2^T
     // transposed here
     const __nv_bfloat16 *at = l ? S->Ht[l - 1] : S->at, *bt = l < 2 ? S->dZt[l] : S->bt;
-    if (l == 0) SCU(mlp::transpose_bf16(S->X, rows, FEATURES, S->at, S->ts_w));
-    if (l == 2) SCU(mlp::transpose_bf16(S->dZ[2], rows, HIDDEN, S->bt, S->ts_w));
-    SCU(mlp::tc_gemm_tt_f32(at, bt, kIn[l], rows, S->g + kOffW[l], S->wpart, kWpartElems, S->err,
-                            S->ts_w));
+    if (l == 0) SCU(mlp::transpose_bf16(S->X, rows, FEATURES, S->at, S->ts_w[0]));
+    if (l == 2) SCU(mlp::transpose_bf16(S->dZ[2], rows, HIDDEN, S->bt, S->ts_w[2]));
+    SCU(mlp::tc_gemm_tt_f32(at, bt, kIn[l], rows, S->g + kOffW[l], S->wpart + l * kWpartElems,
+                            kWpartElems, S->err, S->ts_w[l]));
     // db_l = column sums of dZ_l
     SCU(mlp::colsum(S->dZ[l], rows, HIDDEN, S->g + kOffB[l], S->cpart, S->ts_c));
     if (l) {
@@ -331,9 +336,9 @@ static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
                           ep, S->err, s));
     }
   }
-  SCU(cudaEventRecord(S->ev_w, S->ts_w));
+  for (int l = 0; l < 3; ++l) SCU(cudaEventRecord(S->ev_w[l], S->ts_w[l]));
   SCU(cudaEventRecord(S->ev_c, S->ts_c));
-  SCU(cudaStreamWaitEvent(s, S->ev_w, 0));
+  for (int l = 0; l < 3; ++l) SCU(cudaStreamWaitEvent(s, S->ev_w[l], 0));
   SCU(cudaStreamWaitEvent(s, S->ev_c, 0));
   return DOCK_OK;
 }
@@ -366,13 +371,14 @@ extern "C" int dock_surrogate_create(uint64_t seed, void *stream, dock_surrogate
     SCU(cudaMalloc(&S->wt16[l], sizeof(__nv_bfloat16) * kIn[l] * HIDDEN));
   }
   SCU(cudaMalloc(&S->wc, sizeof(__nv_bfloat16) * mlp::canon_weight_elems()));
-  SCU(cudaMalloc(&S->wpart, sizeof(float) * kWpartElems));
+  SCU(cudaMalloc(&S->wpart, sizeof(float) * 3 * kWpartElems));
   SCU(cudaMalloc(&S->err, sizeof(int)));
   SCU(cudaMalloc(&S->d_r0, sizeof(int64_t)));
   SCU(cudaStreamCreateWithFlags(&S->ts, cudaStreamNonBlocking));
-  SCU(cudaStreamCreateWithFlags(&S->ts_w, cudaStreamNonBlocking));
+  for (int l = 0; l < 3; ++l) SCU(cudaStreamCreateWithFlags(&S->ts_w[l], cudaStreamNonBlocking));
   SCU(cudaStreamCreateWithFlags(&S->ts_c, cudaStreamNonBlocking));
-  for (cudaEvent_t *e : {&S->ev_dz[0], &S->ev_dz[1], &S->ev_dz[2], &S->ev_w, &S->ev_c})
+  for (cudaEvent_t *e : {&S->ev_dz[0], &S->ev_dz[1], &S->ev_dz[2], &S->ev_w[0], &S->ev_w[1],
+                         &S->ev_w[2], &S->ev_c})
     SCU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   SCU(cudaMalloc(&S->cpart, sizeof(float) * mlp::kColsumChunks * HIDDEN));
   SCU(cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
