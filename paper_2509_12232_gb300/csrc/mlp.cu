@@ -1,7 +1,8 @@
 // Non-GEMM kernels of the candidate-pose surrogate MLP (128 -> 256 -> 256 ->
-// 256 -> 1, GELU in erf form, BF16 weights and activations, FP32 master
-// weights): the 256 -> 1 output layer and its backward pass, column sums for
-// the bias gradients, the Adam step and the BF16 weight copies. The dense
+// 256 -> 1, GELU in tanh form, BF16 weights and activations, FP32 master
+// weights): the 256 -> 1 output layer's backward pass (its forward is part of
+// the last training product's epilogue), column sums for the bias gradients,
+// the Adam step and the BF16 weight copies. The dense
 // products of training and prediction run on the 5th-generation tensor cores
 // (mlp_tc.cu).
 #include <cuda_bf16.h>
@@ -16,28 +17,22 @@ namespace {
 
 __device__ __forceinline__ float gelu_d(float z) { return gelu_t_grad(z); }
 
-// y[m] = b + sum_j H[m][j] w[j] (the 256 -> 1 output layer; one warp per row).
-__global__ void out_layer_kernel(const __nv_bfloat16 *H, const float *w, const float *b, int rows,
-                                 float *y) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= rows) return;
-  const __nv_bfloat16 *h = H + (int64_t)warp * HIDDEN;
-  float s = 0.0f;
-#pragma unroll
-  for (int j = lane; j < HIDDEN; j += 32) s += __bfloat162float(h[j]) * w[j];
-  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (lane == 0) y[warp] = s + b[0];
-}
-
-// Output-layer backward: dy = 2 (y - t) / n (rows >= n: 0); dZ3 = dy w4 gelu'(Z3) (BF16);
+// Output-layer backward: y = b4 + the partial dot products (g = 0..7 in
+// order); dy = 2 (y - t) / n (rows >= n: 0); dZ3 = dy w4 gelu'(Z3) (BF16);
 // per-block partial sums of dW4 (H3^T dy), db4 and the loss.
-__global__ void out_layer_bwd_kernel(const float *y, const float *t, int n, int rows,
-                                     const __nv_bfloat16 *H3, const float *Z3, const float *w4,
-                                     __nv_bfloat16 *dZ3, float *part /* [blocks][HIDDEN + 2] */) {
+__global__ void out_layer_bwd_kernel(float *y, const float *ydot, const float *b4, const float *t,
+                                     int n, int rows, const __nv_bfloat16 *H3, const float *Z3,
+                                     const float *w4, __nv_bfloat16 *dZ3,
+                                     float *part /* [blocks][HIDDEN + 2] */) {
   const int j = threadIdx.x;  // blockDim == HIDDEN
   float dw = 0.0f, db = 0.0f, ls = 0.0f;
   for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-    const float e = r < n ? y[r] - t[r] : 0.0f;
+    float sum = ydot[r];
+#pragma unroll
+    for (int g = 1; g < 8; ++g) sum += ydot[(int64_t)g * rows + r];
+    const float yr = b4[0] + sum;
+    if (j == 0) y[r] = yr;
+    const float e = r < n ? yr - t[r] : 0.0f;
     const float dy = 2.0f * e / (float)n;
     const int64_t o = (int64_t)r * HIDDEN + j;
     dw += __bfloat162float(H3[o]) * dy;
@@ -67,16 +62,21 @@ __global__ void colsum_part_kernel(const __nv_bfloat16 *X, int rows, int cols, i
   }
 }
 
-// out[c] = sum over b of part[b][c], one warp per column: lane l adds parts
-// l, l + 32, ... in order, then a fixed shuffle tree (the same sum every run).
-__global__ void reduce_cols_kernel(const float *part, int blocks, int width, float *out) {
+// sum over b of part[b][c], one warp per column: lane l adds parts l, l + 32,
+// ... in order, then a fixed shuffle tree (the same sum every run); columns
+// c < split go to out[c], the others to out2[c - split].
+__global__ void reduce_cols_kernel(const float *part, int blocks, int width, float *out, int split,
+                                   float *out2) {
   const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (c >= width) return;
   float s = 0.0f;
   for (int b = lane; b < blocks; b += 32) s += part[(int64_t)b * width + c];
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-  if (lane == 0) out[c] = s;
+  if (lane == 0) {
+    if (c < split) out[c] = s;
+    else out2[c - split] = s;
+  }
 }
 
 // Adam on FP32 masters (Kingma & Ba 2015): m = b1 m + (1-b1) g; v = b2 v +
@@ -85,10 +85,9 @@ __global__ void reduce_cols_kernel(const float *part, int blocks, int width, flo
 // else step.
 // With copies (training): the updated W1..W3 are also written as their BF16
 // copies w16 [in][out] and wt16 [out][in] (what cast_weights_kernel makes).
-__global__ void adam_kernel(float *p, float *m, float *v, const float *g, int n, float lr, float b1,
-                            float b2, float eps, int step, const int *step_dev, WeightCopies wc) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void adam_one(float *p, float *m, float *v, const float *g, int i,
+                                         float lr, float b1, float b2, float eps, int step,
+                                         const int *step_dev, const WeightCopies &wc) {
   const float t = (float)(step_dev ? *step_dev : step);
   const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
   const float gi = g[i];
@@ -113,6 +112,25 @@ __global__ void adam_kernel(float *p, float *m, float *v, const float *g, int n,
   wc.wt16[l][(int64_t)(e % HIDDEN) * in + e / HIDDEN] = b;
 }
 
+__global__ void adam_kernel(float *p, float *m, float *v, const float *g, int n, float lr, float b1,
+                            float b2, float eps, int step, int *step_dev, WeightCopies wc,
+                            int64_t *r0_dev, int64_t batch, unsigned *ticket) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) adam_one(p, m, v, g, i, lr, b1, b2, eps, step, step_dev, wc);
+  if (r0_dev == nullptr) return;
+  // the last block to finish (every block has read the step) advances the counters
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(ticket, 1u) == gridDim.x - 1) {
+      *r0_dev += batch;
+      *step_dev += 1;
+      *ticket = 0u;
+      __threadfence();
+    }
+  }
+}
+
 // BF16 copies of a weight matrix W [in][out]: w16 (same layout) and wt16 [out][in].
 __global__ void cast_weights_kernel(const float *W, int in, int out, __nv_bfloat16 *w16,
                                     __nv_bfloat16 *wt16) {
@@ -125,18 +143,13 @@ __global__ void cast_weights_kernel(const float *W, int in, int out, __nv_bfloat
 }
 }  // namespace
 
-cudaError_t out_layer(const __nv_bfloat16 *H, const float *w, const float *b, int rows, float *y,
-                      cudaStream_t s) {
-  if (rows <= 0) return cudaSuccess;
-  out_layer_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(H, w, b, rows, y);
-  return cudaGetLastError();
-}
-
-cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const __nv_bfloat16 *H3,
-                          const float *Z3, const float *w4, __nv_bfloat16 *dZ3, float *part,
-                          int blocks, float *out /* [HIDDEN + 2] */, cudaStream_t s) {
-  out_layer_bwd_kernel<<<blocks, HIDDEN, 0, s>>>(y, t, n, rows, H3, Z3, w4, dZ3, part);
-  reduce_cols_kernel<<<(HIDDEN + 2 + 7) / 8, 256, 0, s>>>(part, blocks, HIDDEN + 2, out);
+cudaError_t out_layer_bwd(float *y, const float *ydot, const float *b4, const float *t, int n,
+                          int rows, const __nv_bfloat16 *H3, const float *Z3, const float *w4,
+                          __nv_bfloat16 *dZ3, float *part, int blocks, float *grad, float *loss,
+                          cudaStream_t s) {
+  out_layer_bwd_kernel<<<blocks, HIDDEN, 0, s>>>(y, ydot, b4, t, n, rows, H3, Z3, w4, dZ3, part);
+  reduce_cols_kernel<<<(HIDDEN + 2 + 7) / 8, 256, 0, s>>>(part, blocks, HIDDEN + 2, grad,
+                                                          HIDDEN + 1, loss);
   return cudaGetLastError();
 }
 
@@ -146,14 +159,17 @@ cudaError_t colsum(const __nv_bfloat16 *X, int rows, int cols, float *out, float
   const int chunks = rows < kColsumChunks ? rows : kColsumChunks;
   const int chunk_rows = (rows + chunks - 1) / chunks;
   colsum_part_kernel<<<chunks, 256, 0, s>>>(X, rows, cols, chunk_rows, scratch);
-  reduce_cols_kernel<<<(cols + 7) / 8, 256, 0, s>>>(scratch, chunks, cols, out);
+  reduce_cols_kernel<<<(cols + 7) / 8, 256, 0, s>>>(scratch, chunks, cols, out, cols, nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t adam(float *p, float *m, float *v, const float *g, int n, float lr, int step,
-                 const int *step_dev, const WeightCopies *copies, cudaStream_t s) {
+                 int *step_dev, const WeightCopies *copies, int64_t *r0_dev, int64_t batch,
+                 unsigned *ticket, cudaStream_t s) {
+  if (r0_dev && (!step_dev || !ticket)) return cudaErrorInvalidValue;
   adam_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, m, v, g, n, lr, 0.9f, 0.999f, 1e-8f, step,
-                                              step_dev, copies ? *copies : WeightCopies{});
+                                              step_dev, copies ? *copies : WeightCopies{}, r0_dev,
+                                              batch, ticket);
   return cudaGetLastError();
 }
 

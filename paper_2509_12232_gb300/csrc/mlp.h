@@ -62,13 +62,21 @@ struct Epilogue {
   int64_t split_stride;     // STORE with split K: elements between the splits' partial outputs
   __nv_bfloat16 *c16t;      // BIAS_GELU / GELU_BWD, or null: c16 transposed, [col][row]
   int64_t ldt;              // row stride of c16t (elements)
+  // BIAS_GELU, or null: ydot[g][row] = sum over the 32 columns of group g of the
+  // BF16 activation times w4 (the output layer's partial dot products, g < 8)
+  float *ydot;
+  const float *w4;
+  int64_t ldy;
 };
 
-cudaError_t out_layer(const __nv_bfloat16 *H, const float *w, const float *b, int rows, float *y,
-                      cudaStream_t s);
-cudaError_t out_layer_bwd(const float *y, const float *t, int n, int rows, const __nv_bfloat16 *H3,
-                          const float *Z3, const float *w4, __nv_bfloat16 *dZ3, float *part,
-                          int blocks, float *out, cudaStream_t s);
+// Output-layer backward. y = b4 + the eight partial dot products ydot[g][row]
+// (summed in order g = 0..7; y is written); dy = 2 (y - t) / n; dZ3 = dy w4
+// gelu'(Z3); dW4, db4 into grad[0..256] and the summed squared error into
+// *loss (fixed-order reductions over `blocks` partials in part).
+cudaError_t out_layer_bwd(float *y, const float *ydot, const float *b4, const float *t, int n,
+                          int rows, const __nv_bfloat16 *H3, const float *Z3, const float *w4,
+                          __nv_bfloat16 *dZ3, float *part, int blocks, float *grad, float *loss,
+                          cudaStream_t s);
 // out[c] = sum over rows of X[r][c]: kColsumChunks row chunks in parallel, then a
 // fixed-order sum (scratch: at least kColsumChunks * cols floats).
 constexpr int kColsumChunks = 128;
@@ -81,8 +89,11 @@ struct WeightCopies {
 };
 // Adam step t = *step_dev if step_dev is given (read on the device), else step;
 // with copies, the updated W1..W3 are also written to them (one kernel).
+// With counters (r0_dev, batch), the last block to finish also advances the
+// batch start and the step (the form replayed in the training graph).
 cudaError_t adam(float *p, float *m, float *v, const float *g, int n, float lr, int step,
-                 const int *step_dev, const WeightCopies *copies, cudaStream_t s);
+                 int *step_dev, const WeightCopies *copies, int64_t *r0_dev, int64_t batch,
+                 unsigned *ticket, cudaStream_t s);
 cudaError_t cast_weights(const float *W, int in, int out, __nv_bfloat16 *w16, __nv_bfloat16 *wt16,
                          cudaStream_t s);
 

@@ -748,6 +748,16 @@ __global__ void __launch_bounds__(G_THREADS, 2)
 #pragma unroll
         for (int j = 0; j < 4; ++j) dst[j] = make_uint4(h[4 * j], h[4 * j + 1], h[4 * j + 2], h[4 * j + 3]);
         store_transposed(ep, h, row, col);
+        if (ep.ydot) {  // the output layer's partial dot product over these 32 columns
+          float d = 0.0f;
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            const __nv_bfloat162 hv = *reinterpret_cast<const __nv_bfloat162 *>(&h[k]);
+            d = fmaf(__low2float(hv), __ldg(ep.w4 + col + 2 * k), d);
+            d = fmaf(__high2float(hv), __ldg(ep.w4 + col + 2 * k + 1), d);
+          }
+          ep.ydot[(int64_t)(col >> 5) * ep.ldy + row] = d;
+        }
       } else {  // EPI_GELU_BWD: dZ = dH gelu'(Z)
         uint32_t h[16];
         const float4 *zin = reinterpret_cast<const float4 *>(ep.zin + o);

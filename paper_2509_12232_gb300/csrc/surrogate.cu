@@ -119,10 +119,6 @@ __global__ void set_counters_kernel(int64_t *r0, int64_t r0_value, int *step, in
   *r0 = r0_value;
   *step = step_value;
 }
-__global__ void advance_counters_kernel(int64_t *r0, int64_t batch, int *step) {
-  *r0 += batch;
-  *step += 1;
-}
 
 // mean and sum of squares of min(t, clip) (double accumulation, one block)
 __global__ void target_stats_kernel(const float *t, int64_t n, float clip, double *out) {
@@ -190,11 +186,15 @@ struct dock_surrogate {
   bool wc_valid = false;
   int *err = nullptr;
   float *wpart = nullptr;  // split-K partial weight gradients, one region per layer
+  float *ydot = nullptr;   // the output layer's partial dot products [8][rows]
+  unsigned *ticket = nullptr;  // blocks of a replayed step's Adam kernel that are done
   ~dock_surrogate() {
     for (float *q : {p, m, v, g, y, t, part, outg}) if (q) cudaFree(q);
     if (wc) cudaFree(wc);
     if (err) cudaFree(err);
     if (wpart) cudaFree(wpart);
+    if (ydot) cudaFree(ydot);
+    if (ticket) cudaFree(ticket);
     if (d_r0) cudaFree(d_r0);
     if (d_step) cudaFree(d_step);
     if (ev_in) cudaEventDestroy(ev_in);
@@ -249,7 +249,7 @@ static int ensure_workspace(dock_surrogate *S, int rows) {
     S->H[l] = S->dZ[l] = nullptr;
     S->Z[l] = nullptr;
   }
-  for (float **q : {&S->y, &S->t}) {
+  for (float **q : {&S->y, &S->t, &S->ydot}) {
     if (*q) cudaFree(*q);
     *q = nullptr;
   }
@@ -267,6 +267,7 @@ static int ensure_workspace(dock_surrogate *S, int rows) {
     SCU(cudaMalloc(&S->Z[l], sizeof(float) * (size_t)rows * HIDDEN));
   }
   SCU(cudaMalloc(&S->y, sizeof(float) * rows));
+  SCU(cudaMalloc(&S->ydot, sizeof(float) * 8 * (size_t)rows));
   SCU(cudaMalloc(&S->t, sizeof(float) * rows));
   S->cap = rows;
   return DOCK_OK;
@@ -290,13 +291,17 @@ static int forward(dock_surrogate *S, int rows, bool keep, cudaStream_t s) {
     ep.c16 = S->H[l];
     ep.c16t = keep && l < 2 ? S->Ht[l] : nullptr;  // the next layer's weight gradient reads H_l^T
     ep.ldt = rows;
+    if (l == 2) {  // the output layer as eight partial dot products per row
+      ep.ydot = S->ydot;
+      ep.w4 = S->p + mlp::OFF_W4;
+      ep.ldy = rows;
+    }
     ep.bias = S->p + kOffB[l];
     ep.ldc = HIDDEN;
     SCU(mlp::tc_gemm_nt(in, kIn[l], S->wt16[l], kIn[l], rows, kIn[l], mlp::EPI_BIAS_GELU, ep,
                         S->err, s));
     in = S->H[l];
   }
-  SCU(mlp::out_layer(S->H[2], S->p + mlp::OFF_W4, S->p + mlp::OFF_B4, rows, S->y, s));
   return DOCK_OK;
 }
 
@@ -306,10 +311,10 @@ static int forward(dock_surrogate *S, int rows, bool keep, cudaStream_t s) {
 // ts_w[l]) and bias gradient (on ts_c) start once its dZ is written, and s waits
 // for both before it returns (also inside a captured step graph).
 static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
-  SCU(mlp::out_layer_bwd(S->y, S->t, n, rows, S->H[2], S->Z[2], S->p + mlp::OFF_W4, S->dZ[2],
-                         S->part, kBwdBlocks, S->outg, s));
-  SCU(cudaMemcpyAsync(S->g + mlp::OFF_W4, S->outg, sizeof(float) * (HIDDEN + 1),
-                      cudaMemcpyDeviceToDevice, s));
+  // dW4 and db4 straight into the gradient, the loss into outg[HIDDEN + 1]
+  SCU(mlp::out_layer_bwd(S->y, S->ydot, S->p + mlp::OFF_B4, S->t, n, rows, S->H[2], S->Z[2],
+                         S->p + mlp::OFF_W4, S->dZ[2], S->part, kBwdBlocks, S->g + mlp::OFF_W4,
+                         S->outg + HIDDEN + 1, s));
   for (int l = 2; l >= 0; --l) {
     SCU(cudaEventRecord(S->ev_dz[l], s));
     SCU(cudaStreamWaitEvent(S->ts_w[l], S->ev_dz[l], 0));
@@ -372,6 +377,8 @@ extern "C" int dock_surrogate_create(uint64_t seed, void *stream, dock_surrogate
   }
   SCU(cudaMalloc(&S->wc, sizeof(__nv_bfloat16) * mlp::canon_weight_elems()));
   SCU(cudaMalloc(&S->wpart, sizeof(float) * 3 * kWpartElems));
+  SCU(cudaMalloc(&S->ticket, sizeof(unsigned)));
+  SCU(cudaMemsetAsync(S->ticket, 0, sizeof(unsigned), s));
   SCU(cudaMalloc(&S->err, sizeof(int)));
   SCU(cudaMalloc(&S->d_r0, sizeof(int64_t)));
   SCU(cudaStreamCreateWithFlags(&S->ts, cudaStreamNonBlocking));
@@ -549,13 +556,10 @@ extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features,
       wcp.w16[l] = S->w16[l];
       wcp.wt16[l] = S->wt16[l];
     }
+    // replayed form: Adam's last block also advances the batch start and the step
     SCU(mlp::adam(S->p, S->m, S->v, S->g, N_PARAMS, tp->lr, S->step + 1, dev ? S->d_step : nullptr,
-                  &wcp, s));
+                  &wcp, dev ? S->d_r0 : nullptr, B, S->ticket, s));
     S->wc_valid = false;  // the prediction's tensor-core layout is rebuilt when next needed
-    if (dev) {
-      advance_counters_kernel<<<1, 1, 0, s>>>(S->d_r0, B, S->d_step);
-      SCU(cudaGetLastError());
-    }
     return DOCK_OK;
   };
   // full batches replay one captured graph of the step (captured at the first)
