@@ -16,6 +16,7 @@
 #include "dock_internal.h"
 #include "surrogate_kernels.h"
 #include "handles.h"
+#include "nvtx_range.h"
 
 
 using namespace dk;
@@ -99,6 +100,7 @@ static void pair_coeffs(const dock_type_params *tp, int ti, int tj, double &c12,
 
 
 extern "C" int dock_create_pocket(const dock_pocket_desc *d, void *stream, dock_pocket **out) {
+  const dk::NvtxRange nvtx_range("dock_create_pocket");
   if (!d || !out) return fail(DOCK_EINVAL, "dock_create_pocket: NULL argument");
   *out = nullptr;
   if (d->n_types < 1 || d->n_types > DOCK_MAX_TYPES || !d->params)
@@ -529,6 +531,7 @@ static int checked_report(dock_ligands *L, cudaStream_t s, const char *what) {
 
 extern "C" int dock_load_ligands(const dock_pocket *P, const dock_ligand_batch *b, void *stream,
                                  dock_ligands **out) {
+  const dk::NvtxRange nvtx_range("dock_load_ligands");
   if (!P || !b || !out) return fail(DOCK_EINVAL, "dock_load_ligands: NULL argument");
   *out = nullptr;
   const int nl = b->n_ligands;
@@ -732,6 +735,7 @@ struct LaunchCfg {
 
 extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_params *sp, void *stream,
                           dock_job **out) {
+  const dk::NvtxRange nvtx_range("dock_batch");
   if (!P || !L || !sp || !out) return fail(DOCK_EINVAL, "dock_batch: NULL argument");
   *out = nullptr;
   if (sp->pop < 2 || sp->pop > DOCK_MAX_POP) return fail(DOCK_EINVAL, "dock_batch: pop %d", sp->pop);
@@ -1250,6 +1254,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
 }
 
 extern "C" int dock_results(dock_job *J, dock_result *out, int32_t cap, uint64_t timeout_ns) {
+  const dk::NvtxRange nvtx_range("dock_results");
   if (!J) return fail(DOCK_EINVAL, "dock_results: NULL job");
   if (cap < 0 || (cap > 0 && !out)) return fail(DOCK_EINVAL, "dock_results: bad output buffer");
   CU(cudaSetDevice(J->L->device));
@@ -1305,6 +1310,7 @@ extern "C" void dock_job_destroy(dock_job *J) { delete J; }
 extern "C" int dock_score(dock_pocket *P, dock_ligands *L, const int32_t *pose_ligand,
                           const float *genos, int64_t n_poses, float *scores, double *scores64,
                           float *coords, int32_t fp64, void *stream) {
+  const dk::NvtxRange nvtx_range("dock_score");
   if (!P || !L) return fail(DOCK_EINVAL, "dock_score: NULL pocket or ligands");
   if (n_poses < 0) return fail(DOCK_EINVAL, "dock_score: n_poses < 0");
   if (n_poses == 0) return DOCK_OK;
@@ -1360,6 +1366,7 @@ extern "C" int dock_local_search(dock_pocket *P, dock_ligands *L, const dock_ls_
                                  uint64_t seed, uint32_t generation, const int32_t *pose_ligand,
                                  int64_t n_poses, float *genos, float *scores, float *trace,
                                  uint32_t *evals, void *stream) {
+  const dk::NvtxRange nvtx_range("dock_local_search");
   if (!P || !L || !ls) return fail(DOCK_EINVAL, "dock_local_search: NULL argument");
   if (n_poses < 0) return fail(DOCK_EINVAL, "dock_local_search: n_poses < 0");
   const int st = check_ls_params(ls, "dock_local_search");
@@ -1411,6 +1418,7 @@ extern "C" int dock_local_search(dock_pocket *P, dock_ligands *L, const dock_ls_
 
 extern "C" int dock_score_pairwise(dock_pocket *P, dock_ligands *L, const int32_t *pose_ligand,
                                    const float *genos, int64_t n_poses, float *scores, void *stream) {
+  const dk::NvtxRange nvtx_range("dock_score_pairwise");
   if (!P || !L) return fail(DOCK_EINVAL, "dock_score_pairwise: NULL pocket or ligands");
   if (n_poses < 0) return fail(DOCK_EINVAL, "dock_score_pairwise: n_poses < 0");
   if (n_poses == 0) return DOCK_OK;
@@ -1441,6 +1449,7 @@ extern "C" int dock_score_pairwise(dock_pocket *P, dock_ligands *L, const int32_
 extern "C" int dock_features(dock_pocket *P, dock_ligands *L, const int32_t *pose_ligand,
                              const float *genotypes, int64_t n_poses, uint16_t *features,
                              float *scores, void *stream) {
+  const dk::NvtxRange nvtx_range("dock_features");
   if (!P || !L) return fail(DOCK_EINVAL, "dock_features: NULL pocket or ligands");
   if (n_poses < 0) return fail(DOCK_EINVAL, "dock_features: n_poses < 0");
   if (n_poses == 0) return DOCK_OK;
@@ -1524,6 +1533,7 @@ extern "C" int dock_features_population(dock_pocket *P, dock_ligands *L, int32_t
 // ---------------------------------------------------------------------------
 extern "C" int dock_autotune(dock_pocket *P, dock_ligands *L, const dock_search_params *sp,
                              void *stream, dock_tune_table *table) {
+  const dk::NvtxRange nvtx_range("dock_autotune");
   if (!P || !L || !sp || !table) return fail(DOCK_EINVAL, "dock_autotune: NULL argument");
   if (sp->mode != DOCK_MODE_PLAIN || sp->lanes_per_pose != 0)
     return fail(DOCK_EINVAL, "dock_autotune: tunes the plain search with lanes_per_pose = 0");

@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "handles.h"
+#include "nvtx_range.h"
 
 namespace dk {
 namespace {
@@ -60,6 +61,7 @@ __global__ void noalloc_items_kernel(const LigInfo *ligs, int n_ligands, int pop
 
 extern "C" int dock_batch_noalloc(dock_pocket *P, dock_ligands *L, const dock_search_params *sp,
                                   dock_result *results, void *stream) {
+  const dk::NvtxRange nvtx_range("dock_batch_noalloc");
   using namespace dk;
   if (!P || !L || !sp || !results) return fail(DOCK_EINVAL, "dock_batch_noalloc: NULL argument");
   if (sp->pop < 2 || sp->pop > DOCK_MAX_POP)

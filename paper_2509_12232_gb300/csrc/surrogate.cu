@@ -13,6 +13,7 @@
 
 #include "handles.h"
 #include "mlp.h"
+#include "nvtx_range.h"
 
 using namespace dk;
 using dk::mlp::FEATURES;
@@ -460,6 +461,7 @@ int dk_surrogate_predict_raw(dock_surrogate *S, const uint16_t *features, int64_
 
 extern "C" int dock_surrogate_predict(dock_surrogate *S, const uint16_t *features, int64_t n,
                                       float *out, void *stream) {
+  const dk::NvtxRange nvtx_range("dock_surrogate_predict");
   if (!S || (n > 0 && (!features || !out))) return sfail(DOCK_EINVAL, "dock_surrogate_predict: NULL");
   if (n < 0 || n > INT32_MAX) return sfail(DOCK_EINVAL, "dock_surrogate_predict: n out of range");
   if ((reinterpret_cast<uintptr_t>(features) & 15) != 0)
@@ -481,6 +483,7 @@ extern "C" int dock_surrogate_predict(dock_surrogate *S, const uint16_t *feature
 extern "C" int dock_surrogate_gradients(dock_surrogate *S, const uint16_t *features,
                                         const float *targets, int32_t n, float *grad, float *loss,
                                         void *stream) {
+  const dk::NvtxRange nvtx_range("dock_surrogate_gradients");
   if (!S || !features || !targets || !grad) return sfail(DOCK_EINVAL, "dock_surrogate_gradients: NULL");
   if (n < 1 || n > kMaxTrainBatch) return sfail(DOCK_EINVAL, "dock_surrogate_gradients: n %d", n);
   SCU(cudaSetDevice(S->device));
@@ -509,6 +512,7 @@ extern "C" int dock_surrogate_gradients(dock_surrogate *S, const uint16_t *featu
 extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features, const float *scores,
                                     int64_t n, const dock_train_params *tp, float *loss_per_epoch,
                                     void *stream) {
+  const dk::NvtxRange nvtx_range("dock_surrogate_train");
   if (!S || !features || !scores || !tp) return sfail(DOCK_EINVAL, "dock_surrogate_train: NULL");
   if (n < 2 || tp->epochs < 1 || tp->batch < 128 || tp->batch > kMaxTrainBatch || tp->batch % 128 ||
       !(tp->lr > 0.0f))
