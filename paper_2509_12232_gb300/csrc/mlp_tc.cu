@@ -3,16 +3,16 @@
 //
 // One persistent CTA per SM takes tiles of 128 feature rows, two at a time in
 // two slots, so that one slot's products run while the other slot's
-// epilogue runs (the epilogue is as long as the products):
+// epilogue runs (the epilogue is about as long as the products):
 //   - a slot's A operand (features, then each hidden layer) is a 64 KB tile
 //     in shared memory in the K-major "core matrix" layout the tensor core
-//     reads without swizzling (8 rows x 16 bytes per 128-byte block, blocks
-//     ordered by row group then by K); its accumulator is one half (256
-//     columns) of the CTA's tensor memory;
-//   - the BF16 weights are kept in global memory as chunks of 64 K columns
-//     (32 KB, the same layout with K = 64); a copy warp streams them, in the
-//     order the products use them, through a ring of two shared-memory
-//     stages (bulk asynchronous copies completing on the stage's "full"
+//     reads without swizzling (8 rows x 16 bytes per 128-byte block); its
+//     accumulator is one half (256 columns) of the CTA's tensor memory;
+//   - a copy warp fetches a slot's features by 2-D tensor copies once the
+//     slot's last product is done, and streams the BF16 weights, kept in
+//     global memory as chunks of 64 K columns (32 KB, the core-matrix layout
+//     with K = 64), in the order the products use them through a ring of two
+//     shared-memory stages (bulk copies completing on the stage's "full"
 //     mbarrier; the products that read a stage commit to its "empty" one);
 //   - an MMA warp issues, per slot and layer, tcgen05.mma (M = 128, N = 256,
 //     K = 16 per instruction) into the slot's accumulator once the slot's A
@@ -22,15 +22,14 @@
 //     32 (w mod 4) .. + 31 (the lane quarter its position in the warp group
 //     may access) and columns 64 (w / 4) .. + 63 with tcgen05.ld: GELU,
 //     rounding to BF16 and stores into the slot's A operand for the next
-//     layer, then they set those columns to the next layer's bias with
-//     tcgen05.st, so that the products accumulate onto it; after the third
-//     layer each thread forms a quarter of its row's
-//     output (a dot product with the FP32 w4) and parts 1-3 hand theirs to
-//     part 0 through shared memory. Each step signals the MMA warp through
-//     the slot's "A ready" mbarrier; the copy warp fetches the slot's next
-//     features (2-D tensor copies) once the slot's last product is done. The hidden activations
-//     are kept doubled and W2, W3 and w4 halved (exact powers of two: the
-//     same roundings and products, one multiply fewer per activation).
+//     layer; then they set those columns to the next layer's bias with
+//     tcgen05.st, so that the products accumulate onto it, and signal the
+//     MMA warp through the slot's "A ready" mbarrier. After the third layer
+//     each thread forms a quarter of its row's output (a dot product with the
+//     FP32 w4) and parts 1-3 hand theirs to part 0 through shared memory.
+// The hidden activations are kept doubled and W2, W3 and w4 halved (exact
+// powers of two: the same roundings and products, one multiply fewer per
+// activation).
 // Every mbarrier wait is bounded (one second of globaltimer) and also ends
 // when another role has given up; a timeout sets *err, the roles leave their
 // loops (the caller fills the output with NaN beforehand), and the tensor
