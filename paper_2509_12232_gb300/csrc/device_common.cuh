@@ -338,14 +338,6 @@ __device__ __forceinline__ float4 ld4(const float *p) {
   return v;
 }
 
-// One 256-bit read-only load (8 floats, 32-byte aligned address).
-__device__ __forceinline__ void ld8(const float *p, float (&v)[8]) {
-  asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
-                 "=f"(v[6]), "=f"(v[7])
-               : "l"(p));
-}
-
 // ---------------------------------------------------------------------------
 // Pair energy (FP32) from a 32-byte pair record
 // {c12, c6, c10, cap, qq, ds, bits(i | j << 16), 0} (weights folded in):

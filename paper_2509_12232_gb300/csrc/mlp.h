@@ -114,14 +114,10 @@ cudaError_t fused_forward(const __nv_bfloat16 *X, int64_t n, const __nv_bfloat16
 // *err is set if a device wait runs out (the output is then incomplete).
 cudaError_t tc_gemm_nt(const __nv_bfloat16 *A, int lda, const __nv_bfloat16 *Bt, int ldb, int M,
                        int K, int epi, const Epilogue &ep, int *err, cudaStream_t s);
-// C (FP32 [M][256]) = A^T B for A stored [K][M] and B stored [K][256] (the
-// weight gradients): both transposed to K-major copies (at and bt, M x K and
-// 256 x K BF16), K split over CTAs with FP32 partials in scratch (split x M x
-// 256 floats, split <= scratch_elems / (M 256)) summed in a fixed order.
-cudaError_t tc_gemm_tn_f32(const __nv_bfloat16 *A, int M, const __nv_bfloat16 *B, int K, float *C,
-                           __nv_bfloat16 *at, __nv_bfloat16 *bt, float *scratch,
-                           int64_t scratch_elems, int *err, cudaStream_t s);
-// The same from operands already K-major: at [M][K] (A^T) and bt [256][K] (B^T).
+// C (FP32 [M][256]) = A^T B (the weight gradients) from K-major copies of
+// the operands, at [M][K] (A^T) and bt [256][K] (B^T): K split over CTAs with
+// FP32 partials in scratch (split x M x 256 floats, split <= scratch_elems /
+// (M 256)) summed in a fixed order.
 cudaError_t tc_gemm_tt_f32(const __nv_bfloat16 *at, const __nv_bfloat16 *bt, int M, int K, float *C,
                            float *scratch, int64_t scratch_elems, int *err, cudaStream_t s);
 // out[c][r] = in[r][c] for in [rows][cols] BF16.

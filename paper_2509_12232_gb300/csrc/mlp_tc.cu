@@ -976,16 +976,5 @@ cudaError_t tc_gemm_tt_f32(const __nv_bfloat16 *at, const __nv_bfloat16 *bt, int
   return cudaGetLastError();
 }
 
-cudaError_t tc_gemm_tn_f32(const __nv_bfloat16 *A, int M, const __nv_bfloat16 *B, int K, float *C,
-                           __nv_bfloat16 *at, __nv_bfloat16 *bt, float *scratch,
-                           int64_t scratch_elems, int *err, cudaStream_t s) {
-  if (M <= 0) return cudaSuccess;
-  if (M % 128 || K % GK || K <= 0) return cudaErrorInvalidValue;
-  cudaError_t e = transpose_bf16(A, K, M, at, s);
-  if (e == cudaSuccess) e = transpose_bf16(B, K, HIDDEN, bt, s);
-  if (e != cudaSuccess) return e;
-  return tc_gemm_tt_f32(at, bt, M, K, C, scratch, scratch_elems, err, s);
-}
-
 }  // namespace mlp
 }  // namespace dk
