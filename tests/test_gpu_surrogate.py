@@ -127,9 +127,18 @@ def feature_rows(dock, env):
     return feats
 
 
-def test_mlp_gradients_match_oracle(dock, feature_rows):
+@pytest.mark.parametrize("rows", [256, 4096])
+def test_mlp_gradients_match_oracle(dock, feature_rows, rows):
+    """Gradients of one batch against the oracle's FP64 backward: 256 rows of
+    realistic features, and a full training batch (4,096 rows: 32 row tiles
+    per product, the split-K weight gradients at their training split)."""
     S = dock.dock_surrogate_create(seed=3)
-    X = feature_rows[:256]
+    if rows <= feature_rows.shape[0]:
+        X = feature_rows[:rows]
+    else:
+        g = torch.Generator(device="cuda").manual_seed(rows)
+        X = (torch.randn(rows, 128, device="cuda", generator=g) * 0.5).to(torch.bfloat16)
+        X = X.view(torch.int16)
     t = np.random.default_rng(4).normal(size=X.shape[0]).astype(np.float32)
     grad = torch.zeros(dock.DOCK_MLP_N_PARAMS, dtype=torch.float32, device="cuda")
     loss = dock.dock_surrogate_gradients(S, X, to_dev(torch, t), grad)
@@ -160,10 +169,11 @@ def test_mlp_predict_matches_oracle(dock, feature_rows):
     assert np.corrcoef(got, ref)[0, 1] > 0.999
 
 
-@pytest.mark.parametrize("n", [1, 127, 129, 50_001, 400_001])
+@pytest.mark.parametrize("n", [1, 127, 129, 50_001, 400_001, 4_194_304])
 def test_mlp_predict_tiles_and_ragged_tail(dock, n):
-    """The fused tensor-core forward pass over many 128-row tiles per CTA (the
-    largest case gives every CTA about ten rounds of its two tile slots) and
+    """The fused tensor-core forward pass over many 128-row tiles per CTA
+    (400,001 rows give every CTA about ten rounds of its two tile slots;
+    4,194,304 is the benchmark's pre-screened generation, sampled) and
     a ragged last tile: every sampled row equals the oracle's network within
     the BF16 budget, no row is left unwritten, a second call gives the same
     bits, and the result does not depend on how the rows are batched."""
