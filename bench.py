@@ -86,12 +86,38 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def src_hash():
+def src_hash(files=("search.cu", "pose.cuh", "device_common.cuh", "dock_internal.h")):
+    """Hash of the kernel sources a committed ncu summary was taken on."""
     h = hashlib.sha256()
-    for f in ("search.cu", "pose.cuh", "device_common.cuh", "dock_internal.h"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2509_12232_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+MLP_SOURCES = ("mlp_tc.cu", "mlp.h")
+
+
+def read_mlp_traffic(rows):
+    """DRAM bytes of one fused-forward launch over `rows` feature rows: the
+    committed ncu summary's bytes scaled by rows (the features are read once
+    and the weights come from L2, so the traffic grows with the rows), if the
+    summary was taken on the current kernel source, else None."""
+    p = os.path.join(ROOT, "profiles", "mlp_forward_1m.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_hash") != src_hash(MLP_SOURCES):
+        return None
+    try:
+        per_row = (float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])) / float(kv["rows"])
+    except (KeyError, ValueError):
+        return None
+    return round(per_row * rows)
 
 
 def read_profile():
@@ -627,7 +653,8 @@ def run_mlp(args, rank, world):
                                    "ligands x 4,096 candidates)" % (rows, rows // 4096),
                        "l2": "flushed between steps (256 MiB write)"},
             "roofline": {"bound": "tensor", "achieved": round(ach, 2), "peak": bf16,
-                         "unit": "TFLOP/s", "frac": round(ach / bf16, 4), "traffic": None,
+                         "unit": "TFLOP/s", "frac": round(ach / bf16, 4),
+                         "traffic": read_mlp_traffic(rows),
                          "kernel": "fused_forward_kernel",
                          "peak_source": "bf16_tflops (%s)" % peak_kind},
             "training": {"rows_per_epoch": n_tr, "batch": 4096, "s_per_epoch": round(tr_s, 4),
