@@ -375,7 +375,8 @@ int dock_batch_noalloc(dock_pocket *pocket, dock_ligands *ligands, const dock_se
  *   [104, 113) rotation matrix of the quaternion, row-major
  *   [113, 116) translation gene / R; 116: n / 100; 117: k / 16; rest 0.
  * Values are computed in FP32 and rounded to BF16 (round to nearest even).
- * The network is MLP 128 -> 256 -> 256 -> 256 -> 1 with GELU (erf form):
+ * The network is MLP 128 -> 256 -> 256 -> 256 -> 1 with GELU in its tanh form
+ * (within 4.7e-4 of the erf form, under the BF16 rounding of the activations):
  * BF16 weights and activations, FP32 accumulation on the tensor cores, FP32
  * master weights; parameters packed as W1[128][256], b1[256], W2[256][256],
  * b2[256], W3[256][256], b3[256], W4[256], b4 (W stored [in][out]). */
