@@ -86,10 +86,8 @@ __global__ void reduce_cols_kernel(const float *part, int blocks, int width, flo
 // With copies (training): the updated W1..W3 are also written as their BF16
 // copies w16 [in][out] and wt16 [out][in] (what cast_weights_kernel makes).
 __device__ __forceinline__ void adam_one(float *p, float *m, float *v, const float *g, int i,
-                                         float lr, float b1, float b2, float eps, int step,
-                                         const int *step_dev, const WeightCopies &wc) {
-  const float t = (float)(step_dev ? *step_dev : step);
-  const float c1 = 1.0f - powf(b1, t), c2 = 1.0f - powf(b2, t);
+                                         float lr, float b1, float b2, float eps, float c1,
+                                         float c2, const WeightCopies &wc) {
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.0f - b1) * gi;
   const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
@@ -116,7 +114,15 @@ __global__ void adam_kernel(float *p, float *m, float *v, const float *g, int n,
                             float b2, float eps, int step, int *step_dev, WeightCopies wc,
                             int64_t *r0_dev, int64_t batch, unsigned *ticket) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) adam_one(p, m, v, g, i, lr, b1, b2, eps, step, step_dev, wc);
+  // the bias corrections 1 - b^t, once per block
+  __shared__ float s_c[2];
+  if (threadIdx.x == 0) {
+    const float t = (float)(step_dev ? *step_dev : step);
+    s_c[0] = 1.0f - powf(b1, t);
+    s_c[1] = 1.0f - powf(b2, t);
+  }
+  __syncthreads();
+  if (i < n) adam_one(p, m, v, g, i, lr, b1, b2, eps, s_c[0], s_c[1], wc);
   if (r0_dev == nullptr) return;
   // the last block to finish (every block has read the step) advances the counters
   __syncthreads();

@@ -91,10 +91,18 @@ __device__ __forceinline__ uint64_t train_row(const TrainOrder &o, uint64_t r) {
   return o.n;  // unreachable: the row is then skipped (zeros)
 }
 
+// order[i] = pi(i) for i < n: the run's order of the training rows, made
+// once so that a step's gather reads it instead of walking the permutation.
+__global__ void train_order_kernel(TrainOrder o, int64_t n, int64_t *order) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    order[i] = (int64_t)train_row(o, (uint64_t)i);
+}
+
 // Gathers `rows` rows (r < rows_valid real, the rest zero) into the batch:
-// with use_order, row r is training row pi(r0 + r), else row r.
-__global__ void gather_rows_kernel(const __nv_bfloat16 *X, const float *t, int use_order,
-                                   TrainOrder o, int64_t r0, const int64_t *r0_dev, int64_t n_src,
+// row r is training row order[r0 + r] when order is given, else row r.
+__global__ void gather_rows_kernel(const __nv_bfloat16 *X, const float *t, const int64_t *order,
+                                   int64_t r0, const int64_t *r0_dev, int64_t n_src,
                                    int rows,
                                    int rows_valid, __nv_bfloat16 *Xb, float *tb, float t_mean,
                                    float t_inv_std, float t_clip) {
@@ -105,7 +113,7 @@ __global__ void gather_rows_kernel(const __nv_bfloat16 *X, const float *t, int u
   uint2 v = make_uint2(0, 0);
   float tv = 0.0f;
   if (r < rows_valid) {
-    const int64_t src = use_order ? (int64_t)train_row(o, (uint64_t)(r0 + r)) : r;
+    const int64_t src = order ? order[r0 + r] : r;
     if (src < n_src) {
       v = reinterpret_cast<const uint2 *>(X + src * FEATURES)[lane];
       if (t) tv = (fminf(t[src], t_clip) - t_mean) * t_inv_std;
@@ -180,6 +188,8 @@ struct dock_surrogate {
   cudaEvent_t ev_dz[3] = {nullptr, nullptr, nullptr}, ev_w[3] = {nullptr, nullptr, nullptr},
               ev_c = nullptr;
   float *cpart = nullptr;  // column-sum partials of the bias gradients
+  int64_t *order = nullptr;  // the training rows' order for the current run
+  int64_t order_cap = 0;
   float t_mean = 0.0f, t_std = 1.0f, t_clip = 1e30f;
   // weights of the fused tensor-core forward pass (refreshed lazily after the
   // FP32 masters change) and its device error flag
@@ -206,6 +216,7 @@ struct dock_surrogate {
     for (cudaStream_t q : {ts_w[0], ts_w[1], ts_w[2]}) if (q) cudaStreamDestroy(q);
     if (ts_c) cudaStreamDestroy(ts_c);
     if (cpart) cudaFree(cpart);
+    if (order) cudaFree(order);
     for (int l = 0; l < 3; ++l) {
       if (w16[l]) cudaFree(w16[l]);
       if (wt16[l]) cudaFree(wt16[l]);
@@ -493,7 +504,7 @@ extern "C" int dock_surrogate_gradients(dock_surrogate *S, const uint16_t *featu
   if (st != DOCK_OK) return st;
   // targets used as given (identity standardisation)
   gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(
-      reinterpret_cast<const __nv_bfloat16 *>(features), targets, 0, TrainOrder{}, 0, nullptr, n,
+      reinterpret_cast<const __nv_bfloat16 *>(features), targets, nullptr, 0, nullptr, n,
       rows, n, S->X, S->t, 0.0f, 1.0f, 3.0e38f);
   SCU(cudaGetLastError());
   if ((st = forward(S, rows, true, s)) != DOCK_OK) return st;
@@ -539,6 +550,15 @@ extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features,
   S->t_clip = clip;
   // one order of the rows for the run, keyed by the seed (the same every epoch)
   const TrainOrder ord = make_train_order(tp->seed, (uint64_t)n);
+  if (S->order_cap < n) {
+    if (S->order) cudaFree(S->order);
+    S->order = nullptr;
+    S->order_cap = 0;
+    SCU(cudaMalloc(&S->order, sizeof(int64_t) * (size_t)n));
+    S->order_cap = n;
+  }
+  train_order_kernel<<<152 * 8, 256, 0, s>>>(ord, n, S->order);
+  SCU(cudaGetLastError());
   const __nv_bfloat16 *F = reinterpret_cast<const __nv_bfloat16 *>(features);
   const int B = tp->batch;
   const int64_t steps_per_epoch = (n + B - 1) / B;
@@ -548,7 +568,7 @@ extern "C" int dock_surrogate_train(dock_surrogate *S, const uint16_t *features,
   auto step_body = [&](int64_t r0, int valid, bool dev) -> int {
     const int rows = (valid + 127) / 128 * 128;
     gather_rows_kernel<<<(rows * 32 + 255) / 256, 256, 0, s>>>(
-        F, scores, 1, ord, r0, dev ? S->d_r0 : nullptr, n, rows, valid, S->X, S->t, S->t_mean,
+        F, scores, S->order, r0, dev ? S->d_r0 : nullptr, n, rows, valid, S->X, S->t, S->t_mean,
         1.0f / S->t_std, clip);
     SCU(cudaGetLastError());
     int rc;
