@@ -186,7 +186,7 @@ struct dock_surrogate {
   // beside its chain of input gradients, forked and joined by events
   cudaStream_t ts_w[3] = {nullptr, nullptr, nullptr}, ts_c = nullptr;
   cudaEvent_t ev_dz[3] = {nullptr, nullptr, nullptr}, ev_w[3] = {nullptr, nullptr, nullptr},
-              ev_c = nullptr;
+              ev_c = nullptr, ev_x = nullptr;
   float *cpart = nullptr;  // column-sum partials of the bias gradients
   int64_t *order = nullptr;  // the training rows' order for the current run
   int64_t order_cap = 0;
@@ -210,7 +210,7 @@ struct dock_surrogate {
     if (d_step) cudaFree(d_step);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
-    for (cudaEvent_t e : {ev_dz[0], ev_dz[1], ev_dz[2], ev_w[0], ev_w[1], ev_w[2], ev_c})
+    for (cudaEvent_t e : {ev_dz[0], ev_dz[1], ev_dz[2], ev_w[0], ev_w[1], ev_w[2], ev_c, ev_x})
       if (e) cudaEventDestroy(e);
     if (ts) cudaStreamDestroy(ts);
     for (cudaStream_t q : {ts_w[0], ts_w[1], ts_w[2]}) if (q) cudaStreamDestroy(q);
@@ -323,6 +323,11 @@ static int forward(dock_surrogate *S, int rows, bool keep, cudaStream_t s) {
 // ts_w[l]) and bias gradient (on ts_c) start once its dZ is written, and s waits
 // for both before it returns (also inside a captured step graph).
 static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
+  // X^T for the first layer's weight gradient, on its side stream while the
+  // input-gradient chain runs (X is final once the forward pass is queued)
+  SCU(cudaEventRecord(S->ev_x, s));
+  SCU(cudaStreamWaitEvent(S->ts_w[0], S->ev_x, 0));
+  SCU(mlp::transpose_bf16(S->X, rows, FEATURES, S->at, S->ts_w[0]));
   // dW4 and db4 straight into the gradient, the loss into outg[HIDDEN + 1]
   SCU(mlp::out_layer_bwd(S->y, S->ydot, S->p + mlp::OFF_B4, S->t, n, rows, S->H[2], S->Z[2],
                          S->p + mlp::OFF_W4, S->dZ[2], S->part, kBwdBlocks, S->g + mlp::OFF_W4,
@@ -332,10 +337,9 @@ static int backward(dock_surrogate *S, int rows, int n, cudaStream_t s) {
     SCU(cudaStreamWaitEvent(S->ts_w[l], S->ev_dz[l], 0));
     SCU(cudaStreamWaitEvent(S->ts_c, S->ev_dz[l], 0));
     // dW_l = act_in^T dZ_l (tensor cores, K = rows split over CTAs) from
-    // K-major copies: H_{l-1}^T and dZ_l^T from the epilogues, X^T and dZ_2^T
-    // transposed here
+    // K-major copies: H_{l-1}^T and dZ_l^T from the epilogues, X^T (above) and
+    // dZ_2^T transposed here
     const __nv_bfloat16 *at = l ? S->Ht[l - 1] : S->at, *bt = l < 2 ? S->dZt[l] : S->bt;
-    if (l == 0) SCU(mlp::transpose_bf16(S->X, rows, FEATURES, S->at, S->ts_w[0]));
     if (l == 2) SCU(mlp::transpose_bf16(S->dZ[2], rows, HIDDEN, S->bt, S->ts_w[2]));
     SCU(mlp::tc_gemm_tt_f32(at, bt, kIn[l], rows, S->g + kOffW[l], S->wpart + l * kWpartElems,
                             kWpartElems, S->err, S->ts_w[l]));
@@ -397,7 +401,7 @@ extern "C" int dock_surrogate_create(uint64_t seed, void *stream, dock_surrogate
   for (int l = 0; l < 3; ++l) SCU(cudaStreamCreateWithFlags(&S->ts_w[l], cudaStreamNonBlocking));
   SCU(cudaStreamCreateWithFlags(&S->ts_c, cudaStreamNonBlocking));
   for (cudaEvent_t *e : {&S->ev_dz[0], &S->ev_dz[1], &S->ev_dz[2], &S->ev_w[0], &S->ev_w[1],
-                         &S->ev_w[2], &S->ev_c})
+                         &S->ev_w[2], &S->ev_c, &S->ev_x})
     SCU(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   SCU(cudaMalloc(&S->cpart, sizeof(float) * mlp::kColsumChunks * HIDDEN));
   SCU(cudaEventCreateWithFlags(&S->ev_in, cudaEventDisableTiming));
