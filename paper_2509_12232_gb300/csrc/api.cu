@@ -680,45 +680,52 @@ struct LaunchGroup {
   int32_t ls_L, ls_apl;                   // lanes per chain, shared-memory atoms per lane
 };
 
-// With ls (Lamarckian search), each group's search launch is followed on the
-// same stream by its Solis-Wets launch over the same items (queue counter
-// 4 + group).
+// One group's launches of generation a.gen on stream st: its search launch,
+// then, with ls (Lamarckian search), its Solis-Wets launch over the same items
+// (queue counters i and 4 + i of the generation).
+static cudaError_t enqueue_group(const SearchArgs &a, const std::vector<LaunchGroup> &groups,
+                                 size_t i, int threads, cudaStream_t st, const LsArgs *ls,
+                                 bool pairwise) {
+  SearchArgs b = a;
+  b.items = a.items + groups[i].begin;
+  b.n_items = groups[i].count;
+  b.counter = a.counter + i;
+  cudaError_t r = launch_search(b, groups[i].blocks, threads, groups[i].L, st, pairwise);
+  if (r != cudaSuccess || ls == nullptr) return r;
+  if (groups[i].ls_count == 0) return r;
+  LsArgs c = *ls;
+  const int64_t gl = (int64_t)a.gen * c.n_ligands;
+  c.units = ls->units + groups[i].ls_begin;
+  c.n_units = groups[i].ls_count;
+  c.counter = a.counter + 4 + i;
+  c.gen = (uint32_t)a.gen;
+  c.sel_bits = ls->sel_bits + gl * c.sel_words;
+  c.sel_count = ls->sel_count + gl;
+  c.chain_ctr = ls->chain_ctr + gl;
+  c.atoms_per_lane = groups[i].ls_apl;
+  c.geno = a.geno_next;
+  c.score = a.score_next;
+  c.best = a.best_next;
+  return launch_ls(c, groups[i].ls_blocks, threads, groups[i].ls_L, st);
+}
+
+// The launches of one generation, every group forked from q onto the
+// workspace's side streams and joined back, so a group's CTAs take over SMs as
+// the previous group's queue drains.
 static cudaError_t enqueue_search(Workspace &W, const SearchArgs &a, const std::vector<LaunchGroup> &groups,
                                   int threads, cudaStream_t q, const LsArgs *ls = nullptr,
                                   bool pairwise = false) {
   cudaError_t e = cudaSuccess;
-  auto one = [&](size_t i, cudaStream_t st) {
-    SearchArgs b = a;
-    b.items = a.items + groups[i].begin;
-    b.n_items = groups[i].count;
-    b.counter = a.counter + i;
-    cudaError_t r = launch_search(b, groups[i].blocks, threads, groups[i].L, st, pairwise);
-    if (r != cudaSuccess || ls == nullptr) return r;
-    if (groups[i].ls_count == 0) return r;
-    LsArgs c = *ls;
-    const int64_t gl = (int64_t)a.gen * c.n_ligands;
-    c.units = ls->units + groups[i].ls_begin;
-    c.n_units = groups[i].ls_count;
-    c.counter = a.counter + 4 + i;
-    c.gen = (uint32_t)a.gen;
-    c.sel_bits = ls->sel_bits + gl * c.sel_words;
-    c.sel_count = ls->sel_count + gl;
-    c.chain_ctr = ls->chain_ctr + gl;
-    c.atoms_per_lane = groups[i].ls_apl;
-    c.geno = a.geno_next;
-    c.score = a.score_next;
-    c.best = a.best_next;
-    return launch_ls(c, groups[i].ls_blocks, threads, groups[i].ls_L, st);
-  };
   if (groups.empty()) return cudaSuccess;
-  if (groups.size() == 1) return one(0, q);
+  if (groups.size() == 1) return enqueue_group(a, groups, 0, threads, q, ls, pairwise);
   if ((e = cudaEventRecord(W.fork, q)) != cudaSuccess) return e;
   for (size_t i = 1; i < groups.size(); ++i) {
     if ((e = cudaStreamWaitEvent(W.side[i - 1], W.fork, 0)) != cudaSuccess) return e;
-    if ((e = one(i, W.side[i - 1])) != cudaSuccess) return e;
+    if ((e = enqueue_group(a, groups, i, threads, W.side[i - 1], ls, pairwise)) != cudaSuccess)
+      return e;
     if ((e = cudaEventRecord(W.join[i - 1], W.side[i - 1])) != cudaSuccess) return e;
   }
-  if ((e = one(0, q)) != cudaSuccess) return e;
+  if ((e = enqueue_group(a, groups, 0, threads, q, ls, pairwise)) != cudaSuccess) return e;
   for (size_t i = 1; i < groups.size(); ++i)
     if ((e = cudaStreamWaitEvent(q, W.join[i - 1], 0)) != cudaSuccess) return e;
   return cudaSuccess;
@@ -1131,6 +1138,15 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   };
 
   const int g_first = resume ? sp->resume_from + 1 : 0;  // first generation this call runs
+  // The groups hold disjoint ligands and every buffer a generation writes is
+  // indexed by ligand (genotypes, scores, best keys, Solis-Wets selections and
+  // chain counters), so unless a whole generation is copied out (traces) or
+  // timed, each group runs its generations on its own stream and the streams
+  // join once, before the finalize: one group's tail (the last items of a
+  // generation, the longest Solis-Wets chains) overlaps the others' next
+  // generations instead of idling SMs at a join per generation.
+  const bool free_run = groups.size() > 1 && !sur && !profile && !sp->trace_genotypes &&
+                        !sp->trace_scores;
   auto enqueue = [&](cudaStream_t q) -> int {
     CU(cudaMemsetAsync(W.counters, 0, sizeof(uint32_t) * gens * 8, q));
     if (lamarck) {
@@ -1155,7 +1171,7 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
                            cudaMemcpyDeviceToDevice, q));
       CU(launch_best_keys(W.score[g & 1], nl, pop, W.best + (size_t)g * nl, q));
     }
-    for (int g = g_first; g < gens; ++g) {
+    auto gen_args = [&](int g) {
       SearchArgs a = A;
       a.gen = g;
       a.counter = W.counters + (size_t)g * 8;  // 4 search + 4 local-search queues
@@ -1165,13 +1181,37 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
       a.score_next = W.score[g & 1];
       a.best_prev = g ? W.best + (size_t)(g - 1) * nl : nullptr;
       a.best_next = W.best + (size_t)g * nl;
+      return a;
+    };
+    auto gen_ls = [&](int g) {
+      LsArgs la = LA;
+      if (lamarck && sp->trace_ls)
+        la.trace = sp->trace_ls + (size_t)g * n_scores * (size_t)(2 + 2 * sp->ls.max_its);
+      return la;
+    };
+    if (free_run) {
+      // each group runs all its generations on its own stream; one join
+      CU(cudaEventRecord(W.fork, q));
+      for (size_t i = 1; i < groups.size(); ++i) CU(cudaStreamWaitEvent(W.side[i - 1], W.fork, 0));
+      for (int g = g_first; g < gens; ++g) {
+        const SearchArgs a = gen_args(g);
+        const LsArgs la = gen_ls(g);
+        for (size_t i = 0; i < groups.size(); ++i)
+          CU(enqueue_group(a, groups, i, cfg.threads, i ? W.side[i - 1] : q,
+                           lamarck ? &la : nullptr, pairwise));
+      }
+      for (size_t i = 1; i < groups.size(); ++i) {
+        CU(cudaEventRecord(W.join[i - 1], W.side[i - 1]));
+        CU(cudaStreamWaitEvent(q, W.join[i - 1], 0));
+      }
+    }
+    for (int g = free_run ? gens : g_first; g < gens; ++g) {
+      const SearchArgs a = gen_args(g);
       if (sur && g > 0) {
         const int st2 = surrogate_generation(g, q);
         if (st2 != DOCK_OK) return st2;
       } else {
-        LsArgs la = LA;
-        if (lamarck && sp->trace_ls)
-          la.trace = sp->trace_ls + (size_t)g * n_scores * (size_t)(2 + 2 * sp->ls.max_its);
+        const LsArgs la = gen_ls(g);
         if (profile) {
           cudaEvent_t e0, e1;
           CU(cudaEventCreate(&e0));

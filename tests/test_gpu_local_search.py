@@ -215,6 +215,29 @@ def test_lamarckian_improves_on_the_plain_ga(dock, setup):
     assert np.mean(best["plain"] - best["lga"]) > 0.5
 
 
+@pytest.mark.parametrize("mode", ["plain", "lga", "pairwise"])
+def test_free_running_groups_match_the_joined_schedule(dock, setup, mode):
+    """Untraced, each lanes-per-pose group (here four: 1, 2, 4 and 8 lanes) runs
+    all its generations on its own stream and the streams join once; with a
+    score trace every generation joins. A ligand's arithmetic does not depend
+    on the schedule, so the result records are identical field by field."""
+    pocket, gl, nl = setup["pocket"], setup["gl"], setup["ligs"].n_ligands
+    pop, gens = 64, 8
+    ls = dock.ls_params(0.06, 300) if mode == "lga" else None
+    inter = dock.DOCK_INTER_PAIRWISE if mode == "pairwise" else dock.DOCK_INTER_GRID
+    ts = torch.zeros(gens * nl * pop, dtype=torch.float32, device="cuda")
+    out = []
+    for trace in (None, ts):
+        job = dock.dock_batch(pocket, gl, pop, gens, seed=3, stream=torch.cuda.current_stream(),
+                              ls=ls, inter=inter, trace_scores=trace, **SEARCH)
+        out.append(dock.dock_results(job))
+        job.close()
+    free, joined = out
+    assert np.all(free["status"] == 0)
+    for name in free.dtype.names:
+        np.testing.assert_array_equal(free[name], joined[name], err_msg=name)
+
+
 def test_bad_pose_ligand_and_invalid_settings(dock, setup):
     pocket, gl = setup["pocket"], setup["gl"]
     g = np.zeros((3, 23), np.float32)
