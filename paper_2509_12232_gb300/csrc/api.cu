@@ -1141,12 +1141,20 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   // The groups hold disjoint ligands and every buffer a generation writes is
   // indexed by ligand (genotypes, scores, best keys, Solis-Wets selections and
   // chain counters), so unless a whole generation is copied out (traces) or
-  // timed, each group runs its generations on its own stream and the streams
-  // join once, before the finalize: one group's tail (the last items of a
-  // generation, the longest Solis-Wets chains) overlaps the others' next
-  // generations instead of idling SMs at a join per generation.
+  // timed, each group can run its generations on its own stream, the streams
+  // joined once, before the finalize: one group's tail (the last items of a
+  // generation, the longest Solis-Wets chains) then overlaps the others' next
+  // generations instead of idling SMs at a join per generation. That pays
+  // where tails are a sizeable share of a generation: with local search, or
+  // when a persistent CTA takes few items per generation (c2: about 30;
+  // 62.0 vs 62.9 ms per step). With hundreds per CTA (c3: about 600) the
+  // tails are negligible and groups that stay in step share the SMs better
+  // (1,500 vs 1,541 ms per step with free-running groups).
+  int64_t most_per_block = 0;
+  for (const LaunchGroup &gr : groups)
+    most_per_block = std::max<int64_t>(most_per_block, gr.count / std::max(gr.blocks, 1));
   const bool free_run = groups.size() > 1 && !sur && !profile && !sp->trace_genotypes &&
-                        !sp->trace_scores;
+                        !sp->trace_scores && (lamarck || most_per_block < 128);
   auto enqueue = [&](cudaStream_t q) -> int {
     CU(cudaMemsetAsync(W.counters, 0, sizeof(uint32_t) * gens * 8, q));
     if (lamarck) {
