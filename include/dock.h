@@ -259,6 +259,16 @@ typedef struct dock_job dock_job;
  * exactly (FP32) and keeps the best pop of population and kept candidates by
  * exact score (ties: population first, then index); every reported score is
  * exact. */
+/* Environment overrides of the launch shape, for tuning and benchmarking (read
+ * at each call; unset = dock_autotune's pick for these ligands, else 128
+ * threads x 16 atoms per lane): DOCK_THREADS (CTA threads, a power of two in
+ * 32..128), DOCK_ATOMS_PER_LANE (shared-memory atoms per lane; raised to fit
+ * the largest ligand in 8 lanes), DOCK_LS_LANES (lanes per Solis-Wets chain:
+ * 0, 1, 2, 4, 8, 16 or 32, at least the search's lanes per pose; default 16)
+ * and DOCK_LS_CHAINS (chains a lane group runs one after another; raised to at
+ * least 0.25; default 2). DOCK_THREADS or DOCK_LS_LANES outside those values
+ * fails with DOCK_EINVAL. None changes what is computed, only which lanes sum
+ * which terms and so the rounding of the FP32 sums. */
 int dock_batch(dock_pocket *pocket, dock_ligands *ligands, const dock_search_params *params,
                void *stream, dock_job **out);
 
