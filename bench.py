@@ -637,12 +637,19 @@ def run_mlp(args, rank, world):
     ach = flops_row * rows / (ms / 1000.0) / 1e12
     n_tr = 2 << 20
     Y = torch.randn(n_tr, device="cuda", generator=g)
-    dock.dock_surrogate_train(S, X[:n_tr], Y, epochs=1, batch=4096)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    dock.dock_surrogate_train(S, X[:n_tr], Y, epochs=2, batch=4096)
-    torch.cuda.synchronize()
-    tr_s = (time.perf_counter() - t0) / 2
+    # training throughput by batch size: a step is a dozen dependent small
+    # launches, so small batches are bound by the chain, large ones by the products
+    by_batch = {}
+    for b in (4096, 16384, 65536):
+        dock.dock_surrogate_train(S, X[:n_tr], Y, epochs=1, batch=b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dock.dock_surrogate_train(S, X[:n_tr], Y, epochs=2, batch=b)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / 2
+        by_batch[b] = {"s_per_epoch": round(sec, 4), "us_per_step": round(sec / (n_tr // b) * 1e6, 1),
+                       "tflops": round(3 * flops_row * n_tr / sec / 1e12, 2)}
+    tr_s = by_batch[4096]["s_per_epoch"]
     line = {"metric": "surrogate candidates predicted per s (fused tensor-core forward pass, "
                       "128-256-256-256-1 BF16 MLP)",
             "value": round(rows / (ms / 1000.0), 1), "unit": "rows/s", "n_gpus": 1,
@@ -658,7 +665,8 @@ def run_mlp(args, rank, world):
                          "kernel": "fused_forward_kernel",
                          "peak_source": "bf16_tflops (%s)" % peak_kind},
             "training": {"rows_per_epoch": n_tr, "batch": 4096, "s_per_epoch": round(tr_s, 4),
-                         "tflops": round(3 * flops_row * n_tr / tr_s / 1e12, 2)}}
+                         "tflops": round(3 * flops_row * n_tr / tr_s / 1e12, 2),
+                         "by_batch": by_batch}}
     print(json.dumps(line), flush=True)
     return 0
 

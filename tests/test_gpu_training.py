@@ -128,3 +128,39 @@ def test_two_batch_epoch_uses_the_order_in_batches(dock, data):
     tight = err <= 1e-7 + 1e-6 * np.abs(p)
     assert tight.mean() >= 0.999, (float(tight.mean()), float(err.max()))
     assert np.all(err <= 2e-6 + 1e-5 * np.abs(p)), float(err.max())
+
+
+@pytest.mark.parametrize("rows", [16384, 65536])
+def test_large_batch_step_matches_oracle(dock, rows):
+    """One Adam step on a batch of 16,384 or 65,536 rows (the sizes the
+    training benchmark times; the training products then span hundreds of
+    tiles and the reductions many blocks): the FP32 masters after the step
+    equal the oracle's FP64 Adam step from the initial masters with the
+    gradient at them, to FP32 rounding."""
+    rng = np.random.default_rng(rows)
+    X = rng.normal(0, 0.6, size=(rows, 128))
+    X[:, 118:] = 0.0
+    Xb = _bf16_bits(X)
+    scores = rng.normal(-6.0, 3.0, size=rows).astype(np.float32)
+    seed_w, seed_order = 5, 11
+    S = dock.dock_surrogate_create(seed=seed_w)
+    W0 = dock.dock_surrogate_get_params(S)[0]
+    dock.dock_surrogate_train(S, to_dev(torch, Xb.view(np.int16)), to_dev(torch, scores), epochs=1,
+                              batch=rows, lr=LR, score_clip=CLIP, seed=seed_order)
+    W1, tm, ts, _ = dock.dock_surrogate_get_params(S)
+    order = o.train_order(seed_order, rows)
+    inv = np.float32(1.0) / np.float32(ts)
+    tgt = ((np.minimum(scores[order], np.float32(CLIP)) - np.float32(tm)) * inv).astype(np.float32)
+    G = dock.dock_surrogate_create(seed=seed_w)
+    dock.dock_surrogate_set_params(G, W0, tm, ts, CLIP)
+    grad = torch.zeros(dock.DOCK_MLP_N_PARAMS, dtype=torch.float32, device="cuda")
+    dock.dock_surrogate_gradients(G, to_dev(torch, Xb[order].view(np.int16)), to_dev(torch, tgt), grad)
+    torch.cuda.synchronize()
+    p = W0.astype(np.float64)
+    m, v = np.zeros_like(p), np.zeros_like(p)
+    o.adam_step(p, m, v, grad.cpu().numpy().astype(np.float64), 1, lr=LR)
+    err = np.abs(W1.astype(np.float64) - p)
+    assert np.all(err <= 5e-8 + 3e-7 * np.abs(p)), float(err.max())
+    assert np.median(np.abs(W1 - W0)) > 0.3 * LR
+    S.close()
+    G.close()
