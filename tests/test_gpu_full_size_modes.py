@@ -170,3 +170,28 @@ def test_lamarckian_c2_full_size_sampled(dock, c2):
     assert checked >= 500 and near <= checked // 20
     assert np.all(res["status"] == 0)
     assert np.all(res["exact_evals"] > pop * gens)
+
+
+@pytest.mark.parametrize("mode", ["plain", "lga", "nogrid"])
+def test_c2_free_running_groups_match_the_joined_schedule(dock, c2, mode):
+    """At the full c2 size an untraced search runs each lanes-per-pose group's
+    generations on its own stream, joined once (about 30 work items per
+    persistent CTA and generation); a score trace makes every generation join.
+    The result records of the two schedules are identical field by field."""
+    w, gl, nl = c2["w"], c2["gl"], c2["ligs"].n_ligands
+    kw = dict(p_cross=0.8, p_mut=0.02)
+    if mode == "lga":
+        kw["ls"] = dock.ls_params(0.06, 300)
+    if mode == "nogrid":
+        kw["inter"] = dock.DOCK_INTER_PAIRWISE
+    ts = torch.zeros(w.generations * nl * w.pop, dtype=torch.float32, device="cuda")
+    out = []
+    for trace in (None, ts):
+        job = dock.dock_batch(c2["pocket"], gl, w.pop, w.generations, seed=1, use_graph=1,
+                              trace_scores=trace, stream=torch.cuda.current_stream(), **kw)
+        out.append(dock.dock_results(job))
+        job.close()
+    free, joined = out
+    assert np.all(free["status"] == 0)
+    for name in free.dtype.names:
+        np.testing.assert_array_equal(free[name], joined[name], err_msg=name)
