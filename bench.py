@@ -996,8 +996,13 @@ def main():
 
     # end to end through the public API from host arrays, as a screening run
     # streams its batches: a second host thread prepares and uploads batch
-    # k + 1 (dock_load_ligands on a side stream) while batch k is searched;
-    # the first batch's preparation (pipeline fill) is inside the timed region
+    # k + 1 (dock_load_ligands on a side stream) while batch k is searched,
+    # and batch k's results are read once batch k + 1 is queued behind it, so
+    # the GPU does not idle while the host reads results and enqueues. The
+    # ligand sets are destroyed after the last results (freeing device memory
+    # waits for the whole device to drain); the first batch's preparation
+    # (pipeline fill), the last batch's results and the destroys are inside
+    # the timed region
     h2d = info["h2d_bytes"]
     d2h = ligs.n_ligands * dock.RESULT_DTYPE.itemsize + 4
     side = torch.cuda.Stream()
@@ -1010,14 +1015,22 @@ def main():
     with ThreadPoolExecutor(1) as ex:
         t0 = time.perf_counter()
         nxt = ex.submit(load)
+        prev, sets = None, []
         for i in range(args.e2e_steps):
             g2 = nxt.result()
+            sets.append(g2)
             j = dock.dock_batch(pocket, g2, w.pop, w.generations, seed=0, use_graph=1,
                                 stream=stream, ls=ls, inter=inter)
             if i + 1 < args.e2e_steps:
                 nxt = ex.submit(load)
-            dock.dock_results(j)
-            j.close()
+            if prev is not None:
+                dock.dock_results(prev)
+                prev.close()
+            prev = j
+        if prev is not None:
+            dock.dock_results(prev)
+            prev.close()
+        for g2 in sets:
             g2.close()
         e2e_s = (time.perf_counter() - t0) / max(args.e2e_steps, 1)
     if world > 1:
@@ -1077,7 +1090,9 @@ def main():
                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                     "steps": args.e2e_steps,
                     "pipeline": "batch k+1 prepared and uploaded by a second host thread "
-                                "while batch k is searched; first preparation included"},
+                                "while batch k is searched; batch k's results read once batch "
+                                "k+1 is queued; ligand sets destroyed after the last results; "
+                                "first preparation, last results and destroys included"},
             "gpu_launches": args.steps * (w.generations * len(groups) * (2 if lga else 1) + 1),
             "clocks": clk}
     if nogrid:

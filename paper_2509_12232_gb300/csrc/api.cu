@@ -900,13 +900,21 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     }
     CU(cudaEventCreateWithFlags(&W.fork, cudaEventDisableTiming));
   }
+  if (!W.io) {
+    CU(cudaStreamCreateWithFlags(&W.io, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&W.io_done, cudaEventDisableTiming));
+  }
+  // buffers allocated by this call: no queued work can be reading them
+  bool fresh_items = false, fresh_goff = false, fresh_units = false;
   if (host_items.size() > W.item_cap || !W.items) {
     dfree(W.items);
     W.item_cap = 0;
     CU(dalloc(&W.items, host_items.size()));
     W.item_cap = host_items.size();
+    fresh_items = true;
   }
   if ((size_t)nl > W.lig_cap || !W.geno_off) {
+    fresh_goff = true;
     dfree(W.geno_off);
     dfree(W.lig_status);
     dfree(W.results);
@@ -942,14 +950,33 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
       W.ls_units_cap = 0;
       CU(dalloc(&W.ls_units, host_units.size()));
       W.ls_units_cap = host_units.size();
+      fresh_units = true;
     }
-    if (!host_units.empty())
-      CU(cudaMemcpyAsync(W.ls_units, host_units.data(), sizeof(int32_t) * host_units.size(),
-                         cudaMemcpyHostToDevice, s));
   }
-  CU(cudaMemcpyAsync(W.geno_off, goff.data(), sizeof(int64_t) * nl, cudaMemcpyHostToDevice, s));
-  CU(cudaMemcpyAsync(W.items, host_items.data(), sizeof(Item) * host_items.size(),
-                     cudaMemcpyHostToDevice, s));
+  // The host tables: one the device already holds is not copied again; one
+  // going into a buffer allocated above is copied on the io stream, which s
+  // then waits for; a changed one in a buffer that searches queued on s may
+  // still read is copied on s, after them.
+  bool io_used = false;
+  auto upload = [&](void *dst, const void *src, size_t bytes, std::vector<uint8_t> &last,
+                    bool fresh) -> cudaError_t {
+    const uint8_t *b = static_cast<const uint8_t *>(src);
+    if (!fresh && last.size() == bytes && (bytes == 0 || memcmp(last.data(), b, bytes) == 0))
+      return cudaSuccess;
+    last.assign(b, b + bytes);
+    if (bytes == 0) return cudaSuccess;
+    io_used |= fresh;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, fresh ? W.io : s);
+  };
+  if (lamarck)
+    CU(upload(W.ls_units, host_units.data(), sizeof(int32_t) * host_units.size(), W.up_units,
+              fresh_units));
+  CU(upload(W.geno_off, goff.data(), sizeof(int64_t) * nl, W.up_goff, fresh_goff));
+  CU(upload(W.items, host_items.data(), sizeof(Item) * host_items.size(), W.up_items, fresh_items));
+  if (io_used) {
+    CU(cudaEventRecord(W.io_done, W.io));
+    CU(cudaStreamWaitEvent(s, W.io_done, 0));
+  }
   int n_sm = 0;
   CU(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, L->device));
   for (LaunchGroup &gr : groups) {
@@ -1316,10 +1343,15 @@ extern "C" int dock_results(dock_job *J, dock_result *out, int32_t cap, uint64_t
     if (timeout_ns && el > timeout_ns) return fail(DOCK_ETIMEOUT, "dock_results: job still running");
     std::this_thread::sleep_for(std::chrono::microseconds(50));
   }
+  // read on the workspace's own stream: a copy on the legacy default stream
+  // would also wait for any search queued there after this job
+  Workspace &W = J->L->ws;
   int32_t status = 0;
-  CU(cudaMemcpy(&status, J->L->ws.status, sizeof status, cudaMemcpyDeviceToHost));
+  CU(cudaMemcpyAsync(&status, W.status, sizeof status, cudaMemcpyDeviceToHost, W.io));
   const int n = std::min(cap, J->n_ligands);
-  if (n > 0) CU(cudaMemcpy(out, J->L->ws.results, sizeof(dock_result) * n, cudaMemcpyDeviceToHost));
+  if (n > 0)
+    CU(cudaMemcpyAsync(out, W.results, sizeof(dock_result) * n, cudaMemcpyDeviceToHost, W.io));
+  CU(cudaStreamSynchronize(W.io));
   if (status == DOCK_ETIMEOUT) return fail(DOCK_ETIMEOUT, "dock_results: device deadline exceeded");
   if (status <= kCheckBase)
     return fail(DOCK_EDEVICE, "dock_results: bounds check failed at site %d", kCheckBase - status);

@@ -141,6 +141,15 @@ struct Workspace {
   // run concurrently, forked from the caller's stream and joined back
   cudaStream_t side[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t fork = nullptr, join[3] = {nullptr, nullptr, nullptr};
+  // Host-to-device tables of dock_batch and the device-to-host reads of
+  // dock_results go through `io`, a stream of their own: a copy from or to
+  // pageable host memory on the caller's stream would wait for everything
+  // queued there (the previous search, or a later one), stalling the host
+  // while the GPU drains. up_* hold the bytes each table last received, so a
+  // repeated search on the same set copies nothing.
+  cudaStream_t io = nullptr;
+  cudaEvent_t io_done = nullptr;
+  std::vector<uint8_t> up_goff, up_items, up_units;
   // cached graph
   cudaGraphExec_t graph = nullptr;
   std::vector<uint8_t> graph_key;
@@ -175,6 +184,8 @@ struct Workspace {
       if (join[i]) cudaEventDestroy(join[i]);
     }
     if (fork) cudaEventDestroy(fork);
+    if (io) cudaStreamDestroy(io);
+    if (io_done) cudaEventDestroy(io_done);
   }
 };
 
