@@ -963,10 +963,14 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
     const uint8_t *b = static_cast<const uint8_t *>(src);
     if (!fresh && last.size() == bytes && (bytes == 0 || memcmp(last.data(), b, bytes) == 0))
       return cudaSuccess;
+    last.clear();  // unknown until the copy is queued
+    if (bytes) {
+      const cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, fresh ? W.io : s);
+      if (e != cudaSuccess) return e;
+      io_used |= fresh;
+    }
     last.assign(b, b + bytes);
-    if (bytes == 0) return cudaSuccess;
-    io_used |= fresh;
-    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, fresh ? W.io : s);
+    return cudaSuccess;
   };
   if (lamarck)
     CU(upload(W.ls_units, host_units.data(), sizeof(int32_t) * host_units.size(), W.up_units,
