@@ -1177,10 +1177,11 @@ extern "C" int dock_batch(dock_pocket *P, dock_ligands *L, const dock_search_par
   // generation, the longest Solis-Wets chains) then overlaps the others' next
   // generations instead of idling SMs at a join per generation. That pays
   // where tails are a sizeable share of a generation: with local search, or
-  // when a persistent CTA takes few items per generation (c2: about 30;
-  // 62.0 vs 62.9 ms per step). With hundreds per CTA (c3: about 600) the
-  // tails are negligible and groups that stay in step share the SMs better
-  // (1,500 vs 1,541 ms per step with free-running groups).
+  // when a persistent CTA takes few items per generation (1,000 ligands of
+  // 10-60 atoms x 1,024 poses: about 30; 62.0 vs 62.9 ms per search). With
+  // hundreds per CTA (100,000 ligands of 8-100 atoms x 512 poses: about 600)
+  // the tails are negligible and groups that stay in step share the SMs
+  // better (1,500 vs 1,541 ms per search with free-running groups).
   int64_t most_per_block = 0;
   for (const LaunchGroup &gr : groups)
     most_per_block = std::max<int64_t>(most_per_block, gr.count / std::max(gr.blocks, 1));
